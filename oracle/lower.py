@@ -1,0 +1,287 @@
+"""Lower-level trajectory optimisation, FP64, batched over samples p_j.
+
+Follows Sec. III-C (cost and constraints), Alg. 1 Step 1 with Eq. (over_2),
+Appendix A (Table I, Eqs. sphere_proposed .. lane_reform, the augmented
+Lagrangian aug_lag) and Alg. 2 (Eqs. split_xy .. update_lagrange).  All
+matrices are assembled literally (F stacks W once per obstacle, G = [W; -W]
+on the y block) so the code can be read against the paper.
+
+Shapes: B samples, m timesteps, n coefficients per axis, N obstacles.
+xi is (B, 2n) = [c_x | c_y].
+
+Readings of the paper adopted here:
+  * PD tracking (Eq. cost, printed with unbalanced parentheses): stable
+    tracking c_l = (ydd + kp (y - y_d) + kv yd)^2, c_v = (xdd + kp (xd - v_d))^2,
+    weights of c_s, c_l, c_v all one.
+  * Equality constraints: initial state b0 only (the goal rows of
+    Eq. final_boundary are not part of p in the paper's MPC-Bi-Level).
+  * Ellipse: a, b are the semi-axes used in Table I's collision expression;
+    h_y uses y_o + b d sin(alpha) (the printed "x_o + a d sin" is a slip).
+  * v_min-bar of Eq. (clip_d_v): max(v_min, sqrt(d_a |sin(a_a - a_v)| / kappa_max)),
+    i.e. Eq. (d_reform_2) solved for d_v; v_max-bar from Eq. (d_reform_3),
+    equal to v_max on a straight road.  clip(x, lo, hi) = min(max(x, lo), hi).
+  * a_max-bar (Eq. clip_d_a) when |sin| = 0: a_max.
+  * atan2(0, 0) = 0.
+  * Slack (Eq. update_slack, printed sign garbled): s = max(0, e - G xi).
+  * Multipliers (Eq. update_lagrange, operator missing between the terms):
+    lambda <- lambda - rho/2 F^T (F xi - h) - rho/2 G^T (G xi - e + s).
+  * Alg. 2 start: xi^0 = xi_bar, lambda^0 = 0, d_a^{-1} = min(|a(xi^0)|, a_max),
+    then alpha^0, d^0, s^0 from xi^0 by the same steps as an iteration.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+# ----------------------------------------------------------------------------
+# behavioural inputs -> set-point vectors
+# ----------------------------------------------------------------------------
+
+def segment_lengths(m: int, n_seg: int):
+    """Contiguous segments; with m = n_seg*q + r the first r get q+1 steps."""
+    q, r = divmod(m, n_seg)
+    return [q + 1 if j < r else q for j in range(n_seg)]
+
+
+def setpoint_vectors(p: np.ndarray, m: int, n_seg: int):
+    """y_d, v_d (B, m): each segment's set-point repeated over its steps
+    (Sec. III-C, the sentence after the cost terms; p per Eq. behaviour_param)."""
+    seg_of_t = np.repeat(np.arange(n_seg), segment_lengths(m, n_seg))
+    return p[:, :n_seg][:, seg_of_t], p[:, n_seg:][:, seg_of_t]
+
+
+def lane_bounds(scene, prm):
+    """y_lb, y_ub of Table I's lane-boundary row (straight road, margin inside)."""
+    return prm.lane_margin, scene.n_lanes * scene.lane_width - prm.lane_margin
+
+
+def obstacle_trajectories(scene, m: int, dt: float):
+    """x_o,i(t), y_o,i(t), (N, m): constant-velocity neighbours."""
+    t = np.arange(m) * dt
+    ob = np.asarray(scene.obstacles, dtype=np.float64).reshape(-1, 6)
+    xo = ob[:, 0:1] + ob[:, 2:3] * t[None, :]
+    yo = ob[:, 1:2] + ob[:, 3:4] * t[None, :]
+    return xo, yo, ob[:, 4:5], ob[:, 5:6]
+
+
+# ----------------------------------------------------------------------------
+# Step 1: QP without inequalities (Alg. 1 line 7, Eq. over_2)
+# ----------------------------------------------------------------------------
+
+def step1_cost_matrices(basis, prm):
+    """Per-axis (Q, L): cost sum_t c_s + c_v (x) and c_s + c_l (y) as
+    1/2 c^T Q c + q^T c with q = -2 k L^T (set-point)."""
+    W, Wd, Wdd = basis
+    Lx = Wdd + prm.kp_lon * Wd
+    Ly = Wdd + prm.kv_lat * Wd + prm.kp_lat * W
+    Qx = 2.0 * (Wdd.T @ Wdd + Lx.T @ Lx)
+    Qy = 2.0 * (Wdd.T @ Wdd + Ly.T @ Ly)
+    return (Qx, Lx), (Qy, Ly)
+
+
+def initial_rows(basis):
+    """A of one axis: position, velocity and acceleration at t0."""
+    W, Wd, Wdd = basis
+    return np.stack([W[0], Wd[0], Wdd[0]])
+
+
+def kkt_solve(Q, A, rhs_top, rhs_bot):
+    """Solve [[Q, A^T], [A, 0]] [z; mu] = [rhs_top; rhs_bot] for B columns
+    (LU with partial pivoting via numpy); returns z (B, n)."""
+    n, ne = Q.shape[0], A.shape[0]
+    K = np.zeros((n + ne, n + ne))
+    K[:n, :n] = Q
+    K[:n, n:] = A.T
+    K[n:, :n] = A
+    R = np.concatenate([rhs_top.T, np.broadcast_to(np.asarray(rhs_bot, float).reshape(ne, -1),
+                                                     (ne, rhs_top.shape[0]))], axis=0)
+    return np.linalg.solve(K, R)[:n].T
+
+
+def step1(p, scene, prm, basis):
+    """xi_bar (B, 2n): the equality-constrained QP of Alg. 1 line 7 for each p_j."""
+    m = basis[0].shape[0]
+    yd, vd = setpoint_vectors(np.atleast_2d(p), m, prm.n_seg)
+    (Qx, Lx), (Qy, Ly) = step1_cost_matrices(basis, prm)
+    A = initial_rows(basis)
+    x0, y0, vx0, vy0, ax0, ay0 = np.asarray(scene.ego, dtype=np.float64)
+    qx = -2.0 * prm.kp_lon * (vd @ Lx)          # (B, n) rows are (L^T v_d)^T
+    qy = -2.0 * prm.kp_lat * (yd @ Ly)
+    cx = kkt_solve(Qx, A, -qx, [x0, vx0, ax0])
+    cy = kkt_solve(Qy, A, -qy, [y0, vy0, ay0])
+    return np.concatenate([cx, cy], axis=1)
+
+
+# ----------------------------------------------------------------------------
+# Alg. 2: batch projection
+# ----------------------------------------------------------------------------
+
+def projection_operators(basis, n_obs: int):
+    """F (Eq. after lane_reform), G (lane rows, y block) and A_eq, literal."""
+    W, Wd, Wdd = basis
+    m, n = W.shape
+    Fax = np.vstack([W] * n_obs + [Wd, Wdd])
+    Z = np.zeros_like(Fax)
+    F = np.block([[Fax, Z], [Z, Fax]])
+    Zm = np.zeros_like(W)
+    G = np.block([[Zm, W], [Zm, -W]])
+    Aax = initial_rows(basis)
+    Za = np.zeros_like(Aax)
+    A = np.block([[Aax, Za], [Za, Aax]])
+    return F, G, A
+
+
+def _angle(sy, cx):
+    """atan2 with the convention atan2(0, 0) = 0 whatever the zero signs."""
+    return np.where((sy == 0) & (cx == 0), 0.0, np.arctan2(sy, cx))
+
+
+def kinematics(xi, basis):
+    """x, y, xd, yd, xdd, ydd, each (B, m), through Eq. (param)."""
+    W, Wd, Wdd = basis
+    n = W.shape[1]
+    cx, cy = xi[:, :n], xi[:, n:]
+    return cx @ W.T, cy @ W.T, cx @ Wd.T, cy @ Wd.T, cx @ Wdd.T, cy @ Wdd.T
+
+
+def alpha_d_step(xi, scene, prm, basis, da_prev):
+    """Eq. (split_alpha_o) followed by the clips (clip_d_o), (clip_d_v), (clip_d_a).
+
+    The unconstrained minimiser of ||F xi - h(alpha, d)||^2 makes every block
+    residual zero: for obstacle i, (x - x_o, y - y_o) = (a d cos(al), b d sin(al))
+    gives al = atan2((y - y_o)/b, (x - x_o)/a), d = its scaled length; for the
+    velocity and acceleration blocks the polar angle and magnitude.
+    Returns h (B, rows of F), the clipped d_a (B, m) and the pieces as a dict.
+    """
+    W = basis[0]
+    m = W.shape[0]
+    x, y, xd, yd, xdd, ydd = kinematics(xi, basis)
+    xo, yo, a, b = obstacle_trajectories(scene, m, prm.dt)
+
+    # obstacles, (B, N, m)
+    dx = x[:, None, :] - xo[None]
+    dy = y[:, None, :] - yo[None]
+    al_o = _angle(dy / b[None], dx / a[None])
+    d_o = np.sqrt((dx / a[None]) ** 2 + (dy / b[None]) ** 2)
+    d_o = np.maximum(1.0, d_o)                                   # clip_d_o
+    hox = xo[None] + a[None] * d_o * np.cos(al_o)
+    hoy = yo[None] + b[None] * d_o * np.sin(al_o)
+
+    # velocity and acceleration, (B, m)
+    al_v = _angle(yd, xd)
+    d_v = np.hypot(xd, yd)
+    al_a = _angle(ydd, xdd)
+    d_a = np.hypot(xdd, ydd)
+    S = np.abs(np.sin(al_a - al_v))
+    vmin_bar = np.maximum(prm.v_min, np.sqrt(da_prev * S / prm.kappa_max))
+    cos2 = np.cos(al_v) ** 2
+    kr = abs(scene.kappa_road)
+    with np.errstate(divide="ignore"):
+        vmax_bar = np.where(kr * cos2 > 0.0,
+                            np.minimum(prm.v_max, np.sqrt(prm.c_max / np.maximum(kr * cos2, 1e-300))),
+                            prm.v_max)
+    d_v = np.minimum(np.maximum(d_v, vmin_bar), vmax_bar)        # clip_d_v
+    kd = d_v ** 2 * prm.kappa_max
+    with np.errstate(divide="ignore", invalid="ignore"):
+        amax_bar = np.where(S * prm.a_max <= kd, prm.a_max, kd / S)
+    d_a = np.minimum(np.maximum(d_a, 0.0), amax_bar)             # clip_d_a
+
+    hvx, hvy = d_v * np.cos(al_v), d_v * np.sin(al_v)
+    hax, hay = d_a * np.cos(al_a), d_a * np.sin(al_a)
+    B = xi.shape[0]
+    h = np.concatenate([hox.reshape(B, -1), hvx, hax, hoy.reshape(B, -1), hvy, hay], axis=1)
+    parts = dict(d_o=d_o, al_o=al_o, d_v=d_v, al_v=al_v, d_a=d_a, al_a=al_a,
+                 vmin_bar=vmin_bar, vmax_bar=vmax_bar, amax_bar=amax_bar,
+                 hox=hox, hoy=hoy, hv=(hvx, hvy), ha=(hax, hay))
+    return h, d_a, parts
+
+
+def lane_vector(scene, prm, m):
+    """e of Eq. (lane_reform): G xi <= e with G = [W; -W] on the y block."""
+    ylb, yub = lane_bounds(scene, prm)
+    return np.concatenate([np.full(m, yub), np.full(m, -ylb)])
+
+
+def slack_step(xi, G, e):
+    """s = max(0, e - G xi), the minimiser of ||G xi - e + s||^2 over s >= 0."""
+    return np.maximum(0.0, e[None, :] - xi @ G.T)
+
+
+def xi_step(xi_bar, lam, h, s, ops, e, b_eq, rho):
+    """Eq. (split_xy): minimise the augmented Lagrangian over xi with A xi = b."""
+    F, G, A = ops
+    nn = F.shape[1]
+    H = np.eye(nn) + rho * (F.T @ F) + rho * (G.T @ G)
+    rhs = xi_bar + lam + rho * (h @ F) + rho * ((e[None, :] - s) @ G)
+    return kkt_solve(H, A, rhs, b_eq)
+
+
+def project(xi_bar, scene, prm, basis, iters: int | None = None, trace: bool = False):
+    """Alg. 2 for every row of xi_bar; returns xi^K (and a per-iteration trace).
+
+    The trace holds, per iteration, the mean over samples of
+    ||F xi - h|| + ||G xi - e + s|| (the residual the multipliers drive to zero).
+    """
+    K = prm.inner_iters if iters is None else iters
+    m = basis[0].shape[0]
+    ops = projection_operators(basis, scene.n_obs)
+    F, G, A = ops
+    e = lane_vector(scene, prm, m)
+    x0, y0, vx0, vy0, ax0, ay0 = np.asarray(scene.ego, dtype=np.float64)
+    b_eq = [x0, vx0, ax0, y0, vy0, ay0]
+
+    xi = np.array(xi_bar, dtype=np.float64, copy=True)
+    lam = np.zeros_like(xi)
+    _, _, _, _, xdd, ydd = kinematics(xi, basis)
+    da = np.minimum(np.hypot(xdd, ydd), prm.a_max)
+    h, da, _ = alpha_d_step(xi, scene, prm, basis, da)
+    s = slack_step(xi, G, e)
+    hist = []
+    for _ in range(K):
+        xi = xi_step(xi_bar, lam, h, s, ops, e, b_eq, prm.rho)           # split_xy
+        h, da, _ = alpha_d_step(xi, scene, prm, basis, da)              # split_alpha_o + clips
+        s = slack_step(xi, G, e)                                        # update_slack
+        rf = xi @ F.T - h
+        rg = xi @ G.T - e[None, :] + s
+        lam = lam - 0.5 * prm.rho * (rf @ F) - 0.5 * prm.rho * (rg @ G)  # update_lagrange
+        if trace:
+            hist.append(float(np.mean(np.linalg.norm(rf, axis=1) + np.linalg.norm(rg, axis=1))))
+    return (xi, hist) if trace else xi
+
+
+# ----------------------------------------------------------------------------
+# scoring (Alg. 1 line 9 and the upper-level cost of Sec. V-A)
+# ----------------------------------------------------------------------------
+
+def score(xi, scene, prm, basis):
+    """r_j = sum over t (and obstacles) of max(0, g) for every row of Table I,
+    and c_u = sum_t (sqrt(xd^2 + yd^2) - v_max)^2.  Returns (r, c_u), (B,) each.
+
+    Curvature is taken as 0 where the speed is exactly 0.
+    """
+    m = basis[0].shape[0]
+    x, y, xd, yd, xdd, ydd = kinematics(xi, basis)
+    xo, yo, a, b = obstacle_trajectories(scene, m, prm.dt)
+    dx = x[:, None, :] - xo[None]
+    dy = y[:, None, :] - yo[None]
+    coll = np.maximum(0.0, 1.0 - (dx / a[None]) ** 2 - (dy / b[None]) ** 2).sum(axis=(1, 2))
+    speed = np.hypot(xd, yd)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        kappa = np.where(speed > 0.0, (ydd * xd - xdd * yd) / speed ** 3, 0.0)
+    ylb, yub = lane_bounds(scene, prm)
+    per_t = (np.maximum(0.0, speed - prm.v_max)
+             + np.maximum(0.0, np.hypot(xdd, ydd) - prm.a_max)
+             + np.maximum(0.0, np.abs(kappa) - prm.kappa_max)
+             + np.maximum(0.0, xd ** 2 * abs(scene.kappa_road) - prm.c_max)
+             + np.maximum(0.0, y - yub) + np.maximum(0.0, ylb - y))
+    r = coll + per_t.sum(axis=1)
+    cu = ((speed - prm.v_max) ** 2).sum(axis=1)
+    return r, cu
+
+
+def solve(p, scene, prm, basis, iters: int | None = None):
+    """Alg. 1 lines 6-9 for every p_j: Step 1, Step 2 (Alg. 2), residual and cost."""
+    xb = step1(p, scene, prm, basis)
+    xs = project(xb, scene, prm, basis, iters)
+    r, cu = score(xs, scene, prm, basis)
+    return xs, r, cu
