@@ -1,0 +1,338 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 bi-level planner on the dense-traffic workload.
+
+One step = one MPC cycle = Alg. 1 with L = 5 outer iterations over one scene
+(4 lanes, 12 constant-velocity obstacles), B = 1000 sampled behavioural inputs,
+m = 100 timesteps, 11 Bernstein coefficients per axis, K = 100 projection
+iterations, ConstraintEliteSet 150 and EliteSet 50 (the paper's sizes).
+
+value  : sample-iterations / s = B * K * L / device time of one cycle, inputs
+         resident in HBM, CUDA events on the launching stream, L2 flushed
+         (256 MiB write) before every timed cycle.
+e2e    : the same metric through plan_step with host buffers (scene and
+         distribution uploaded, best pair and distribution read back).
+plain_fp64 : the same cycle on the plain float64 path (reference GPU path).
+roofline   : the fused solve kernel against the FP32 FMA pipe.
+cpu_baseline: the FP64 oracle on a bounded sample, one host thread.
+
+--impl reference times the FP64 CPU oracle on the same metric instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = ("dense-traffic single scene: 4 lanes, 12 obstacles, B=1000 samples, m=100 steps, "
+            "n=11 coefficients/axis, K=100 projection iterations, L=5 CEM iterations, elites 150/50")
+METRIC = "plan solves/sec (samples x inner iters x outer iters)"
+UNIT = "sample-iters/s"
+FP32_LANES_PER_SM = 128
+SM_COUNT_NOMINAL = 152
+
+
+def algorithmic_flops_per_sample_iter(m, n, N, n_eq=3):
+    """Per sample and Alg. 2 iteration: forward and transposed contractions
+    (24 m n), obstacle projection (12 N m), velocity / acceleration / lane rows
+    (40 m), multiplier and xi-step updates (4 n^2 + 4 n n_eq)."""
+    return 24 * m * n + 12 * N * m + 40 * m + 4 * n * n + 4 * n * n_eq
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+_ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from oracle import lower
+from oracle.basis import bernstein
+from paper_2212_02224_gb300 import scenegen as sg
+prm, sc, B = sg.workload(1)
+basis = bernstein(prm.m, prm.n_coef, prm.dt)
+p = sg.make_samples(303, sc, {nsamp}, prm.n_seg)
+lower.solve(p[:2], sc, prm, basis, iters=2)          # warm caches / imports
+t0 = time.perf_counter(); reps = 0
+while True:
+    lower.solve(p, sc, prm, basis)
+    reps += 1
+    if time.perf_counter() - t0 >= {budget}:
+        break
+dt = time.perf_counter() - t0
+print(json.dumps(dict(units=reps * {nsamp} * prm.inner_iters, seconds=dt, reps=reps)))
+"""
+
+
+def run_oracle(nsamp=40, budget=12.0):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = _ORACLE_SNIPPET.format(root=ROOT, nsamp=nsamp, budget=budget)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         timeout=600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr)
+    res = json.loads(out.stdout.strip().splitlines()[-1])
+    return dict(value=res["units"] / res["seconds"], unit=UNIT, cores=1, kind="oracle",
+                sample=f"{res['reps']} x lower-level solve of {nsamp} samples of the workload "
+                       f"(K=100), numpy float64, one thread; one sample-iteration = one Alg. 2 "
+                       f"iteration of one sample")
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    def __init__(self, index=0):
+        self.proc = None
+        self.path = None
+        self.index = index
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                rows.append((float(f[0]), float(f[1]), f[4:8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v == "Active"})
+        return dict(sm_mhz=statistics.median(r[0] for r in rows), sm_max_mhz=max(r[1] for r in rows),
+                    reasons=reasons, samples=len(rows))
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+
+    from paper_2212_02224_gb300 import scenegen as sg
+    from paper_2212_02224_gb300.planner import Planner
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    prm, sc, B = sg.workload(1)
+    K, L = prm.inner_iters, prm.outer_iters
+    units = B * K * L
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- value: resident inputs, graph-captured cycle
+    pl = Planner(prm, prec="fp32", max_obs=16, max_samples=B)
+    pl.upload([sc])
+    pl.set_state(0, seed=1234 + rank)
+    for _ in range(args.warmup):
+        pl.step_resident([B])
+    barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record(stream)
+            pl.step_resident([B])
+            ends[i].record(stream)
+        barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_s = sum(step_ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([total_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * units * args.steps / total_s
+    clocks = clk.summary()
+
+    # ---- e2e: through host buffers (plan_step), wall clock per cycle
+    e2e_ms = []
+    mu = sigma = None
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = pl.step(sc, B, mu=mu, sigma=sigma, seed=99, step=i)
+        dt_ms = (time.perf_counter() - t0) * 1e3
+        if i >= args.warmup:
+            e2e_ms.append(dt_ms)
+    e2e_total = sum(e2e_ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([e2e_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * units * len(e2e_ms) / e2e_total
+    dev_scene = 96 + 48 * sc.n_obs
+    dev_cem = 1464
+    h2d = dev_scene + dev_cem
+    d2h = 2 * dev_cem
+
+    # ---- roofline of the fused solve kernel (timed alone on this stream)
+    p = torch.tensor(sg.make_samples(303, sc, B, prm.n_seg), dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        pl.solve(sc, p, want_xi=False)
+    reps = 20
+    ks = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    ke = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    for i in range(reps):
+        flush.zero_()
+        ks[i].record(stream)
+        pl.solve(sc, p, want_xi=False)
+        ke[i].record(stream)
+    torch.cuda.synchronize()
+    kern_ms = statistics.mean(s.elapsed_time(e) for s, e in zip(ks, ke))
+    flops = algorithmic_flops_per_sample_iter(prm.m, prm.n_coef, sc.n_obs) * B * K
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_clock = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = sms * FP32_LANES_PER_SM * 2 * peak_clock * 1e6 / 1e12
+    achieved = flops / (kern_ms * 1e-3) / 1e12
+    pl.close()
+
+    # ---- plain FP64 path, same cycle
+    plain = None
+    if not args.skip_fp64:
+        pf = Planner(prm, prec="fp64", max_obs=16, max_samples=B)
+        pf.upload([sc])
+        pf.set_state(0, seed=1234 + rank)
+        pf.step_resident([B])
+        torch.cuda.synchronize()
+        n64 = max(1, min(args.steps, 3))
+        fs = [torch.cuda.Event(enable_timing=True) for _ in range(n64)]
+        fe = [torch.cuda.Event(enable_timing=True) for _ in range(n64)]
+        for i in range(n64):
+            flush.zero_()
+            fs[i].record(stream)
+            pf.step_resident([B])
+            fe[i].record(stream)
+        torch.cuda.synchronize()
+        ms64 = statistics.mean(s.elapsed_time(e) for s, e in zip(fs, fe))
+        plain = dict(value=units / (ms64 * 1e-3), unit=UNIT, ms_per_step=ms64, steps=n64)
+        pf.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        cpu = run_oracle()
+
+    if rank == 0:
+        srt = sorted(e2e_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": f"replicas{world}",
+                       "l2": "flushed before every timed step (256 MiB write)",
+                       "graph": "whole cycle captured as one CUDA graph"},
+            "latency_ms": {"p50": statistics.median(step_ms),
+                           "p99": float(np.percentile(step_ms, 99)),
+                           "e2e_p50": statistics.median(e2e_ms),
+                           "e2e_p99": float(np.percentile(srt, 99))},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps * 3 * L,
+            "plain_fp64": plain,
+            "speedup_vs_plain_fp64": (value / plain["value"]) if plain else None,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "fused_kernel<11,4> (one lower-level solve, B=1000, K=100)",
+                         "kernel_ms": kern_ms,
+                         "peak_basis": f"FP32 FMA pipe: {sms} SMs x 128 lanes x 2 flop x "
+                                       f"{peak_clock:.0f} MHz"},
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def reference_arm(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals = []
+    per_step = max(3.0, 60.0 / max(1, args.steps + args.warmup))
+    for i in range(args.warmup + args.steps):
+        r = run_oracle(nsamp=20, budget=per_step)
+        if i >= args.warmup:
+            vals.append(r)
+    value = statistics.mean(v["value"] for v in vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "parallelism": "none (CPU oracle)"},
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
+                         "sample": vals[0]["sample"].replace("40 samples", "20 samples")},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

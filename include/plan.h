@@ -1,0 +1,245 @@
+/*
+ * plan.h -- C ABI of the GB300 batched bi-level trajectory planner.
+ *
+ * The library implements the data-parallel hot path of "Bi-Level Optimization
+ * Augmented with Conditional Variational Autoencoder for Autonomous Driving in
+ * Dense Traffic" (Singh, Shrestha, Albarella): for each of B sampled
+ * behavioural inputs p_j it solves the lower-level trajectory problem (Step 1
+ * QP of Alg. 1 via the shared KKT inverse of Eq. over_3, then the batch
+ * projection of Alg. 2), scores every solution (Alg. 1 line 9 and the
+ * upper-level cost of Sec. V-A) and runs the gradient-free outer loop of
+ * Alg. 1 (elite sets, distribution update of Eqs. mean_update / cov_update /
+ * s_formula, re-sampling).
+ *
+ * Conventions shared by every call:
+ *   - Every function returns a plan_status; none aborts, throws or exits.
+ *     On an error return no device work has been enqueued by that call and
+ *     plan_last_error() describes the failure.
+ *   - Floating-point buffers at this boundary are IEEE float64, row-major.
+ *   - "device" pointers are CUDA global memory of the device that was current
+ *     when plan_init ran; "host" pointers are ordinary process memory
+ *     (pinned memory makes the copies asynchronous).
+ *   - Work is enqueued on the caller's stream (a cudaStream_t passed as
+ *     void*, NULL = the legacy default stream) and is asynchronous unless the
+ *     function says otherwise; results are valid after the stream is
+ *     synchronised.
+ *   - Inputs are copied into the context before the call returns; callers keep
+ *     ownership of every buffer they pass.
+ *   - A context is not thread-safe: use one per host thread, or lock.
+ *
+ * Coordinates: a scene is expressed in a frame where the road's lanes run
+ * along +x, lane i spans y in [i w, (i+1) w] and the lane-boundary
+ * constraint of Table I is y_lb <= y <= y_ub with y_lb = lane_margin and
+ * y_ub = n_lanes w - lane_margin.
+ */
+#ifndef PLAN_H_
+#define PLAN_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct plan_ctx plan_ctx;   /* opaque; owns all device memory it uses */
+
+typedef enum {
+    PLAN_OK = 0,
+    PLAN_EINVAL = -1,      /* an argument is out of range or inconsistent      */
+    PLAN_ENOMEM = -2,      /* a device or pinned-host allocation failed        */
+    PLAN_ECAPACITY = -3,   /* request exceeds the capacities given to plan_init */
+    PLAN_ETIMEOUT = -4,    /* a bounded wait expired                            */
+    PLAN_ECUDA = -5,       /* a CUDA runtime call failed (see plan_last_error) */
+    PLAN_ESTATE = -6,      /* call not valid in the context's current state    */
+    PLAN_ENONFINITE = -7   /* a result is not finite                            */
+} plan_status;
+
+/* Arithmetic of the lower-level solve.  FP64: one kernel per step of Alg. 2
+ * with intermediates in HBM, float64 throughout (the reference GPU path).
+ * FP32: the fused multi-iteration kernel, float32 projections and
+ * contractions with constants formed and inverted in float64. */
+typedef enum {
+    PLAN_PREC_FP64 = 0,
+    PLAN_PREC_FP32 = 1
+} plan_prec;
+
+/* Planner configuration (plan_init).  Symbols follow the paper.
+ *   m            timesteps t_i = i dt of the horizon (Eq. param), 8..256
+ *   n_coef       polynomial coefficients per axis (degree + 1), 4..16; the
+ *                paper uses a 10th-order polynomial, n_coef = 11 (Sec. V-A)
+ *   n_seg        set-point segments of p (Eq. behaviour_param), 1..4;
+ *                p = [y_d,1..y_d,n_seg, v_d,1..v_d,n_seg] has d_p = 2 n_seg entries
+ *   inner_iters  K, iterations of Alg. 2 (>= 1)
+ *   outer_iters  L, iterations of Alg. 1 (>= 1)
+ *   n_elite_c    size of ConstraintEliteSet (Alg. 1 line 10); <= 0 means
+ *                min(B, 3 n_elite); at most 2048
+ *   n_elite      size q of EliteSet (Alg. 1 line 13), 1..n_elite_c
+ *   prec         a plan_prec value
+ *   max_obs      capacity: obstacles per scene (<= 64)
+ *   max_samples  capacity: samples per call, summed over scenes
+ *   max_scenes   capacity: scenes per call
+ *   dt           time step [s]
+ *   rho          penalty of the augmented Lagrangian, Eq. (aug_lag)
+ *   kp_lat, kv_lat, kp_lon   PD / P gains of the tracking costs c_l, c_v
+ *   gamma, eta   s_formula scaling and learning rate of the distribution update
+ *   cov_eps      jitter added to Sigma before its Cholesky factorisation
+ *   v_min, v_max, a_max, kappa_max, c_max   bounds of Table I and Eq. d_reform_1
+ *   lane_margin  distance kept from the road edges [m]
+ *   v_des_lo, v_des_hi   range of v_d in the first iteration of a fresh episode
+ */
+typedef struct {
+    int m, n_coef, n_seg, inner_iters, outer_iters, n_elite_c, n_elite;
+    int prec;
+    int max_obs, max_samples, max_scenes;
+    int reserved0;
+    double dt, rho, kp_lat, kv_lat, kp_lon, gamma, eta, cov_eps;
+    double v_min, v_max, a_max, kappa_max, c_max, lane_margin, v_des_lo, v_des_hi;
+} plan_config;
+
+/* Ego state at t0: the vector b0 of Eq. (boundary_cond_initial). */
+typedef struct { double x, y, vx, vy, ax, ay; } plan_ego;
+
+/* A neighbouring vehicle moving at constant velocity: centre
+ * (x0 + vx t, y0 + vy t), ellipse semi-axes a (along x) and b (along y) of
+ * Table I's collision constraint. */
+typedef struct { double x0, y0, vx, vy, a, b; } plan_obstacle;
+
+/* One driving scene; `obs` is host memory with n_obs entries (may be NULL
+ * when n_obs == 0).  kappa_road is the road curvature of Eq. (cent_bounds);
+ * 0 for a straight road. */
+typedef struct {
+    plan_ego ego;
+    int n_lanes;
+    double lane_width;
+    double kappa_road;
+    int n_obs;
+    const plan_obstacle* obs;
+} plan_scene;
+
+/* Sampling distribution of p carried between MPC cycles (Alg. 1 lines 2, 14).
+ * mu[0..d_p-1] and sigma (d_p x d_p, row-major, leading dimension 8) are
+ * used when fresh == 0; when fresh != 0 the first iteration draws y_d
+ * uniformly over lane centres and v_d ~ U[v_des_lo, v_des_hi] and mu, sigma
+ * start at that distribution's moments.  seed and episode_step select the
+ * Philox4x32-10 stream (key = seed, counter = (j, l | c << 16, step)). */
+typedef struct {
+    double mu[8];
+    double sigma[64];
+    uint64_t seed;
+    uint64_t episode_step;
+    int fresh;
+    int reserved0;
+} plan_cem_state;
+
+/* Best pair of the final EliteSet (the return line of Alg. 1). */
+typedef struct {
+    double p[8];         /* d_p entries                                      */
+    double xi[32];       /* 2 n_coef entries: (c_x, c_y)                      */
+    double cost;         /* c_u + r_j                                         */
+    double resid;        /* r_j, Alg. 1 line 9                                */
+    double cu;           /* c_u, upper-level driving cost                     */
+    int index;           /* sample index within the last outer iteration      */
+    int reserved0;
+} plan_result;
+
+/* ---------------------------------------------------------------- lifecycle */
+
+/* Create a context on the current CUDA device: validates `cfg`, allocates the
+ * device arena sized by max_obs / max_samples / max_scenes, and builds in
+ * float64 on the GPU the Bernstein basis (Eq. param) and the inverted KKT
+ * systems of Step 1 (Eq. over_2) and of the projection xi-step (Eq. split_xy)
+ * for every obstacle count 0..max_obs.  Synchronous.  On failure *out is NULL. */
+int plan_init(const plan_config* cfg, plan_ctx** out);
+
+/* Release the context and everything it allocated.  NULL is accepted. */
+int plan_destroy(plan_ctx* ctx);
+
+/* Static description of a status code. */
+const char* plan_status_str(int status);
+
+/* Copy the context's last error message (NUL-terminated, truncated to len). */
+int plan_last_error(const plan_ctx* ctx, char* buf, size_t len);
+
+/* ------------------------------------------------------ lower level (Alg. 1 l.6-9) */
+
+/* Solve the lower-level problem for B given behavioural inputs of one scene:
+ * Step 1 (Eq. over_3), inner_iters iterations of Alg. 2, then the residual
+ * r_j = sum max(0, g(xi*_j)) over Table I (Alg. 1 line 9) and the driving
+ * cost c_u = sum_t (|v(t)| - v_max)^2 (Sec. V-A).
+ *   p       device, B x d_p
+ *   xi      device, B x 2 n_coef, or NULL
+ *   resid   device, B
+ *   cu      device, B
+ * Errors: EINVAL (bad scene or B < 0), ECAPACITY (B > max_samples or
+ * n_obs > max_obs).  B == 0 is a no-op. */
+int plan_solve(plan_ctx* ctx, const plan_scene* scene, const double* p, int B,
+               double* xi, double* resid, double* cu, void* stream);
+
+/* As plan_solve for S scenes in one launch.  Scene s owns samples
+ * [off_s, off_s + B[s]) of the concatenated p / xi / resid / cu, with
+ * off_s = B[0] + ... + B[s-1].  `B` is host memory. */
+int plan_solve_batch(plan_ctx* ctx, const plan_scene* scenes, const int* B, int S,
+                     const double* p, double* xi, double* resid, double* cu,
+                     void* stream);
+
+/* ---------------------------------------------------------- Alg. 1 (MPC cycle) */
+
+/* Copy S scenes into the context's device-resident scene slots 0..S-1 (the
+ * per-cycle inputs of plan_step_resident).  Asynchronous on `stream`. */
+int plan_upload_scenes(plan_ctx* ctx, const plan_scene* scenes, int S, void* stream);
+
+/* Load (host -> device) or read back (device -> host, synchronous) the
+ * sampling distribution of scene slot `slot`. */
+int plan_set_state(plan_ctx* ctx, int slot, const plan_cem_state* st, void* stream);
+int plan_get_state(plan_ctx* ctx, int slot, plan_cem_state* st, void* stream);
+
+/* Run Alg. 1 (outer_iters iterations: sample, solve, select, update) for the
+ * resident scene slots 0..S-1 with B[s] samples each, entirely on the device.
+ * Afterwards each slot holds its updated distribution (fresh cleared,
+ * episode_step incremented) and its best pair.  The first call for a given
+ * (S, B[]) captures the work into a CUDA graph that later calls replay; the
+ * first call must therefore not itself be inside a stream capture.
+ * Errors: EINVAL, ECAPACITY (sum B > max_samples, S > max_scenes, or a slot
+ * that was never uploaded). */
+int plan_step_resident(plan_ctx* ctx, const int* B, int S, void* stream);
+
+/* Read back (synchronous) the best pair of slot `slot` from the last
+ * plan_step_resident. */
+int plan_get_result(plan_ctx* ctx, int slot, plan_result* out, void* stream);
+
+/* One MPC cycle through host memory: upload `scene` and `*st` to slot 0, run
+ * Alg. 1 with B samples, and write the best pair to *out and the updated
+ * distribution back to *st.  Synchronous on `stream`. */
+int plan_step(plan_ctx* ctx, const plan_scene* scene, plan_cem_state* st, int B,
+              plan_result* out, void* stream);
+
+/* ------------------------------------------------------------- single stages */
+
+/* Alg. 1 lines 10-13 for one set of B scores: ConstraintEliteSet = the n_c
+ * samples with the lowest resid, EliteSet = the q of those with the lowest
+ * resid + cu, ties to the lower index.  Writes the q EliteSet indices in
+ * ascending order of cost to `elite` (device int, q entries).  All buffers
+ * are device memory. */
+int plan_select_elites(plan_ctx* ctx, const double* resid, const double* cu, int B,
+                       int n_c, int q, int* elite, void* stream);
+
+/* Eqs. (mean_update, cov_update, s_formula) from q elites: p_elite (device,
+ * q x d_p) with costs (device, q), mu (device, d_p) and sigma (device,
+ * d_p x d_p) updated in place. */
+int plan_update_distribution(plan_ctx* ctx, const double* p_elite, const double* cost,
+                             int q, double* mu, double* sigma, void* stream);
+
+/* Alg. 1 line 4: draw B samples (device, B x d_p) for outer iteration l
+ * (1-based) from N(mu, sigma + cov_eps I) or, when fresh != 0 and l == 1,
+ * from the uniform initial distribution of `scene`'s lanes.  mu, sigma are
+ * host memory (d_p and d_p x d_p). */
+int plan_sample(plan_ctx* ctx, const plan_scene* scene, const double* mu,
+                const double* sigma, int fresh, int l, uint64_t seed,
+                uint64_t episode_step, int B, double* p, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PLAN_H_ */

@@ -1,0 +1,259 @@
+"""ctypes binding of include/plan.h: the same names, argument marshalling only.
+
+Every step of the planner runs in the CUDA library; this module only converts
+Python objects to the C structs and raw pointers the C ABI takes.  It raises
+if the library has not been built -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libplan.so")
+
+PLAN_OK = 0
+PLAN_EINVAL = -1
+PLAN_ENOMEM = -2
+PLAN_ECAPACITY = -3
+PLAN_ETIMEOUT = -4
+PLAN_ECUDA = -5
+PLAN_ESTATE = -6
+PLAN_ENONFINITE = -7
+
+PLAN_PREC_FP64 = 0
+PLAN_PREC_FP32 = 1
+
+
+class PlanConfig(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in (
+        "m", "n_coef", "n_seg", "inner_iters", "outer_iters", "n_elite_c", "n_elite", "prec",
+        "max_obs", "max_samples", "max_scenes", "reserved0")] + [(n, ctypes.c_double) for n in (
+        "dt", "rho", "kp_lat", "kv_lat", "kp_lon", "gamma", "eta", "cov_eps", "v_min", "v_max",
+        "a_max", "kappa_max", "c_max", "lane_margin", "v_des_lo", "v_des_hi")]
+
+
+class PlanEgo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("x", "y", "vx", "vy", "ax", "ay")]
+
+
+class PlanObstacle(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("x0", "y0", "vx", "vy", "a", "b")]
+
+
+class PlanScene(ctypes.Structure):
+    _fields_ = [("ego", PlanEgo), ("n_lanes", ctypes.c_int), ("lane_width", ctypes.c_double),
+                ("kappa_road", ctypes.c_double), ("n_obs", ctypes.c_int),
+                ("obs", ctypes.POINTER(PlanObstacle))]
+
+
+class PlanCemState(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_double * 8), ("sigma", ctypes.c_double * 64),
+                ("seed", ctypes.c_uint64), ("episode_step", ctypes.c_uint64),
+                ("fresh", ctypes.c_int), ("reserved0", ctypes.c_int)]
+
+
+class PlanResult(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_double * 8), ("xi", ctypes.c_double * 32),
+                ("cost", ctypes.c_double), ("resid", ctypes.c_double), ("cu", ctypes.c_double),
+                ("index", ctypes.c_int), ("reserved0", ctypes.c_int)]
+
+
+EXPORTS = ("plan_init", "plan_destroy", "plan_status_str", "plan_last_error", "plan_solve",
+           "plan_solve_batch", "plan_upload_scenes", "plan_set_state", "plan_get_state",
+           "plan_step_resident", "plan_get_result", "plan_step", "plan_select_elites",
+           "plan_update_distribution", "plan_sample")
+
+_lib = None
+
+
+class PlanError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_str(status)} ({status}): {msg}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libplan.so (built by build.py); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"planner CUDA library not built: {path} is missing "
+                           "(run paper_2212_02224_gb300/build.py)")
+    lib = ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL)
+    P, I, D, V, U64 = ctypes.POINTER, ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_uint64
+    sig = {
+        "plan_init": (I, [P(PlanConfig), P(V)]),
+        "plan_destroy": (I, [V]),
+        "plan_status_str": (ctypes.c_char_p, [I]),
+        "plan_last_error": (I, [V, ctypes.c_char_p, ctypes.c_size_t]),
+        "plan_solve": (I, [V, P(PlanScene), V, I, V, V, V, V]),
+        "plan_solve_batch": (I, [V, P(PlanScene), P(I), I, V, V, V, V, V]),
+        "plan_upload_scenes": (I, [V, P(PlanScene), I, V]),
+        "plan_set_state": (I, [V, I, P(PlanCemState), V]),
+        "plan_get_state": (I, [V, I, P(PlanCemState), V]),
+        "plan_step_resident": (I, [V, P(I), I, V]),
+        "plan_get_result": (I, [V, I, P(PlanResult), V]),
+        "plan_step": (I, [V, P(PlanScene), P(PlanCemState), I, P(PlanResult), V]),
+        "plan_select_elites": (I, [V, V, V, I, I, I, V, V]),
+        "plan_update_distribution": (I, [V, V, V, I, V, V, V]),
+        "plan_sample": (I, [V, P(PlanScene), V, V, I, I, U64, U64, I, V, V]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_str(status: int) -> str:
+    try:
+        return load().plan_status_str(status).decode()
+    except RuntimeError:
+        return str(status)
+
+
+def last_error(ctx) -> str:
+    buf = ctypes.create_string_buffer(512)
+    load().plan_last_error(ctx, buf, 512)
+    return buf.value.decode()
+
+
+def check(status: int, ctx=None) -> None:
+    if status != PLAN_OK:
+        raise PlanError(status, last_error(ctx))
+
+
+# ----------------------------------------------------------------------------- marshalling
+
+def make_config(prm, prec: int, max_obs: int, max_samples: int, max_scenes: int = 1) -> PlanConfig:
+    """PlanConfig from any object with the planner's parameter attributes."""
+    c = PlanConfig()
+    for name in ("m", "n_coef", "n_seg", "inner_iters", "outer_iters", "n_elite_c", "n_elite"):
+        setattr(c, name, int(getattr(prm, name)))
+    for name in ("dt", "rho", "kp_lat", "kv_lat", "kp_lon", "gamma", "eta", "cov_eps", "v_min",
+                 "v_max", "a_max", "kappa_max", "c_max", "lane_margin", "v_des_lo", "v_des_hi"):
+        setattr(c, name, float(getattr(prm, name)))
+    c.prec = int(prec)
+    c.max_obs, c.max_samples, c.max_scenes = int(max_obs), int(max_samples), int(max_scenes)
+    return c
+
+
+def make_scenes(scenes):
+    """(PlanScene array, keep-alive list) from objects with ego / n_lanes /
+    lane_width / kappa_road / obstacles (N x 6 rows x0, y0, vx, vy, a, b)."""
+    arr = (PlanScene * len(scenes))()
+    keep = []
+    for i, sc in enumerate(scenes):
+        e = [float(v) for v in sc.ego]
+        arr[i].ego = PlanEgo(*e)
+        arr[i].n_lanes = int(sc.n_lanes)
+        arr[i].lane_width = float(sc.lane_width)
+        arr[i].kappa_road = float(sc.kappa_road)
+        ob = list(sc.obstacles)
+        arr[i].n_obs = len(ob)
+        if ob:
+            oa = (PlanObstacle * len(ob))(*[PlanObstacle(*[float(v) for v in row]) for row in ob])
+            keep.append(oa)
+            arr[i].obs = ctypes.cast(oa, ctypes.POINTER(PlanObstacle))
+        else:
+            arr[i].obs = None
+    keep.append(arr)
+    return arr, keep
+
+
+def make_state(d_p: int, mu=None, sigma=None, seed: int = 0, step: int = 0, fresh=None) -> PlanCemState:
+    st = PlanCemState()
+    st.seed, st.episode_step = int(seed), int(step)
+    st.fresh = int(mu is None if fresh is None else fresh)
+    if mu is not None:
+        for a in range(d_p):
+            st.mu[a] = float(mu[a])
+            for b in range(d_p):
+                st.sigma[a * 8 + b] = float(sigma[a][b])
+    return st
+
+
+def state_arrays(st: PlanCemState, d_p: int):
+    mu = [st.mu[a] for a in range(d_p)]
+    sigma = [[st.sigma[a * 8 + b] for b in range(d_p)] for a in range(d_p)]
+    return mu, sigma
+
+
+# ----------------------------------------------------------------------------- entry points
+
+def plan_init(cfg: PlanConfig):
+    ctx = ctypes.c_void_p()
+    check(load().plan_init(ctypes.byref(cfg), ctypes.byref(ctx)), None)
+    return ctx
+
+
+def plan_destroy(ctx) -> None:
+    check(load().plan_destroy(ctx), None)
+
+
+def plan_solve(ctx, scene, p_ptr: int, B: int, xi_ptr, r_ptr: int, cu_ptr: int, stream: int = 0):
+    arr, keep = make_scenes([scene])
+    check(load().plan_solve(ctx, arr, p_ptr, B, xi_ptr, r_ptr, cu_ptr, stream), ctx)
+
+
+def plan_solve_batch(ctx, scenes, Bs, p_ptr: int, xi_ptr, r_ptr: int, cu_ptr: int, stream: int = 0):
+    arr, keep = make_scenes(scenes)
+    b = (ctypes.c_int * len(Bs))(*[int(x) for x in Bs])
+    check(load().plan_solve_batch(ctx, arr, b, len(Bs), p_ptr, xi_ptr, r_ptr, cu_ptr, stream), ctx)
+
+
+def plan_upload_scenes(ctx, scenes, stream: int = 0):
+    arr, keep = make_scenes(scenes)
+    check(load().plan_upload_scenes(ctx, arr, len(scenes), stream), ctx)
+
+
+def plan_set_state(ctx, slot: int, st: PlanCemState, stream: int = 0):
+    check(load().plan_set_state(ctx, slot, ctypes.byref(st), stream), ctx)
+
+
+def plan_get_state(ctx, slot: int, stream: int = 0) -> PlanCemState:
+    st = PlanCemState()
+    check(load().plan_get_state(ctx, slot, ctypes.byref(st), stream), ctx)
+    return st
+
+
+def plan_step_resident(ctx, Bs, stream: int = 0):
+    b = (ctypes.c_int * len(Bs))(*[int(x) for x in Bs])
+    check(load().plan_step_resident(ctx, b, len(Bs), stream), ctx)
+
+
+def plan_get_result(ctx, slot: int, stream: int = 0) -> PlanResult:
+    out = PlanResult()
+    check(load().plan_get_result(ctx, slot, ctypes.byref(out), stream), ctx)
+    return out
+
+
+def plan_step(ctx, scene, st: PlanCemState, B: int, stream: int = 0) -> PlanResult:
+    arr, keep = make_scenes([scene])
+    out = PlanResult()
+    check(load().plan_step(ctx, arr, ctypes.byref(st), B, ctypes.byref(out), stream), ctx)
+    return out
+
+
+def plan_select_elites(ctx, r_ptr: int, cu_ptr: int, B: int, n_c: int, q: int, elite_ptr: int,
+                       stream: int = 0):
+    check(load().plan_select_elites(ctx, r_ptr, cu_ptr, B, n_c, q, elite_ptr, stream), ctx)
+
+
+def plan_update_distribution(ctx, p_ptr: int, cost_ptr: int, q: int, mu_ptr: int, sigma_ptr: int,
+                             stream: int = 0):
+    check(load().plan_update_distribution(ctx, p_ptr, cost_ptr, q, mu_ptr, sigma_ptr, stream), ctx)
+
+
+def plan_sample(ctx, scene, mu, sigma, fresh: int, l: int, seed: int, step: int, B: int, p_ptr: int,
+                stream: int = 0):
+    arr, keep = make_scenes([scene])
+    d = len(mu) if mu is not None else 0
+    mu_c = (ctypes.c_double * max(d, 1))(*([float(v) for v in mu] if mu is not None else [0.0]))
+    sg_c = (ctypes.c_double * max(d * d, 1))(
+        *([float(sigma[a][b]) for a in range(d) for b in range(d)] if sigma is not None else [0.0]))
+    check(load().plan_sample(ctx, arr, mu_c, sg_c, int(fresh), int(l), int(seed), int(step), int(B),
+                             p_ptr, stream), ctx)

@@ -1,0 +1,114 @@
+// Internal declarations of the planner library (device structs, launchers).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace plan {
+
+constexpr int kMaxCoef = 16;     // coefficients per axis
+constexpr int kMaxDp = 8;        // entries of p
+constexpr int kMaxObs = 64;      // obstacles per scene
+constexpr int kMaxM = 256;       // timesteps
+constexpr int kMaxEliteC = 2048; // ConstraintEliteSet size
+
+// Geometry of one scene as the kernels see it.
+struct DevScene {
+  double ego[6];        // b0: x, y, vx, vy, ax, ay
+  double y_lb, y_ub;    // lane-boundary rows of Table I
+  double kappa_road;    // road curvature (centripetal bound)
+  double lane_width;
+  int n_lanes, n_obs;
+  int obs_off;          // first obstacle in the obstacle array (6 doubles each)
+  int pad;
+};
+
+// Per-scene state of the outer loop (Alg. 1), device resident.
+struct DevCem {
+  double mu[kMaxDp];
+  double sigma[kMaxDp * kMaxDp];   // leading dimension kMaxDp
+  double chol[kMaxDp * kMaxDp];    // lower Cholesky factor of sigma + eps I
+  double best_p[kMaxDp];
+  double best_xi[2 * kMaxCoef];
+  double best_cost, best_r, best_cu;
+  unsigned long long seed, step;
+  int fresh, best_index;
+  int pad[2];
+};
+
+// Numeric parameters (plan_config) for the kernels.
+struct Params {
+  int m, n, n_seg, K;
+  int L, n_c, q, d_p;
+  int max_obs, pad;
+  double dt, rho, kp_lat, kv_lat, kp_lon, gamma, eta, cov_eps;
+  double v_min, v_max, a_max, kappa_max, c_max, lane_margin, v_des_lo, v_des_hi;
+};
+
+// Constants built in float64 on the device by build_constants().
+//   basis64 [3][m][n]  W, Wd, Wdd row-major (FP64 path)
+//   basis32 [3][n][m]  the same, coefficient-major so that t is contiguous
+//   s1_*    [2][n][n_seg + 3]  Step-1 maps: xi_bar_axis = Gs p_axis + Hs b_axis
+//   pj_*    [N + 1][2][n][2n + 3]  per obstacle count N and axis, row k:
+//           M[k][:], MP[k][:], C[k][:] with xi = M r + C b (KKT inverse of
+//           the xi-step) and MP = rho M P, P = F^T F + G^T G of that axis.
+struct Consts {
+  double* basis64;
+  float* basis32;
+  double* s1_64;
+  float* s1_32;
+  double* pj64;
+  float* pj32;
+  int m, n, n_seg, max_obs;
+};
+
+// Layout of one call: scene s owns samples [off, off + B).
+struct Layout {
+  int B, off;
+};
+
+// A tile of the fused kernel: `count` samples of `scene` starting at `first`
+// (scene-relative).
+struct Tile {
+  int scene, first, count, pad;
+};
+
+// Launchers (return the cudaError_t of the launch).
+cudaError_t build_constants(const Consts& c, const Params& p, cudaStream_t s);
+
+bool fused_supported(int n, int m);
+cudaError_t launch_fused_f32(const DevScene* scenes, const Layout* layout, const double* obs,
+                             const Tile* tiles, int n_tiles, int warps, const double* p,
+                             const Consts& c, const Params& prm, double* xi, double* r,
+                             double* cu, cudaStream_t s);
+
+struct Plain64Work {   // HBM intermediates of the FP64 path
+  double* xibarp;  // [B][32] M xi_bar + C b
+  double* xi;      // [B][32]
+  double* lam;     // [B][32]
+  double* w;       // [B][32]
+  double* state;   // [B][6][m]
+  double* eps;     // [B][7][m]
+  double* da;      // [B][m]
+};
+
+cudaError_t launch_plain64(const DevScene* scenes, const Layout* layout, const int* sample_scene,
+                           const double* obs, int total_B, const double* p, const Consts& c,
+                           const Params& prm, const Plain64Work& w, double* xi_out, double* r,
+                           double* cu, cudaStream_t s);
+
+cudaError_t launch_sample(const DevScene* scenes, const Layout* layout, const DevCem* cem, int S,
+                          int max_B, int l, const Params& prm, double* p, cudaStream_t s);
+
+cudaError_t launch_select_update(const Layout* layout, DevCem* cem, int S, int l,
+                                 const Params& prm, const double* p, const double* xi,
+                                 const double* r, const double* cu, int* elite_out,
+                                 cudaStream_t s);
+
+cudaError_t launch_select_only(const double* r, const double* cu, int B, int n_c, int q,
+                               int* elite, cudaStream_t s);
+cudaError_t launch_update_only(const double* p_elite, const double* cost, int q, int d_p,
+                               double gamma, double eta, double* mu, double* sigma,
+                               cudaStream_t s);
+
+}  // namespace plan

@@ -1,0 +1,709 @@
+// C ABI of the planner: context, device arena, staging, launch sequences and
+// CUDA-graph capture of whole Alg. 1 runs.  See include/plan.h.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/plan.h"
+#include "internal.cuh"
+
+namespace plan {
+void cem_setup();
+void fused_setup();
+}  // namespace plan
+
+using namespace plan;
+
+namespace {
+
+// Device buffers describing one set of scenes and their sample layout.
+struct SceneSet {
+  DevScene* scenes = nullptr;
+  double* obs = nullptr;
+  Layout* layout = nullptr;
+  Tile* tiles = nullptr;
+  int* sample_scene = nullptr;
+};
+
+struct GraphEntry {
+  std::vector<int> B;
+  SceneSet set;            // own layout / tiles / sample_scene (scenes+obs shared)
+  cudaGraphExec_t exec = nullptr;
+  int total_B = 0, max_B = 0;
+};
+
+}  // namespace
+
+struct plan_ctx {
+  plan_config cfg{};
+  Params prm{};
+  Consts c{};
+  int device = 0;
+  int fused_warps = 0;     // 0 = automatic
+  cudaStream_t internal = nullptr;
+  cudaStream_t capture = nullptr;
+
+  // arena
+  std::vector<void*> allocs;
+  SceneSet tr;             // transient scenes (plan_solve)
+  SceneSet res;            // resident scene slots (plan_step_resident)
+  DevCem* cem = nullptr;   // [max_scenes]
+  double* p = nullptr;     // [max_samples][d_p]
+  double* xi = nullptr;    // [max_samples][2n]
+  double* r = nullptr;
+  double* cu = nullptr;
+  int* elite = nullptr;    // [max_scenes][q]
+  Plain64Work pw{};
+  DevCem* cem_tmp = nullptr;   // single-stage sampling
+  Layout* layout_tmp = nullptr;
+
+  // pinned staging
+  unsigned char* stage = nullptr;
+  size_t stage_bytes = 0;
+  cudaEvent_t stage_done = nullptr;
+  bool stage_pending = false;
+
+  // resident bookkeeping
+  int n_uploaded = 0;
+  std::vector<DevScene> res_host;    // host mirror of resident geometry
+  std::vector<GraphEntry> graphs;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_init_err;   // failures of plan_init (no context yet)
+
+int fail(plan_ctx* ctx, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  else g_init_err = buf;
+  return code;
+}
+
+#define CU(ctx, call)                                                                    \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail((ctx), PLAN_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                  __FILE__, __LINE__);                                                   \
+  } while (0)
+
+template <class T>
+int dalloc(plan_ctx* ctx, T** ptr, size_t count) {
+  *ptr = nullptr;
+  if (count == 0) count = 1;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, PLAN_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+                cudaGetErrorString(e));
+  }
+  ctx->allocs.push_back(p);
+  *ptr = static_cast<T*>(p);
+  return PLAN_OK;
+}
+
+#define TRY(x)                    \
+  do {                            \
+    int s_ = (x);                 \
+    if (s_ != PLAN_OK) return s_; \
+  } while (0)
+
+int alloc_set(plan_ctx* ctx, SceneSet& s, bool with_scenes) {
+  const plan_config& c = ctx->cfg;
+  if (with_scenes) {
+    TRY(dalloc(ctx, &s.scenes, c.max_scenes));
+    TRY(dalloc(ctx, &s.obs, size_t(c.max_scenes) * (c.max_obs > 0 ? c.max_obs : 1) * 6));
+  }
+  TRY(dalloc(ctx, &s.layout, c.max_scenes));
+  TRY(dalloc(ctx, &s.tiles, size_t(c.max_samples) + c.max_scenes));
+  TRY(dalloc(ctx, &s.sample_scene, c.max_samples));
+  return PLAN_OK;
+}
+
+int validate_config(const plan_config* cfg, std::string* why) {
+  char b[256];
+  auto bad = [&](const char* m) { *why = m; return PLAN_EINVAL; };
+  if (!cfg) return bad("cfg is NULL");
+  if (cfg->m < 8 || cfg->m > kMaxM) return bad("m must be in [8, 256]");
+  if (cfg->n_coef < 4 || cfg->n_coef > kMaxCoef) return bad("n_coef must be in [4, 16]");
+  if (cfg->n_seg < 1 || cfg->n_seg > 4 || cfg->n_seg > cfg->m) return bad("n_seg must be in [1, 4]");
+  if (cfg->inner_iters < 1) return bad("inner_iters must be >= 1");
+  if (cfg->outer_iters < 1 || cfg->outer_iters > 65535) return bad("outer_iters must be in [1, 65535]");
+  if (cfg->n_elite < 1) return bad("n_elite must be >= 1");
+  if (cfg->n_elite_c > kMaxEliteC || (cfg->n_elite_c <= 0 && 3 * cfg->n_elite > kMaxEliteC))
+    return bad("n_elite_c must be <= 2048");
+  if (cfg->n_elite_c > 0 && cfg->n_elite > cfg->n_elite_c) return bad("n_elite must be <= n_elite_c");
+  if (cfg->prec != PLAN_PREC_FP64 && cfg->prec != PLAN_PREC_FP32) return bad("unknown prec");
+  if (cfg->prec == PLAN_PREC_FP32 && !fused_supported(cfg->n_coef, cfg->m))
+    return bad("the FP32 fused kernel supports n_coef in {8, 11, 16}");
+  if (cfg->max_obs < 0 || cfg->max_obs > kMaxObs) return bad("max_obs must be in [0, 64]");
+  if (cfg->max_samples < 1 || cfg->max_samples > (1 << 24)) return bad("max_samples must be in [1, 2^24]");
+  if (cfg->max_scenes < 1 || cfg->max_scenes > 65535) return bad("max_scenes must be in [1, 65535]");
+  if (!(cfg->dt > 0) || !(cfg->rho > 0) || !(cfg->gamma > 0)) return bad("dt, rho, gamma must be > 0");
+  if (!(cfg->eta > 0 && cfg->eta <= 1)) return bad("eta must be in (0, 1]");
+  if (!(cfg->cov_eps >= 0)) return bad("cov_eps must be >= 0");
+  if (!(cfg->v_min >= 0) || !(cfg->v_max > cfg->v_min)) return bad("need 0 <= v_min < v_max");
+  if (!(cfg->a_max > 0) || !(cfg->kappa_max > 0) || !(cfg->c_max > 0))
+    return bad("a_max, kappa_max, c_max must be > 0");
+  if (!(cfg->lane_margin >= 0)) return bad("lane_margin must be >= 0");
+  if (!(cfg->v_des_hi >= cfg->v_des_lo)) return bad("v_des_hi must be >= v_des_lo");
+  (void)b;
+  return PLAN_OK;
+}
+
+int check_scene(plan_ctx* ctx, const plan_scene* s, int idx) {
+  if (!s) return fail(ctx, PLAN_EINVAL, "scene %d is NULL", idx);
+  if (s->n_lanes < 1) return fail(ctx, PLAN_EINVAL, "scene %d: n_lanes must be >= 1", idx);
+  if (!(s->lane_width > 0)) return fail(ctx, PLAN_EINVAL, "scene %d: lane_width must be > 0", idx);
+  if (!(s->n_lanes * s->lane_width - 2 * ctx->cfg.lane_margin > 0))
+    return fail(ctx, PLAN_EINVAL, "scene %d: road narrower than twice lane_margin", idx);
+  if (s->n_obs < 0) return fail(ctx, PLAN_EINVAL, "scene %d: n_obs < 0", idx);
+  if (s->n_obs > ctx->cfg.max_obs)
+    return fail(ctx, PLAN_ECAPACITY, "scene %d: n_obs %d exceeds max_obs %d", idx, s->n_obs,
+                ctx->cfg.max_obs);
+  if (s->n_obs > 0 && !s->obs) return fail(ctx, PLAN_EINVAL, "scene %d: obs is NULL", idx);
+  const double* e = &s->ego.x;
+  for (int i = 0; i < 6; ++i)
+    if (!std::isfinite(e[i])) return fail(ctx, PLAN_EINVAL, "scene %d: ego state not finite", idx);
+  if (!std::isfinite(s->kappa_road)) return fail(ctx, PLAN_EINVAL, "scene %d: kappa_road", idx);
+  for (int i = 0; i < s->n_obs; ++i) {
+    const plan_obstacle& o = s->obs[i];
+    if (!(o.a > 0) || !(o.b > 0) || !std::isfinite(o.x0) || !std::isfinite(o.y0) ||
+        !std::isfinite(o.vx) || !std::isfinite(o.vy))
+      return fail(ctx, PLAN_EINVAL, "scene %d: obstacle %d invalid (axes must be > 0)", idx, i);
+  }
+  return PLAN_OK;
+}
+
+DevScene to_dev(const plan_ctx* ctx, const plan_scene& s, int obs_off) {
+  DevScene d{};
+  d.ego[0] = s.ego.x; d.ego[1] = s.ego.y; d.ego[2] = s.ego.vx;
+  d.ego[3] = s.ego.vy; d.ego[4] = s.ego.ax; d.ego[5] = s.ego.ay;
+  d.y_lb = ctx->cfg.lane_margin;
+  d.y_ub = s.n_lanes * s.lane_width - ctx->cfg.lane_margin;
+  d.kappa_road = s.kappa_road;
+  d.lane_width = s.lane_width;
+  d.n_lanes = s.n_lanes;
+  d.n_obs = s.n_obs;
+  d.obs_off = obs_off;
+  return d;
+}
+
+// Make the pinned staging buffer reusable (its previous copy has completed)
+// and at least `bytes` large.
+int stage_acquire(plan_ctx* ctx, size_t bytes) {
+  if (ctx->stage_pending) {
+    CU(ctx, cudaEventSynchronize(ctx->stage_done));
+    ctx->stage_pending = false;
+  }
+  if (bytes > ctx->stage_bytes) {
+    if (ctx->stage) cudaFreeHost(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_bytes = 0;
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, bytes, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, PLAN_ENOMEM, "pinned staging allocation of %zu bytes failed", bytes);
+    }
+    ctx->stage = static_cast<unsigned char*>(p);
+    ctx->stage_bytes = bytes;
+  }
+  return PLAN_OK;
+}
+
+int stage_release(plan_ctx* ctx, cudaStream_t s) {
+  CU(ctx, cudaEventRecord(ctx->stage_done, s));
+  ctx->stage_pending = true;
+  return PLAN_OK;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Tiles of `warps` samples per CTA, never crossing a scene.
+void make_tiles(const std::vector<int>& B, int warps, std::vector<Tile>* tiles,
+                std::vector<Layout>* layout, std::vector<int>* sample_scene) {
+  int off = 0;
+  for (size_t s = 0; s < B.size(); ++s) {
+    layout->push_back(Layout{B[s], off});
+    for (int f = 0; f < B[s]; f += warps)
+      tiles->push_back(Tile{int(s), f, std::min(warps, B[s] - f), 0});
+    for (int j = 0; j < B[s]; ++j) sample_scene->push_back(int(s));
+    off += B[s];
+  }
+}
+
+int pick_warps(const plan_ctx* ctx, int total_B) {
+  if (ctx->fused_warps > 0) return ctx->fused_warps;
+  // few samples: small CTAs so every SM gets work; many: 4 warps per CTA
+  return total_B <= 8192 ? 1 : 4;
+}
+
+// Upload scenes (geometry + obstacles) and the layout of B into `set`.
+int upload(plan_ctx* ctx, SceneSet& set, const plan_scene* scenes, int S, const std::vector<int>* B,
+           cudaStream_t s, std::vector<DevScene>* mirror) {
+  std::vector<DevScene> ds;
+  std::vector<double> ob;
+  if (scenes) {
+    for (int i = 0; i < S; ++i) {
+      ds.push_back(to_dev(ctx, scenes[i], int(ob.size() / 6)));
+      for (int k = 0; k < scenes[i].n_obs; ++k) {
+        const plan_obstacle& o = scenes[i].obs[k];
+        ob.insert(ob.end(), {o.x0, o.y0, o.vx, o.vy, o.a, o.b});
+      }
+    }
+  }
+  std::vector<Tile> tiles;
+  std::vector<Layout> layout;
+  std::vector<int> ss;
+  int total = 0;
+  if (B) {
+    for (int b : *B) total += b;
+    make_tiles(*B, pick_warps(ctx, total), &tiles, &layout, &ss);
+  }
+  const size_t n1 = ds.size() * sizeof(DevScene), n2 = ob.size() * sizeof(double);
+  const size_t n3 = layout.size() * sizeof(Layout), n4 = tiles.size() * sizeof(Tile);
+  const size_t n5 = ss.size() * sizeof(int);
+  const size_t o2 = align_up(n1), o3 = o2 + align_up(n2), o4 = o3 + align_up(n3),
+               o5 = o4 + align_up(n4), tot = o5 + align_up(n5);
+  TRY(stage_acquire(ctx, tot));
+  std::memcpy(ctx->stage, ds.data(), n1);
+  std::memcpy(ctx->stage + o2, ob.data(), n2);
+  std::memcpy(ctx->stage + o3, layout.data(), n3);
+  std::memcpy(ctx->stage + o4, tiles.data(), n4);
+  std::memcpy(ctx->stage + o5, ss.data(), n5);
+  if (n1) CU(ctx, cudaMemcpyAsync(set.scenes, ctx->stage, n1, cudaMemcpyHostToDevice, s));
+  if (n2) CU(ctx, cudaMemcpyAsync(set.obs, ctx->stage + o2, n2, cudaMemcpyHostToDevice, s));
+  if (n3) CU(ctx, cudaMemcpyAsync(set.layout, ctx->stage + o3, n3, cudaMemcpyHostToDevice, s));
+  if (n4) CU(ctx, cudaMemcpyAsync(set.tiles, ctx->stage + o4, n4, cudaMemcpyHostToDevice, s));
+  if (n5) CU(ctx, cudaMemcpyAsync(set.sample_scene, ctx->stage + o5, n5, cudaMemcpyHostToDevice, s));
+  TRY(stage_release(ctx, s));
+  if (mirror) *mirror = ds;
+  return PLAN_OK;
+}
+
+// Lower-level solve of all samples described by `set` (Alg. 1 lines 6-9).
+cudaError_t run_solve(plan_ctx* ctx, const SceneSet& set, const SceneSet& lay, int n_tiles,
+                      int warps, int total_B, const double* p, double* xi, double* r, double* cu,
+                      cudaStream_t s) {
+  if (ctx->cfg.prec == PLAN_PREC_FP32)
+    return launch_fused_f32(set.scenes, lay.layout, set.obs, lay.tiles, n_tiles, warps, p, ctx->c,
+                            ctx->prm, xi, r, cu, s);
+  return launch_plain64(set.scenes, lay.layout, lay.sample_scene, set.obs, total_B, p, ctx->c,
+                        ctx->prm, ctx->pw, xi, r, cu, s);
+}
+
+int n_tiles_of(const std::vector<int>& B, int warps) {
+  int n = 0;
+  for (int b : B) n += (b + warps - 1) / warps;
+  return n;
+}
+
+void chol_host(const double* A, double eps, int d, double* L, bool* ok) {
+  *ok = true;
+  for (int i = 0; i < kMaxDp * kMaxDp; ++i) L[i] = 0.0;
+  for (int j = 0; j < d; ++j) {
+    double s = A[j * kMaxDp + j] + eps;
+    for (int k = 0; k < j; ++k) s -= L[j * kMaxDp + k] * L[j * kMaxDp + k];
+    if (!(s > 0)) { *ok = false; return; }
+    const double dj = std::sqrt(s);
+    L[j * kMaxDp + j] = dj;
+    for (int i = j + 1; i < d; ++i) {
+      double v = A[i * kMaxDp + j];
+      for (int k = 0; k < j; ++k) v -= L[i * kMaxDp + k] * L[j * kMaxDp + k];
+      L[i * kMaxDp + j] = v / dj;
+    }
+  }
+}
+
+// DevCem from a host state; the initial moments of a fresh episode follow
+// from the uniform first-iteration distribution of the scene's lanes.
+int make_cem(plan_ctx* ctx, const plan_cem_state* st, int n_lanes, double lane_width, DevCem* out) {
+  const int ns = ctx->cfg.n_seg, d = 2 * ns;
+  DevCem c{};
+  c.seed = st->seed;
+  c.step = st->episode_step;
+  c.fresh = st->fresh ? 1 : 0;
+  if (c.fresh) {
+    const double L = n_lanes, w = lane_width;
+    const double lo = ctx->cfg.v_des_lo, hi = ctx->cfg.v_des_hi;
+    for (int e = 0; e < ns; ++e) {
+      c.mu[e] = L * w / 2.0;
+      c.mu[ns + e] = 0.5 * (lo + hi);
+      c.sigma[e * kMaxDp + e] = w * w * (L * L - 1.0) / 12.0;
+      c.sigma[(ns + e) * kMaxDp + ns + e] = (hi - lo) * (hi - lo) / 12.0;
+    }
+  } else {
+    for (int a = 0; a < d; ++a) {
+      c.mu[a] = st->mu[a];
+      for (int b = 0; b < d; ++b) c.sigma[a * kMaxDp + b] = st->sigma[a * 8 + b];
+    }
+  }
+  for (int a = 0; a < d; ++a)
+    if (!std::isfinite(c.mu[a])) return fail(ctx, PLAN_EINVAL, "mu not finite");
+  bool ok = true;
+  chol_host(c.sigma, ctx->cfg.cov_eps, d, c.chol, &ok);
+  if (!ok && !c.fresh) return fail(ctx, PLAN_EINVAL, "sigma + cov_eps I is not positive definite");
+  *out = c;
+  return PLAN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* plan_status_str(int status) {
+  switch (status) {
+    case PLAN_OK: return "ok";
+    case PLAN_EINVAL: return "invalid argument";
+    case PLAN_ENOMEM: return "out of memory";
+    case PLAN_ECAPACITY: return "capacity exceeded";
+    case PLAN_ETIMEOUT: return "timed out";
+    case PLAN_ECUDA: return "CUDA error";
+    case PLAN_ESTATE: return "invalid state";
+    case PLAN_ENONFINITE: return "non-finite result";
+    default: return "unknown status";
+  }
+}
+
+int plan_last_error(const plan_ctx* ctx, char* buf, size_t len) {
+  if (!buf || len == 0) return PLAN_EINVAL;
+  std::snprintf(buf, len, "%s", ctx ? ctx->err.c_str() : g_init_err.c_str());
+  return PLAN_OK;
+}
+
+int plan_destroy(plan_ctx* ctx) {
+  if (!ctx) return PLAN_OK;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaSetDevice(ctx->device);
+  if (ctx->internal) cudaStreamSynchronize(ctx->internal);
+  for (auto& g : ctx->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (void* p : ctx->allocs) cudaFree(p);
+  if (ctx->stage) cudaFreeHost(ctx->stage);
+  if (ctx->stage_done) cudaEventDestroy(ctx->stage_done);
+  if (ctx->internal) cudaStreamDestroy(ctx->internal);
+  if (ctx->capture) cudaStreamDestroy(ctx->capture);
+  cudaSetDevice(dev);
+  delete ctx;
+  return PLAN_OK;
+}
+
+int plan_init(const plan_config* cfg, plan_ctx** out) {
+  if (!out) return PLAN_EINVAL;
+  *out = nullptr;
+  std::string why;
+  if (validate_config(cfg, &why) != PLAN_OK) return fail(nullptr, PLAN_EINVAL, "%s", why.c_str());
+  plan_ctx* ctx = new (std::nothrow) plan_ctx();
+  if (!ctx) return PLAN_ENOMEM;
+  ctx->cfg = *cfg;
+  const plan_config& c = *cfg;
+  Params& p = ctx->prm;
+  p.m = c.m; p.n = c.n_coef; p.n_seg = c.n_seg; p.K = c.inner_iters; p.L = c.outer_iters;
+  p.q = c.n_elite; p.n_c = c.n_elite_c > 0 ? c.n_elite_c : 3 * c.n_elite;
+  p.d_p = 2 * c.n_seg; p.max_obs = c.max_obs;
+  p.dt = c.dt; p.rho = c.rho; p.kp_lat = c.kp_lat; p.kv_lat = c.kv_lat; p.kp_lon = c.kp_lon;
+  p.gamma = c.gamma; p.eta = c.eta; p.cov_eps = c.cov_eps; p.v_min = c.v_min; p.v_max = c.v_max;
+  p.a_max = c.a_max; p.kappa_max = c.kappa_max; p.c_max = c.c_max; p.lane_margin = c.lane_margin;
+  p.v_des_lo = c.v_des_lo; p.v_des_hi = c.v_des_hi;
+
+  auto bail = [&](int code) {
+    g_init_err = ctx->err.empty() ? "CUDA initialisation failed" : ctx->err;
+    plan_destroy(ctx);
+    return code;
+  };
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) { cudaGetLastError(); return bail(PLAN_ECUDA); }
+  if (cudaStreamCreateWithFlags(&ctx->internal, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->stage_done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(PLAN_ECUDA);
+  }
+  const int m = c.m, n = c.n_coef, ns = c.n_seg, d = 2 * ns;
+  const size_t B = c.max_samples;
+  Consts& k = ctx->c;
+  k.m = m; k.n = n; k.n_seg = ns; k.max_obs = c.max_obs;
+  int st = PLAN_OK;
+  auto A = [&](int s) { if (st == PLAN_OK) st = s; };
+  A(dalloc(ctx, &k.basis64, size_t(3) * m * n));
+  A(dalloc(ctx, &k.basis32, size_t(3) * m * n));
+  A(dalloc(ctx, &k.s1_64, size_t(2) * n * (ns + 3)));
+  A(dalloc(ctx, &k.s1_32, size_t(2) * n * (ns + 3)));
+  A(dalloc(ctx, &k.pj64, size_t(c.max_obs + 1) * 2 * n * (2 * n + 3)));
+  A(dalloc(ctx, &k.pj32, size_t(c.max_obs + 1) * 2 * n * (2 * n + 3)));
+  if (st == PLAN_OK) A(alloc_set(ctx, ctx->tr, true));
+  if (st == PLAN_OK) A(alloc_set(ctx, ctx->res, true));
+  A(dalloc(ctx, &ctx->cem, c.max_scenes));
+  A(dalloc(ctx, &ctx->cem_tmp, 1));
+  A(dalloc(ctx, &ctx->layout_tmp, 1));
+  A(dalloc(ctx, &ctx->p, B * d));
+  A(dalloc(ctx, &ctx->xi, B * 2 * n));
+  A(dalloc(ctx, &ctx->r, B));
+  A(dalloc(ctx, &ctx->cu, B));
+  A(dalloc(ctx, &ctx->elite, size_t(c.max_scenes) * c.n_elite));
+  if (c.prec == PLAN_PREC_FP64) {
+    A(dalloc(ctx, &ctx->pw.xibarp, B * 32));
+    A(dalloc(ctx, &ctx->pw.xi, B * 32));
+    A(dalloc(ctx, &ctx->pw.lam, B * 32));
+    A(dalloc(ctx, &ctx->pw.w, B * 32));
+    A(dalloc(ctx, &ctx->pw.state, B * 6 * m));
+    A(dalloc(ctx, &ctx->pw.eps, B * 7 * m));
+    A(dalloc(ctx, &ctx->pw.da, B * m));
+  }
+  if (st != PLAN_OK) return bail(st);
+  cem_setup();
+  fused_setup();
+  if (build_constants(k, p, ctx->internal) != cudaSuccess ||
+      cudaMemsetAsync(ctx->cem, 0, sizeof(DevCem) * c.max_scenes, ctx->internal) != cudaSuccess ||
+      cudaStreamSynchronize(ctx->internal) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(PLAN_ECUDA);
+  }
+  *out = ctx;
+  return PLAN_OK;
+}
+
+int plan_solve_batch(plan_ctx* ctx, const plan_scene* scenes, const int* B, int S, const double* p,
+                     double* xi, double* resid, double* cu, void* stream) {
+  if (!ctx) return PLAN_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (S < 0 || (S > 0 && (!scenes || !B))) return fail(ctx, PLAN_EINVAL, "bad scenes / B");
+  if (S > ctx->cfg.max_scenes) return fail(ctx, PLAN_ECAPACITY, "S exceeds max_scenes");
+  std::vector<int> Bv(B, B + S);
+  long long total = 0;
+  for (int i = 0; i < S; ++i) {
+    if (Bv[i] < 0) return fail(ctx, PLAN_EINVAL, "B[%d] < 0", i);
+    total += Bv[i];
+    TRY(check_scene(ctx, &scenes[i], i));
+  }
+  if (total > ctx->cfg.max_samples) return fail(ctx, PLAN_ECAPACITY, "samples exceed max_samples");
+  if (total == 0) return PLAN_OK;
+  if (!p || !resid || !cu) return fail(ctx, PLAN_EINVAL, "p, resid and cu must be non-NULL");
+  CU(ctx, cudaSetDevice(ctx->device));
+  TRY(upload(ctx, ctx->tr, scenes, S, &Bv, s, nullptr));
+  const int warps = pick_warps(ctx, int(total));
+  CU(ctx, run_solve(ctx, ctx->tr, ctx->tr, n_tiles_of(Bv, warps), warps, int(total), p, xi, resid,
+                    cu, s));
+  return PLAN_OK;
+}
+
+int plan_solve(plan_ctx* ctx, const plan_scene* scene, const double* p, int B, double* xi,
+               double* resid, double* cu, void* stream) {
+  if (!ctx) return PLAN_EINVAL;
+  return plan_solve_batch(ctx, scene, &B, 1, p, xi, resid, cu, stream);
+}
+
+int plan_upload_scenes(plan_ctx* ctx, const plan_scene* scenes, int S, void* stream) {
+  if (!ctx) return PLAN_EINVAL;
+  if (S < 1 || !scenes) return fail(ctx, PLAN_EINVAL, "need S >= 1 scenes");
+  if (S > ctx->cfg.max_scenes) return fail(ctx, PLAN_ECAPACITY, "S exceeds max_scenes");
+  for (int i = 0; i < S; ++i) TRY(check_scene(ctx, &scenes[i], i));
+  CU(ctx, cudaSetDevice(ctx->device));
+  TRY(upload(ctx, ctx->res, scenes, S, nullptr, static_cast<cudaStream_t>(stream), &ctx->res_host));
+  ctx->n_uploaded = S;
+  return PLAN_OK;
+}
+
+int plan_set_state(plan_ctx* ctx, int slot, const plan_cem_state* st, void* stream) {
+  if (!ctx) return PLAN_EINVAL;
+  if (!st) return fail(ctx, PLAN_EINVAL, "state is NULL");
+  if (slot < 0 || slot >= ctx->n_uploaded)
+    return fail(ctx, PLAN_ESTATE, "slot %d has no uploaded scene", slot);
+  DevCem c;
+  TRY(make_cem(ctx, st, ctx->res_host[slot].n_lanes, ctx->res_host[slot].lane_width, &c));
+  CU(ctx, cudaSetDevice(ctx->device));
+  TRY(stage_acquire(ctx, sizeof(DevCem)));
+  std::memcpy(ctx->stage, &c, sizeof c);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CU(ctx, cudaMemcpyAsync(ctx->cem + slot, ctx->stage, sizeof c, cudaMemcpyHostToDevice, s));
+  return stage_release(ctx, s);
+}
+
+int plan_get_state(plan_ctx* ctx, int slot, plan_cem_state* st, void* stream) {
+  if (!ctx) return PLAN_EINVAL;
+  if (!st || slot < 0 || slot >= ctx->cfg.max_scenes) return fail(ctx, PLAN_EINVAL, "bad slot/state");
+  CU(ctx, cudaSetDevice(ctx->device));
+  TRY(stage_acquire(ctx, sizeof(DevCem)));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CU(ctx, cudaMemcpyAsync(ctx->stage, ctx->cem + slot, sizeof(DevCem), cudaMemcpyDeviceToHost, s));
+  CU(ctx, cudaStreamSynchronize(s));
+  DevCem c;
+  std::memcpy(&c, ctx->stage, sizeof c);
+  const int d = 2 * ctx->cfg.n_seg;
+  std::memset(st, 0, sizeof *st);
+  for (int a = 0; a < d; ++a) {
+    st->mu[a] = c.mu[a];
+    for (int b = 0; b < d; ++b) st->sigma[a * 8 + b] = c.sigma[a * kMaxDp + b];
+  }
+  st->seed = c.seed;
+  st->episode_step = c.step;
+  st->fresh = c.fresh;
+  return PLAN_OK;
+}
+
+int plan_get_result(plan_ctx* ctx, int slot, plan_result* out, void* stream) {
+  if (!ctx) return PLAN_EINVAL;
+  if (!out || slot < 0 || slot >= ctx->cfg.max_scenes) return fail(ctx, PLAN_EINVAL, "bad slot/out");
+  CU(ctx, cudaSetDevice(ctx->device));
+  TRY(stage_acquire(ctx, sizeof(DevCem)));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CU(ctx, cudaMemcpyAsync(ctx->stage, ctx->cem + slot, sizeof(DevCem), cudaMemcpyDeviceToHost, s));
+  CU(ctx, cudaStreamSynchronize(s));
+  DevCem c;
+  std::memcpy(&c, ctx->stage, sizeof c);
+  std::memset(out, 0, sizeof *out);
+  for (int a = 0; a < 2 * ctx->cfg.n_seg; ++a) out->p[a] = c.best_p[a];
+  for (int a = 0; a < 2 * ctx->cfg.n_coef; ++a) out->xi[a] = c.best_xi[a];
+  out->cost = c.best_cost;
+  out->resid = c.best_r;
+  out->cu = c.best_cu;
+  out->index = c.best_index;
+  if (!std::isfinite(c.best_cost)) return fail(ctx, PLAN_ENONFINITE, "best cost is not finite");
+  return PLAN_OK;
+}
+
+int plan_step_resident(plan_ctx* ctx, const int* B, int S, void* stream) {
+  if (!ctx) return PLAN_EINVAL;
+  if (S < 1 || !B) return fail(ctx, PLAN_EINVAL, "need S >= 1 and B");
+  if (S > ctx->n_uploaded) return fail(ctx, PLAN_ECAPACITY, "S exceeds the uploaded scene slots");
+  std::vector<int> Bv(B, B + S);
+  long long total = 0;
+  int max_B = 0;
+  for (int i = 0; i < S; ++i) {
+    if (Bv[i] < 1) return fail(ctx, PLAN_EINVAL, "B[%d] must be >= 1", i);
+    total += Bv[i];
+    max_B = std::max(max_B, Bv[i]);
+  }
+  if (total > ctx->cfg.max_samples) return fail(ctx, PLAN_ECAPACITY, "samples exceed max_samples");
+  CU(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  GraphEntry* g = nullptr;
+  for (auto& e : ctx->graphs)
+    if (e.B == Bv) g = &e;
+  if (!g) {
+    GraphEntry e;
+    e.B = Bv;
+    e.total_B = int(total);
+    e.max_B = max_B;
+    e.set.scenes = ctx->res.scenes;
+    e.set.obs = ctx->res.obs;
+    TRY(dalloc(ctx, &e.set.layout, S));
+    TRY(dalloc(ctx, &e.set.tiles, size_t(total) + S));
+    TRY(dalloc(ctx, &e.set.sample_scene, size_t(total)));
+    TRY(upload(ctx, e.set, nullptr, 0, &Bv, ctx->internal, nullptr));
+    CU(ctx, cudaStreamSynchronize(ctx->internal));
+    const int warps = pick_warps(ctx, int(total));
+    const int nt = n_tiles_of(Bv, warps);
+    cudaGraph_t graph = nullptr;
+    CU(ctx, cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaSuccess;
+    for (int l = 1; l <= ctx->cfg.outer_iters && ce == cudaSuccess; ++l) {
+      ce = launch_sample(e.set.scenes, e.set.layout, ctx->cem, S, max_B, l, ctx->prm, ctx->p,
+                         ctx->capture);
+      if (ce == cudaSuccess)
+        ce = run_solve(ctx, e.set, e.set, nt, warps, int(total), ctx->p, ctx->xi, ctx->r, ctx->cu,
+                       ctx->capture);
+      if (ce == cudaSuccess)
+        ce = launch_select_update(e.set.layout, ctx->cem, S, l, ctx->prm, ctx->p, ctx->xi, ctx->r,
+                                  ctx->cu, ctx->elite, ctx->capture);
+    }
+    cudaError_t ee = cudaStreamEndCapture(ctx->capture, &graph);
+    if (ce != cudaSuccess || ee != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return fail(ctx, PLAN_ECUDA, "graph capture failed: %s",
+                  cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+    }
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, PLAN_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(ie));
+    }
+    e.exec = exec;
+    ctx->graphs.push_back(e);
+    g = &ctx->graphs.back();
+  }
+  CU(ctx, cudaGraphLaunch(g->exec, s));
+  return PLAN_OK;
+}
+
+int plan_step(plan_ctx* ctx, const plan_scene* scene, plan_cem_state* st, int B, plan_result* out,
+              void* stream) {
+  if (!ctx) return PLAN_EINVAL;
+  if (!scene || !st || !out) return fail(ctx, PLAN_EINVAL, "scene, state and out must be non-NULL");
+  TRY(plan_upload_scenes(ctx, scene, 1, stream));
+  TRY(plan_set_state(ctx, 0, st, stream));
+  TRY(plan_step_resident(ctx, &B, 1, stream));
+  TRY(plan_get_result(ctx, 0, out, stream));
+  return plan_get_state(ctx, 0, st, stream);
+}
+
+int plan_select_elites(plan_ctx* ctx, const double* resid, const double* cu, int B, int n_c, int q,
+                       int* elite, void* stream) {
+  if (!ctx) return PLAN_EINVAL;
+  if (!resid || !cu || !elite) return fail(ctx, PLAN_EINVAL, "NULL buffer");
+  if (B < 1 || n_c < 1 || n_c > B || n_c > kMaxEliteC || q < 1 || q > n_c)
+    return fail(ctx, PLAN_EINVAL, "need 1 <= q <= n_c <= min(B, 2048)");
+  CU(ctx, cudaSetDevice(ctx->device));
+  CU(ctx, launch_select_only(resid, cu, B, n_c, q, elite, static_cast<cudaStream_t>(stream)));
+  return PLAN_OK;
+}
+
+int plan_update_distribution(plan_ctx* ctx, const double* p_elite, const double* cost, int q,
+                             double* mu, double* sigma, void* stream) {
+  if (!ctx) return PLAN_EINVAL;
+  if (!p_elite || !cost || !mu || !sigma) return fail(ctx, PLAN_EINVAL, "NULL buffer");
+  if (q < 1 || q > kMaxEliteC) return fail(ctx, PLAN_EINVAL, "q must be in [1, 2048]");
+  CU(ctx, cudaSetDevice(ctx->device));
+  CU(ctx, launch_update_only(p_elite, cost, q, 2 * ctx->cfg.n_seg, ctx->cfg.gamma, ctx->cfg.eta, mu,
+                             sigma, static_cast<cudaStream_t>(stream)));
+  return PLAN_OK;
+}
+
+int plan_sample(plan_ctx* ctx, const plan_scene* scene, const double* mu, const double* sigma,
+                int fresh, int l, uint64_t seed, uint64_t episode_step, int B, double* p,
+                void* stream) {
+  if (!ctx) return PLAN_EINVAL;
+  if (!scene || !p || (!fresh && (!mu || !sigma))) return fail(ctx, PLAN_EINVAL, "NULL argument");
+  if (l < 1 || l > 65535 || B < 0) return fail(ctx, PLAN_EINVAL, "bad l or B");
+  if (B > ctx->cfg.max_samples) return fail(ctx, PLAN_ECAPACITY, "B exceeds max_samples");
+  TRY(check_scene(ctx, scene, 0));
+  if (B == 0) return PLAN_OK;
+  plan_cem_state st{};
+  const int d = 2 * ctx->cfg.n_seg;
+  if (!fresh)
+    for (int a = 0; a < d; ++a) {
+      st.mu[a] = mu[a];
+      for (int b = 0; b < d; ++b) st.sigma[a * 8 + b] = sigma[a * d + b];
+    }
+  st.seed = seed;
+  st.episode_step = episode_step;
+  st.fresh = fresh;
+  DevCem c;
+  TRY(make_cem(ctx, &st, scene->n_lanes, scene->lane_width, &c));
+  CU(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<int> Bv{B};
+  TRY(upload(ctx, ctx->tr, scene, 1, &Bv, s, nullptr));
+  TRY(stage_acquire(ctx, sizeof(DevCem)));
+  std::memcpy(ctx->stage, &c, sizeof c);
+  CU(ctx, cudaMemcpyAsync(ctx->cem_tmp, ctx->stage, sizeof c, cudaMemcpyHostToDevice, s));
+  TRY(stage_release(ctx, s));
+  CU(ctx, launch_sample(ctx->tr.scenes, ctx->tr.layout, ctx->cem_tmp, 1, B, l, ctx->prm, p, s));
+  return PLAN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+"""Torch-facing convenience layer over the C ABI.
+
+PyTorch supplies device memory and the current stream; every computation runs
+in the CUDA library (binding.py marshals the arguments).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import binding as B
+
+
+def _stream(stream=None) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+def _ptr(t):
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _need(t: torch.Tensor, shape, name: str):
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+class Planner:
+    """One planner context on the current CUDA device.
+
+    params: object with the planner parameters (see scenegen.Params);
+    prec: "fp32" (fused kernel) or "fp64" (plain reference path).
+    """
+
+    def __init__(self, params, prec: str = "fp32", max_obs: int = 32, max_samples: int = 4096,
+                 max_scenes: int = 1):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the planner runs on a CUDA GPU; none is available")
+        self.prm = params
+        self.prec = {"fp32": B.PLAN_PREC_FP32, "fp64": B.PLAN_PREC_FP64}[prec]
+        self.cfg = B.make_config(params, self.prec, max_obs, max_samples, max_scenes)
+        self.ctx = B.plan_init(self.cfg)
+        self.n = params.n_coef
+        self.d_p = 2 * params.n_seg
+
+    def close(self):
+        if self.ctx is not None:
+            B.plan_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -------------------------------------------------------------- lower level
+    def solve(self, scene, p: torch.Tensor, stream=None, want_xi: bool = True):
+        Bn = p.shape[0]
+        _need(p, (Bn, self.d_p), "p")
+        dev = p.device
+        xi = torch.empty((Bn, 2 * self.n), dtype=torch.float64, device=dev) if want_xi else None
+        r = torch.empty(Bn, dtype=torch.float64, device=dev)
+        cu = torch.empty(Bn, dtype=torch.float64, device=dev)
+        B.plan_solve(self.ctx, scene, _ptr(p), Bn, _ptr(xi), _ptr(r), _ptr(cu), _stream(stream))
+        return xi, r, cu
+
+    def solve_batch(self, scenes, Bs, p: torch.Tensor, stream=None):
+        tot = int(sum(Bs))
+        _need(p, (tot, self.d_p), "p")
+        xi = torch.empty((tot, 2 * self.n), dtype=torch.float64, device=p.device)
+        r = torch.empty(tot, dtype=torch.float64, device=p.device)
+        cu = torch.empty(tot, dtype=torch.float64, device=p.device)
+        B.plan_solve_batch(self.ctx, scenes, Bs, _ptr(p), _ptr(xi), _ptr(r), _ptr(cu), _stream(stream))
+        return xi, r, cu
+
+    # -------------------------------------------------------------- Alg. 1
+    def upload(self, scenes, stream=None):
+        B.plan_upload_scenes(self.ctx, scenes, _stream(stream))
+
+    def set_state(self, slot: int, mu=None, sigma=None, seed: int = 0, step: int = 0, fresh=None,
+                  stream=None):
+        B.plan_set_state(self.ctx, slot, B.make_state(self.d_p, mu, sigma, seed, step, fresh),
+                         _stream(stream))
+
+    def get_state(self, slot: int, stream=None):
+        st = B.plan_get_state(self.ctx, slot, _stream(stream))
+        mu, sigma = B.state_arrays(st, self.d_p)
+        return dict(mu=mu, sigma=sigma, seed=st.seed, step=st.episode_step, fresh=st.fresh)
+
+    def step_resident(self, Bs, stream=None):
+        B.plan_step_resident(self.ctx, Bs, _stream(stream))
+
+    def get_result(self, slot: int, stream=None):
+        r = B.plan_get_result(self.ctx, slot, _stream(stream))
+        return dict(p=list(r.p[:self.d_p]), xi=list(r.xi[:2 * self.n]), cost=r.cost,
+                    resid=r.resid, cu=r.cu, index=r.index)
+
+    def step(self, scene, Bn: int, mu=None, sigma=None, seed: int = 0, step: int = 0, stream=None):
+        st = B.make_state(self.d_p, mu, sigma, seed, step)
+        r = B.plan_step(self.ctx, scene, st, Bn, _stream(stream))
+        mu1, sg1 = B.state_arrays(st, self.d_p)
+        return dict(p=list(r.p[:self.d_p]), xi=list(r.xi[:2 * self.n]), cost=r.cost, resid=r.resid,
+                    cu=r.cu, index=r.index, mu=mu1, sigma=sg1, step=st.episode_step)
+
+    # -------------------------------------------------------------- single stages
+    def select_elites(self, r: torch.Tensor, cu: torch.Tensor, n_c: int, q: int, stream=None):
+        Bn = r.shape[0]
+        _need(r, (Bn,), "r")
+        _need(cu, (Bn,), "cu")
+        elite = torch.empty(q, dtype=torch.int32, device=r.device)
+        B.plan_select_elites(self.ctx, _ptr(r), _ptr(cu), Bn, n_c, q, _ptr(elite), _stream(stream))
+        return elite
+
+    def update_distribution(self, p_elite: torch.Tensor, cost: torch.Tensor, mu: torch.Tensor,
+                            sigma: torch.Tensor, stream=None):
+        q = p_elite.shape[0]
+        _need(p_elite, (q, self.d_p), "p_elite")
+        _need(cost, (q,), "cost")
+        _need(mu, (self.d_p,), "mu")
+        _need(sigma, (self.d_p, self.d_p), "sigma")
+        B.plan_update_distribution(self.ctx, _ptr(p_elite), _ptr(cost), q, _ptr(mu), _ptr(sigma),
+                                   _stream(stream))
+
+    def sample(self, scene, Bn: int, l: int, seed: int, step: int = 0, mu=None, sigma=None,
+               stream=None, device=None):
+        p = torch.empty((Bn, self.d_p), dtype=torch.float64, device=device or "cuda")
+        B.plan_sample(self.ctx, scene, mu, sigma, int(mu is None), l, seed, step, Bn, _ptr(p),
+                      _stream(stream))
+        return p

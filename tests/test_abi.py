@@ -1,0 +1,78 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads and
+exports every function include/plan.h declares, and plan_init rejects invalid
+configurations before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2212_02224_gb300 import binding, build, scenegen
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib():
+    if not os.path.exists(binding.LIB_PATH):
+        build.build()
+    return binding.load()
+
+
+def _declared():
+    hdr = open(os.path.join(ROOT, "include", "plan.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"\b(plan_[a-z_]+)\s*\(", hdr)))
+
+
+def test_header_declares_the_binding_names():
+    assert _declared() == sorted(binding.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _lib()
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings():
+    lib = _lib()
+    assert lib.plan_status_str(0) == b"ok"
+    assert lib.plan_status_str(binding.PLAN_ECAPACITY) == b"capacity exceeded"
+    assert lib.plan_status_str(12345) == b"unknown status"
+
+
+@pytest.mark.parametrize("field,value,needle", [
+    ("m", 4, "m must be"),
+    ("n_coef", 17, "n_coef"),
+    ("n_seg", 5, "n_seg"),
+    ("inner_iters", 0, "inner_iters"),
+    ("n_elite", 0, "n_elite"),
+    ("eta", 0.0, "eta"),
+    ("v_max", 0.05, "v_min < v_max"),
+    ("n_elite_c", 4096, "2048"),
+])
+def test_init_rejects_invalid_config(field, value, needle):
+    lib = _lib()
+    prm = scenegen.Params()
+    cfg = binding.make_config(prm, binding.PLAN_PREC_FP32, 8, 64)
+    setattr(cfg, field, value)
+    ctx = ctypes.c_void_p()
+    st = lib.plan_init(ctypes.byref(cfg), ctypes.byref(ctx))
+    assert st == binding.PLAN_EINVAL
+    assert ctx.value is None
+    assert needle in binding.last_error(None)
+
+
+def test_fp32_kernel_coefficient_counts():
+    lib = _lib()
+    prm = scenegen.Params(n_coef=9)
+    cfg = binding.make_config(prm, binding.PLAN_PREC_FP32, 8, 64)
+    ctx = ctypes.c_void_p()
+    assert lib.plan_init(ctypes.byref(cfg), ctypes.byref(ctx)) == binding.PLAN_EINVAL
+    assert "n_coef" in binding.last_error(None)
+
+
+def test_null_context_is_rejected():
+    lib = _lib()
+    assert lib.plan_solve(None, None, None, 0, None, None, None, None) == binding.PLAN_EINVAL
+    assert lib.plan_destroy(None) == binding.PLAN_OK

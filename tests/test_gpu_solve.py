@@ -1,0 +1,122 @@
+"""Parity of the lower-level solve (Step 1, Alg. 2, scoring) through the C ABI
+against the FP64 oracle, for both the plain FP64 path and the fused FP32
+kernel.  Sizes span several tiles and a ragged last slot of timesteps."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import lower
+from oracle.basis import bernstein
+from paper_2212_02224_gb300 import binding, scenegen as sg
+
+from gpu_common import compare, planner, scene_with, to_dev
+
+pytestmark = pytest.mark.gpu
+PRECS = ["fp64", "fp32"]
+
+
+def _run(prec, prm, sc, p, max_obs=32):
+    pl = planner(prm, prec, max_obs=max_obs, max_samples=max(len(p), 1))
+    xi, r, cu = pl.solve(sc, to_dev(p))
+    torch.cuda.synchronize()
+    out = xi.cpu().numpy(), r.cpu().numpy(), cu.cpu().numpy()
+    pl.close()
+    return out
+
+
+def _oracle(prm, sc, p):
+    return lower.solve(p, sc, prm, bernstein(prm.m, prm.n_coef, prm.dt))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_small_plain_workload(prec):
+    """2 lanes, 4 obstacles, B = 64, 50 iterations."""
+    prm, sc, B = sg.workload(0)
+    p = sg.make_samples(101, sc, B, prm.n_seg)
+    compare(prec, prm, *_run(prec, prm, sc, p), *_oracle(prm, sc, p))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_dense_traffic_scene(prec):
+    """4 lanes, 12 obstacles, 100 iterations, 96 samples."""
+    prm, sc, _ = sg.workload(1)
+    p = sg.make_samples(202, sc, 96, prm.n_seg)
+    compare(prec, prm, *_run(prec, prm, sc, p), *_oracle(prm, sc, p))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_dense_traffic_full_batch_sampled(prec):
+    """Full size (B = 1000) on the GPU, 24 sampled results checked one by one."""
+    prm, sc, B = sg.workload(1)
+    p = sg.make_samples(303, sc, B, prm.n_seg)
+    xi, r, cu = _run(prec, prm, sc, p)
+    idx = np.unique(sg.Stream(7).integers(0, B - 1, 24))
+    xo, ro, co = _oracle(prm, sc, p[idx])
+    compare(prec, prm, xi[idx], r[idx], cu[idx], xo, ro, co)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("case", ["no_obstacles", "single_sample", "four_segments",
+                                  "ragged_horizon", "wide_basis", "static_obstacles"])
+def test_edge_cases(prec, case):
+    if case == "no_obstacles":
+        prm, sc, _ = sg.workload(0, inner_iters=30)
+        sc.obstacles = np.zeros((0, 6))
+        p = sg.make_samples(1, sc, 40, prm.n_seg)
+    elif case == "single_sample":
+        prm, sc, _ = sg.workload(1, inner_iters=40)
+        p = sg.make_samples(2, sc, 1, prm.n_seg)
+    elif case == "four_segments":
+        prm, sc, _ = sg.workload(1, inner_iters=40, n_seg=4)
+        p = sg.make_samples(3, sc, 50, 4)
+    elif case == "ragged_horizon":
+        prm = sg.Params(m=37, n_coef=8, inner_iters=30)
+        sc = scene_with(4, 3, 5, obs_x=(5.0, 30.0))
+        p = sg.make_samples(4, sc, 33, 1)
+    elif case == "wide_basis":
+        prm, sc, _ = sg.workload(4, inner_iters=40)
+        p = sg.make_samples(5, sc, 20, prm.n_seg)
+    else:
+        prm = sg.Params(m=100, n_coef=11, inner_iters=60)
+        sc = scene_with(6, 3, 6, obs_x=(12.0, 50.0), obs_vx=(0.0, 0.0))
+        p = sg.make_samples(6, sc, 70, 1)
+    compare(prec, prm, *_run(prec, prm, sc, p, max_obs=max(sc.n_obs, 1)), *_oracle(prm, sc, p))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_batched_scenes_uneven(prec):
+    """Several scenes of uneven obstacle and sample counts in one call."""
+    prm, scenes, Bs = sg.batched_workload(S=5, seed=77, B_range=(1, 40), N_range=(0, 14),
+                                          inner_iters=40)
+    ps = [sg.make_samples(500 + i, scenes[i], Bs[i], prm.n_seg) for i in range(5)]
+    pl = planner(prm, prec, max_obs=20, max_samples=sum(Bs), max_scenes=5)
+    xi, r, cu = pl.solve_batch(scenes, Bs, to_dev(np.concatenate(ps)))
+    torch.cuda.synchronize()
+    xi, r, cu = xi.cpu().numpy(), r.cpu().numpy(), cu.cpu().numpy()
+    pl.close()
+    off = 0
+    for i in range(5):
+        sl = slice(off, off + Bs[i])
+        compare(prec, prm, xi[sl], r[sl], cu[sl], *_oracle(prm, scenes[i], ps[i]))
+        off += Bs[i]
+
+
+def test_capacity_and_argument_errors():
+    prm, sc, _ = sg.workload(0)
+    pl = planner(prm, "fp32", max_obs=2, max_samples=16)
+    p = to_dev(sg.make_samples(1, sc, 32, 1))
+    with pytest.raises(binding.PlanError) as e:
+        pl.solve(sc, p)           # 4 obstacles > max_obs
+    assert e.value.status == binding.PLAN_ECAPACITY
+    sc.obstacles = sc.obstacles[:2]
+    with pytest.raises(binding.PlanError) as e:
+        pl.solve(sc, p)           # 32 samples > max_samples
+    assert e.value.status == binding.PLAN_ECAPACITY
+    bad = sg.make_scene(1, n_lanes=2, n_obs=1)
+    bad.obstacles[0, 4] = 0.0     # zero ellipse axis
+    with pytest.raises(binding.PlanError) as e:
+        pl.solve(bad, p[:4].contiguous())
+    assert e.value.status == binding.PLAN_EINVAL
+    xi, r, cu = pl.solve(sc, p[:0].contiguous())   # B = 0 is a no-op
+    assert r.numel() == 0
+    pl.close()
