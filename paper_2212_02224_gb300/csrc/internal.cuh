@@ -47,7 +47,10 @@ struct Params {
 
 // Constants built in float64 on the device by build_constants().
 //   basis64 [3][m][n]  W, Wd, Wdd row-major (FP64 path)
-//   basis32 [3][n][m]  the same, coefficient-major so that t is contiguous
+//   basis32 [m][stride] per timestep the rows W[t], Wd[t], Wdd[t], each padded
+//           to ncp = 4 ceil(n / 4) floats, row stride basis32_stride(n) floats
+//           (an odd multiple of 4, so 16-byte loads of 8 consecutive t are
+//           free of shared-memory bank conflicts)
 //   s1_*    [2][n][n_seg + 3]  Step-1 maps: xi_bar_axis = Gs p_axis + Hs b_axis
 //   pj_*    [N + 1][2][n][2n + 3]  per obstacle count N and axis, row k:
 //           M[k][:], MP[k][:], C[k][:] with xi = M r + C b (KKT inverse of
@@ -72,6 +75,11 @@ struct Layout {
 struct Tile {
   int scene, first, count, pad;
 };
+
+__host__ __device__ constexpr int basis32_ncp(int n) { return (n + 3) / 4 * 4; }
+__host__ __device__ constexpr int basis32_stride(int n) {
+  return ((3 * basis32_ncp(n)) / 4) % 2 == 1 ? 3 * basis32_ncp(n) : 3 * basis32_ncp(n) + 4;
+}
 
 // Launchers (return the cudaError_t of the launch).
 cudaError_t build_constants(const Consts& c, const Params& p, cudaStream_t s);

@@ -39,9 +39,10 @@ __global__ void basis_kernel(int m, int n, double dt, double* b64, float* b32) {
   b64[0 * m * n + t * n + k] = w;
   b64[1 * m * n + t * n + k] = wd;
   b64[2 * m * n + t * n + k] = wdd;
-  b32[0 * n * m + k * m + t] = float(w);
-  b32[1 * n * m + k * m + t] = float(wd);
-  b32[2 * n * m + k * m + t] = float(wdd);
+  const int st = basis32_stride(n), ncp = basis32_ncp(n);
+  b32[t * st + 0 * ncp + k] = float(w);
+  b32[t * st + 1 * ncp + k] = float(wd);
+  b32[t * st + 2 * ncp + k] = float(wdd);
 }
 
 // Invert the (sz x sz) matrix held in smem `a` (leading dimension ld, with
@@ -213,6 +214,8 @@ __global__ void kkt_kernel(Consts c, Params p) {
 
 cudaError_t build_constants(const Consts& c, const Params& p, cudaStream_t s) {
   int mn = c.m * c.n;
+  cudaError_t e0 = cudaMemsetAsync(c.basis32, 0, sizeof(float) * c.m * basis32_stride(c.n), s);
+  if (e0 != cudaSuccess) return e0;
   basis_kernel<<<(mn + 127) / 128, 128, 0, s>>>(c.m, c.n, p.dt, c.basis64, c.basis32);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

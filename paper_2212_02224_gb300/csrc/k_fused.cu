@@ -2,19 +2,25 @@
 // inverse of Eq. over_3), all K iterations of Alg. 2 and the scoring of
 // Alg. 1 line 9 / Sec. V-A, one warp per sample, all state on chip.
 //
-// Per iteration and sample the warp
+// State is kept relative to the Step-1 solution: delta = xi - xi_bar.  Per
+// iteration and sample the warp
 //   A. evaluates x, y and their derivatives at the lane's timesteps
-//      t = s*32 + lane (Eq. param; basis staged in shared memory),
+//      t = s*32 + lane as (reference at xi_bar) + W delta (Eq. param; basis
+//      rows staged in shared memory),
 //   B. projects onto every obstacle ellipse (Eqs. split_alpha_o, clip_d_o),
 //   C. projects velocity and acceleration (Eqs. clip_d_v, clip_d_a), the lane
 //      rows (Eq. update_slack) and accumulates the transposed contraction
 //        w = F^T (h - F xi) + G^T (e - s - G xi),
 //   D. reduce-scatters w over the warp, updates the multipliers
 //      lambda += rho/2 w (Eq. update_lagrange) and takes the xi-step of
-//      Eq. split_xy in folded form
-//        xi' = (M xi_bar + C b0) + M (lambda + rho w) + (rho M P) xi,
-//      which equals M (xi_bar + lambda + rho F^T h + rho G^T (e - s)) + C b0
-//      because F^T h + G^T (e - s) = w + P xi with P = F^T F + G^T G.
+//      Eq. split_xy in increment form
+//        delta' = delta + M (lambda + rho w - delta).
+// The increment form is exact: with H = I + rho P, P = F^T F + G^T G and the
+// KKT inverse [[M, C], [C^T, D]] of [[H, A^T], [A, 0]], M H = I - C A, so
+// M (xi_bar + lambda + rho F^T h + rho G^T (e - s)) + C b0
+//   = xi + M (xi_bar - xi + lambda + rho w) + C (b0 - A xi),
+// and every iterate satisfies A xi = b0.  Working on delta (metres) instead
+// of xi (hundreds of metres) keeps float32 rounding from accumulating.
 //
 // The closed form of Eq. split_alpha_o is used without trigonometry: for an
 // obstacle with scaled offset (sx, sy) = ((x - x_o)/a, (y - y_o)/b) and
@@ -58,13 +64,44 @@ __device__ __forceinline__ float reduce_scatter(const float (&wx)[NC], const flo
   return v[0];
 }
 
+// sqrt(x) for x >= 0 through the hardware reciprocal square root.
+__device__ __forceinline__ float fast_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+
+// W[t] . a, Wd[t] . a, Wdd[t] . a for both axes: row pointer `row` holds the
+// three padded basis rows of timestep t.
+template <int NC>
+__device__ __forceinline__ void kin(const float* __restrict__ row, const float (&xv)[NC],
+                                    const float (&yv)[NC], float (&o)[6]) {
+  constexpr int NCP = basis32_ncp(NC);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) o[q] = 0.f;
+#pragma unroll
+  for (int mat = 0; mat < 3; ++mat) {
+#pragma unroll
+    for (int k4 = 0; k4 < NCP; k4 += 4) {
+      const float4 w = *reinterpret_cast<const float4*>(row + mat * NCP + k4);
+      const float wk[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (k4 + u < NC) {
+          o[2 * mat] = fmaf(wk[u], xv[k4 + u], o[2 * mat]);
+          o[2 * mat + 1] = fmaf(wk[u], yv[k4 + u], o[2 * mat + 1]);
+        }
+      }
+    }
+  }
+}
+
 template <int NC, int SLOTS>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 1)
 fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ layout,
              const double* __restrict__ obs, const Tile* __restrict__ tiles,
              const double* __restrict__ pin, Consts c, Params prm,
              double* __restrict__ xi_out, double* __restrict__ r_out,
              double* __restrict__ cu_out) {
+  constexpr int NCP = basis32_ncp(NC);
+  constexpr int ST = basis32_stride(NC);
+  constexpr bool kRefInRegs = SLOTS <= 4;
   extern __shared__ __align__(16) float smem[];
   const int m = prm.m;
   const int ns = prm.n_seg;
@@ -73,60 +110,84 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   const int N = sc.n_obs;
   const int warps = blockDim.x >> 5;
 
-  float* sW = smem;                                   // [3][NC][m]
-  float4* sObs = reinterpret_cast<float4*>(smem + ((3 * NC * m + 3) & ~3));  // [N][2]
-  float* sBuf = reinterpret_cast<float*>(sObs + 2 * N);                      // [warps][64]
+  float* sW = smem;                                          // [m][ST]
+  float4* sObs = reinterpret_cast<float4*>(smem + m * ST);   // [N][2]
+  float* sBuf = reinterpret_cast<float*>(sObs + 2 * N);      // [warps][64]
+  float* sRef = sBuf + 64 * warps;                           // [warps][6][m] (SLOTS > 4)
 
-  for (int i = threadIdx.x; i < 3 * NC * m; i += blockDim.x) sW[i] = c.basis32[i];
+  {
+    const float4* src = reinterpret_cast<const float4*>(c.basis32);
+    float4* dst = reinterpret_cast<float4*>(sW);
+    for (int i = threadIdx.x; i < m * ST / 4; i += blockDim.x) dst[i] = src[i];
+  }
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    // scaled trajectory x_o(t) / a = x0/a + (vx/a) t and likewise for y
     const double* o = obs + size_t(sc.obs_off + i) * 6;
-    sObs[2 * i] = make_float4(float(o[0]), float(o[1]), float(o[2]), float(o[3]));
-    sObs[2 * i + 1] = make_float4(float(1.0 / o[4]), float(1.0 / o[5]), float(o[4]), float(o[5]));
+    const double ia = 1.0 / o[4], ib = 1.0 / o[5];
+    sObs[2 * i] = make_float4(float(o[0] * ia), float(o[1] * ib), float(o[2] * ia * prm.dt),
+                              float(o[3] * ib * prm.dt));
+    sObs[2 * i + 1] = make_float4(float(ia), float(ib), float(o[4]), float(o[5]));
   }
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp >= tile.count) return;
   const int j = layout[tile.scene].off + tile.first + warp;   // global sample index
-  float* xbuf = sBuf + warp * 64;      // xi, slot layout
-  float* vbuf = xbuf + 32;             // lambda + rho w, slot layout
+  float* xbuf = sBuf + warp * 64;      // slot layout: xi_bar, then delta
+  float* vbuf = xbuf + 32;             // slot layout: lambda + rho w - delta
+  float* ref = sRef + warp * 6 * m;
 
-  const float* W0 = sW;
-  const float* W1 = sW + NC * m;
-  const float* W2 = sW + 2 * NC * m;
-
-  // ---- per-lane coefficient slot and its constant rows
+  // ---- per-lane coefficient slot: Step 1 and the row of M
   const int axis = lane >> 4, kk = lane & 15;
   const bool valid = kk < NC;
-  float Mrow[NC], MProw[NC];
-  float xibp = 0.f, lam = 0.f;
-  const float b_ax0 = float(sc.ego[axis + 0]);   // position
-  const float b_ax1 = float(sc.ego[axis + 2]);   // velocity
-  const float b_ax2 = float(sc.ego[axis + 4]);   // acceleration
+  float Mrow[NC];
+  float xb_l = 0.f;     // xi_bar of this lane's slot
   {
     if (valid) {
       const float* row = c.pj32 + size_t((N * 2 + axis) * NC + kk) * (2 * NC + 3);
 #pragma unroll
-      for (int i = 0; i < NC; ++i) { Mrow[i] = row[i]; MProw[i] = row[NC + i]; }
-      // Step 1: xi_bar = Gs p_axis + Hs b_axis (x uses the v_d entries, y the y_d entries)
+      for (int i = 0; i < NC; ++i) Mrow[i] = row[i];
+      // xi_bar = Gs p_axis + Hs b_axis (x uses the v_d entries, y the y_d entries)
       const float* s1 = c.s1_32 + size_t(axis * NC + kk) * (ns + 3);
       const double* pj = pin + size_t(j) * (2 * ns);
       float xb = 0.f;
-      for (int q = 0; q < ns; ++q) xb += s1[q] * float(pj[(axis == 0 ? ns : 0) + q]);
-      xb += s1[ns] * b_ax0 + s1[ns + 1] * b_ax1 + s1[ns + 2] * b_ax2;
+      for (int q = 0; q < ns; ++q) xb = fmaf(s1[q], float(pj[(axis == 0 ? ns : 0) + q]), xb);
+      xb = fmaf(s1[ns], float(sc.ego[axis]), xb);
+      xb = fmaf(s1[ns + 1], float(sc.ego[axis + 2]), xb);
+      xb = fmaf(s1[ns + 2], float(sc.ego[axis + 4]), xb);
+      xb_l = xb;
       xbuf[lane] = xb;
-      // constant part of the xi-step: M xi_bar + C b0 (needs all of xi_bar)
-      xibp = row[2 * NC] * b_ax0 + row[2 * NC + 1] * b_ax1 + row[2 * NC + 2] * b_ax2;
     } else {
 #pragma unroll
-      for (int i = 0; i < NC; ++i) { Mrow[i] = 0.f; MProw[i] = 0.f; }
-    }
-    __syncwarp();
-    if (valid) {
-#pragma unroll
-      for (int i = 0; i < NC; ++i) xibp += Mrow[i] * xbuf[axis * 16 + i];
+      for (int i = 0; i < NC; ++i) Mrow[i] = 0.f;
     }
   }
+  __syncwarp();
+
+  // ---- reference kinematics at xi_bar
+  float rk[kRefInRegs ? SLOTS : 1][6];
+  {
+    float xv[NC], yv[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) { xv[i] = xbuf[i]; yv[i] = xbuf[16 + i]; }
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      const int t = s * 32 + lane;
+      float o[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (t < m) kin<NC>(sW + t * ST, xv, yv, o);
+      if constexpr (kRefInRegs) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) rk[s][q] = o[q];
+      } else {
+        if (t < m) {
+#pragma unroll
+          for (int q = 0; q < 6; ++q) ref[q * m + t] = o[q];
+        }
+      }
+    }
+  }
+  __syncwarp();
+  if (valid) xbuf[lane] = 0.f;    // delta^0 = 0
 
   const float rho = float(prm.rho);
   const float hrho = 0.5f * rho;
@@ -135,16 +196,16 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   const float c_max = float(prm.c_max);
   const float kr = float(fabs(sc.kappa_road));
   const float y_lb = float(sc.y_lb), y_ub = float(sc.y_ub);
-  const float dt = float(prm.dt);
 
-  float tt[SLOTS];
+  float tt[SLOTS];   // time index t (the obstacle table holds per-step velocities)
 #pragma unroll
-  for (int s = 0; s < SLOTS; ++s) tt[s] = float(s * 32 + lane) * dt;
+  for (int s = 0; s < SLOTS; ++s) tt[s] = float(s * 32 + lane);
 
   float da[SLOTS];
 #pragma unroll
   for (int s = 0; s < SLOTS; ++s) da[s] = 0.f;
 
+  float lam = 0.f, dl = 0.f;     // lambda and delta of this lane's slot
   float r_acc = 0.f, cu_acc = 0.f;
 
   for (int it = 0;; ++it) {
@@ -158,17 +219,21 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) {
       const int t = s * 32 + lane;
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f;
+      float o[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      float r6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       if (t < m) {
+        kin<NC>(sW + t * ST, xv, yv, o);
+        if constexpr (kRefInRegs) {
 #pragma unroll
-        for (int k = 0; k < NC; ++k) {
-          const float w0 = W0[k * m + t], w1 = W1[k * m + t], w2 = W2[k * m + t];
-          a0 = fmaf(w0, xv[k], a0); b0 = fmaf(w0, yv[k], b0);
-          a1 = fmaf(w1, xv[k], a1); b1 = fmaf(w1, yv[k], b1);
-          a2 = fmaf(w2, xv[k], a2); b2 = fmaf(w2, yv[k], b2);
+          for (int q = 0; q < 6; ++q) r6[q] = rk[s][q];
+        } else {
+#pragma unroll
+          for (int q = 0; q < 6; ++q) r6[q] = ref[q * m + t];
         }
       }
-      px[s] = a0; vx[s] = a1; ax[s] = a2; py[s] = b0; vy[s] = b1; ay[s] = b2;
+      px[s] = r6[0] + o[0]; py[s] = r6[1] + o[1];
+      vx[s] = r6[2] + o[2]; vy[s] = r6[3] + o[3];
+      ax[s] = r6[4] + o[4]; ay[s] = r6[5] + o[5];
     }
 
     if (it == prm.K) {
@@ -180,13 +245,13 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
         float coll = 0.f;
         for (int i = 0; i < N; ++i) {
           const float4 o0 = sObs[2 * i], o1 = sObs[2 * i + 1];
-          const float sx = (px[s] - fmaf(o0.z, tt[s], o0.x)) * o1.x;
-          const float sy = (py[s] - fmaf(o0.w, tt[s], o0.y)) * o1.y;
+          const float sx = fmaf(px[s], o1.x, -fmaf(o0.z, tt[s], o0.x));
+          const float sy = fmaf(py[s], o1.y, -fmaf(o0.w, tt[s], o0.y));
           coll += fmaxf(0.f, 1.f - fmaf(sx, sx, sy * sy));
         }
-        const float sp = sqrtf(fmaf(vx[s], vx[s], vy[s] * vy[s]));
-        const float am = sqrtf(fmaf(ax[s], ax[s], ay[s] * ay[s]));
-        const float kap = sp > 0.f ? (ay[s] * vx[s] - ax[s] * vy[s]) / (sp * sp * sp) : 0.f;
+        const float sp = fast_sqrt(fmaf(vx[s], vx[s], vy[s] * vy[s]));
+        const float am = fast_sqrt(fmaf(ax[s], ax[s], ay[s] * ay[s]));
+        const float kap = sp > 0.f ? __fdividef(ay[s] * vx[s] - ax[s] * vy[s], sp * sp * sp) : 0.f;
         r_acc += coll + fmaxf(0.f, sp - v_max) + fmaxf(0.f, am - a_max) +
                  fmaxf(0.f, fabsf(kap) - kmax) + fmaxf(0.f, vx[s] * vx[s] * kr - c_max) +
                  fmaxf(0.f, py[s] - y_ub) + fmaxf(0.f, y_lb - py[s]);
@@ -204,15 +269,14 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       const float4 o0 = sObs[2 * i], o1 = sObs[2 * i + 1];
 #pragma unroll
       for (int s = 0; s < SLOTS; ++s) {
-        const float dx = px[s] - fmaf(o0.z, tt[s], o0.x);
-        const float dy = py[s] - fmaf(o0.w, tt[s], o0.y);
-        const float sx = dx * o1.x, sy = dy * o1.y;
+        const float sx = fmaf(px[s], o1.x, -fmaf(o0.z, tt[s], o0.x));
+        const float sy = fmaf(py[s], o1.y, -fmaf(o0.w, tt[s], o0.y));
         const float d2 = fmaf(sx, sx, sy * sy);
         if (d2 < 1.f) {
           if (d2 > 0.f) {
             const float g = rsqrtf(d2) - 1.f;
-            ex[s] = fmaf(g, dx, ex[s]);
-            ey[s] = fmaf(g, dy, ey[s]);
+            ex[s] = fmaf(g * o1.z, sx, ex[s]);
+            ey[s] = fmaf(g * o1.w, sy, ey[s]);
           } else {
             ex[s] += o1.z;      // atan2(0, 0) = 0: h = (x_o + a, y_o)
           }
@@ -236,44 +300,55 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       if (a2 > 0.f) { const float ra = rsqrtf(a2); ca = ax[s] * ra; sa = ay[s] * ra; am = a2 * ra; }
       const float S = fabsf(sa * cv - ca * sv);               // |sin(alpha_a - alpha_v)|
       const float dap = (it == 0) ? fminf(am, a_max) : da[s];
-      const float vmin_b = fmaxf(v_min, sqrtf(dap * S * inv_kmax));
+      const float vmin_b = fmaxf(v_min, fast_sqrt(dap * S * inv_kmax));
       float vmax_b = v_max;
       if (kr > 0.f) {
         const float tc = kr * cv * cv;
-        if (tc > 0.f) vmax_b = fminf(v_max, sqrtf(c_max / tc));
+        if (tc > 0.f) vmax_b = fminf(v_max, fast_sqrt(__fdividef(c_max, tc)));
       }
       const float dv = fminf(fmaxf(sp, vmin_b), vmax_b);
       const float kd = dv * dv * kmax;
-      const float amax_b = (S * a_max <= kd) ? a_max : kd / S;
+      const float amax_b = (S * a_max <= kd) ? a_max : __fdividef(kd, S);
       const float dan = fminf(am, amax_b);
       da[s] = dan;
       const float evx = fmaf(dv, cv, -vx[s]), evy = fmaf(dv, sv, -vy[s]);
       const float eax = fmaf(dan, ca, -ax[s]), eay = fmaf(dan, sa, -ay[s]);
       const float ely = fminf(fmaxf(py[s], y_lb), y_ub) - py[s];
       const float eoy = ey[s] + ely;
+      const float* row = sW + t * ST;
+      const float ex_[3] = {ex[s], evx, eax};
+      const float ey_[3] = {eoy, evy, eay};
 #pragma unroll
-      for (int k = 0; k < NC; ++k) {
-        const float w0 = W0[k * m + t], w1 = W1[k * m + t], w2 = W2[k * m + t];
-        wx[k] = fmaf(w0, ex[s], fmaf(w1, evx, fmaf(w2, eax, wx[k])));
-        wy[k] = fmaf(w0, eoy, fmaf(w1, evy, fmaf(w2, eay, wy[k])));
+      for (int mat = 0; mat < 3; ++mat) {
+#pragma unroll
+        for (int k4 = 0; k4 < NCP; k4 += 4) {
+          const float4 w = *reinterpret_cast<const float4*>(row + mat * NCP + k4);
+          const float wk[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (k4 + u < NC) {
+              wx[k4 + u] = fmaf(wk[u], ex_[mat], wx[k4 + u]);
+              wy[k4 + u] = fmaf(wk[u], ey_[mat], wy[k4 + u]);
+            }
+          }
+        }
       }
     }
 
-    // ---- D: reduce, multipliers, xi-step
+    // ---- D: reduce, multipliers, xi-step in increment form
     const float wl = reduce_scatter<NC>(wx, wy, lane);
     if (valid) {
       if (it > 0) lam = fmaf(hrho, wl, lam);
-      vbuf[lane] = fmaf(rho, wl, lam);
+      vbuf[lane] = fmaf(rho, wl, lam) - dl;
     }
     __syncwarp();
     if (valid) {
-      float acc = xibp;
       const float* vb = vbuf + axis * 16;
+      float acc = 0.f;
 #pragma unroll
       for (int i = 0; i < NC; ++i) acc = fmaf(Mrow[i], vb[i], acc);
-#pragma unroll
-      for (int i = 0; i < NC; ++i) acc = fmaf(MProw[i], axis ? yv[i] : xv[i], acc);
-      xbuf[lane] = acc;
+      dl += acc;
+      xbuf[lane] = dl;
     }
   }
 
@@ -287,16 +362,23 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     r_out[j] = double(r_acc);
     cu_out[j] = double(cu_acc);
   }
-  if (xi_out != nullptr && valid) xi_out[size_t(j) * 2 * NC + axis * NC + kk] = double(xbuf[lane]);
+  if (xi_out != nullptr && valid)
+    xi_out[size_t(j) * 2 * NC + axis * NC + kk] = double(xb_l) + double(dl);
+}
+
+template <int NC, int SLOTS>
+size_t smem_bytes(const Params& prm, int warps) {
+  size_t f = size_t(prm.m) * basis32_stride(NC) + 8 * prm.max_obs + 64 * warps;
+  if (SLOTS > 4) f += size_t(6) * prm.m * warps;
+  return f * sizeof(float);
 }
 
 template <int NC, int SLOTS>
 cudaError_t launch_t(const DevScene* scenes, const Layout* layout, const double* obs,
                      const Tile* tiles, int n_tiles, int warps, const double* p, const Consts& c,
                      const Params& prm, double* xi, double* r, double* cu, cudaStream_t s) {
-  size_t shm = sizeof(float) * (((3 * NC * prm.m + 3) & ~3) + 8 * prm.max_obs + 64 * warps);
-  fused_kernel<NC, SLOTS><<<n_tiles, warps * 32, shm, s>>>(scenes, layout, obs, tiles, p, c, prm,
-                                                           xi, r, cu);
+  fused_kernel<NC, SLOTS><<<n_tiles, warps * 32, smem_bytes<NC, SLOTS>(prm, warps), s>>>(
+      scenes, layout, obs, tiles, p, c, prm, xi, r, cu);
   return cudaGetLastError();
 }
 

@@ -437,7 +437,7 @@ int plan_init(const plan_config* cfg, plan_ctx** out) {
   int st = PLAN_OK;
   auto A = [&](int s) { if (st == PLAN_OK) st = s; };
   A(dalloc(ctx, &k.basis64, size_t(3) * m * n));
-  A(dalloc(ctx, &k.basis32, size_t(3) * m * n));
+  A(dalloc(ctx, &k.basis32, size_t(m) * basis32_stride(n)));
   A(dalloc(ctx, &k.s1_64, size_t(2) * n * (ns + 3)));
   A(dalloc(ctx, &k.s1_32, size_t(2) * n * (ns + 3)));
   A(dalloc(ctx, &k.pj64, size_t(c.max_obs + 1) * 2 * n * (2 * n + 3)));
