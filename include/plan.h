@@ -214,6 +214,24 @@ int plan_get_result(plan_ctx* ctx, int slot, plan_result* out, void* stream);
 int plan_step(plan_ctx* ctx, const plan_scene* scene, plan_cem_state* st, int B,
               plan_result* out, void* stream);
 
+/* ------------------------------------------------------------------- tuning */
+
+/* Shape of the fused FP32 kernel: warps_per_sample in {1, 2, 4} (the lanes
+ * that share one sample's timesteps) and samples_per_cta with
+ * warps_per_sample * samples_per_cta <= 8.  (0, 0) restores the built-in
+ * choice.  Clears the captured graphs of plan_step_resident.  Not a stage of
+ * the paper's method: it only changes how the work is laid out on the GPU. */
+int plan_set_tuning(plan_ctx* ctx, int warps_per_sample, int samples_per_cta);
+
+/* Time every fused-kernel shape on B samples of `scene` (drawn from the
+ * uniform first-iteration distribution), keep the fastest for this context and
+ * return it.  Synchronous on `stream`; must not overlap other work of the
+ * context.  When the environment variable PLAN_TUNE_CACHE names a file, a
+ * result for the same (n_coef, m, n_obs, B) is read from it instead of timing
+ * and new results are appended to it.  With prec = FP64 it returns (0, 0). */
+int plan_autotune(plan_ctx* ctx, const plan_scene* scene, int B, int* warps_per_sample,
+                  int* samples_per_cta, void* stream);
+
 /* ------------------------------------------------------------- single stages */
 
 /* Alg. 1 lines 10-13 for one set of B scores: ConstraintEliteSet = the n_c

@@ -62,7 +62,7 @@ class PlanResult(ctypes.Structure):
 EXPORTS = ("plan_init", "plan_destroy", "plan_status_str", "plan_last_error", "plan_solve",
            "plan_solve_batch", "plan_upload_scenes", "plan_set_state", "plan_get_state",
            "plan_step_resident", "plan_get_result", "plan_step", "plan_select_elites",
-           "plan_update_distribution", "plan_sample")
+           "plan_update_distribution", "plan_sample", "plan_set_tuning", "plan_autotune")
 
 _lib = None
 
@@ -99,6 +99,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "plan_select_elites": (I, [V, V, V, I, I, I, V, V]),
         "plan_update_distribution": (I, [V, V, V, I, V, V, V]),
         "plan_sample": (I, [V, P(PlanScene), V, V, I, I, U64, U64, I, V, V]),
+        "plan_set_tuning": (I, [V, I, I]),
+        "plan_autotune": (I, [V, P(PlanScene), I, P(I), P(I), V]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -257,3 +259,14 @@ def plan_sample(ctx, scene, mu, sigma, fresh: int, l: int, seed: int, step: int,
         *([float(sigma[a][b]) for a in range(d) for b in range(d)] if sigma is not None else [0.0]))
     check(load().plan_sample(ctx, arr, mu_c, sg_c, int(fresh), int(l), int(seed), int(step), int(B),
                              p_ptr, stream), ctx)
+
+
+def plan_set_tuning(ctx, warps_per_sample: int, samples_per_cta: int):
+    check(load().plan_set_tuning(ctx, int(warps_per_sample), int(samples_per_cta)), ctx)
+
+
+def plan_autotune(ctx, scene, B: int, stream: int = 0):
+    arr, keep = make_scenes([scene])
+    w, s = ctypes.c_int(), ctypes.c_int()
+    check(load().plan_autotune(ctx, arr, int(B), ctypes.byref(w), ctypes.byref(s), stream), ctx)
+    return w.value, s.value

@@ -85,8 +85,10 @@ __host__ __device__ constexpr int basis32_stride(int n) {
 cudaError_t build_constants(const Consts& c, const Params& p, cudaStream_t s);
 
 bool fused_supported(int n, int m);
+// wps = warps per sample (1, 2, 4), spc = samples per CTA (spc * wps <= 8)
+bool fused_shape_ok(int wps, int spc);
 cudaError_t launch_fused_f32(const DevScene* scenes, const Layout* layout, const double* obs,
-                             const Tile* tiles, int n_tiles, int warps, const double* p,
+                             const Tile* tiles, int n_tiles, int wps, int spc, const double* p,
                              const Consts& c, const Params& prm, double* xi, double* r,
                              double* cu, cudaStream_t s);
 

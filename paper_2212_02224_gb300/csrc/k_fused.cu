@@ -92,8 +92,23 @@ __device__ __forceinline__ void kin(const float* __restrict__ row, const float (
   }
 }
 
-template <int NC, int SLOTS>
-__global__ void __launch_bounds__(256, 1)
+__device__ __forceinline__ void group_barrier(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// One sample per group of WPS warps (32 WPS lanes); a CTA holds blockDim.x /
+// (32 WPS) groups, each on its own named barrier.  Timestep t = s * 32 WPS +
+// (warp-in-group) * 32 + lane for slot s; lanes with t >= m compute on the
+// last timestep's data and contribute nothing.
+template <int SLOTS, int WPS>
+struct RegCap {
+  // registers per thread: one timestep slot per 32 lanes needs about 70, the
+  // rest is per-sample state; capped so that enough warps stay resident
+  static constexpr int value = SLOTS * WPS >= 8 ? 255 : (SLOTS >= 4 ? 208 : (SLOTS == 2 ? 144 : 96));
+};
+
+template <int NC, int SLOTS, int WPS>
+__global__ void __launch_bounds__(256) __maxnreg__((RegCap<SLOTS, WPS>::value))
 fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ layout,
              const double* __restrict__ obs, const Tile* __restrict__ tiles,
              const double* __restrict__ pin, Consts c, Params prm,
@@ -101,7 +116,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
              double* __restrict__ cu_out) {
   constexpr int NCP = basis32_ncp(NC);
   constexpr int ST = basis32_stride(NC);
-  constexpr bool kRefInRegs = SLOTS <= 4;
+  constexpr int LPS = 32 * WPS;
   extern __shared__ __align__(16) float smem[];
   const int m = prm.m;
   const int ns = prm.n_seg;
@@ -109,11 +124,15 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   const DevScene& sc = scenes[tile.scene];
   const int N = sc.n_obs;
   const int warps = blockDim.x >> 5;
+  const int groups = warps / WPS;
 
   float* sW = smem;                                          // [m][ST]
   float4* sObs = reinterpret_cast<float4*>(smem + m * ST);   // [N][2]
   float* sBuf = reinterpret_cast<float*>(sObs + 2 * N);      // [warps][64]
-  float* sRef = sBuf + 64 * warps;                           // [warps][6][m] (SLOTS > 4)
+  float* sPart = sBuf + 64 * warps;                          // [groups][2][WPS][32]
+  float* sScore = sPart + groups * 2 * WPS * 32;             // [groups][WPS][2]
+  float* sM = sScore + groups * WPS * 2;                     // [2][NC][NC] rows of M
+  float* sRef = sM + 2 * NC * NC;                            // [warps][6][SLOTS][32]
 
   {
     const float4* src = reinterpret_cast<const float4*>(c.basis32);
@@ -121,69 +140,71 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     for (int i = threadIdx.x; i < m * ST / 4; i += blockDim.x) dst[i] = src[i];
   }
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    // scaled trajectory x_o(t) / a = x0/a + (vx/a) t and likewise for y
+    // scaled trajectory x_o(t) / a = x0/a + (vx dt / a) t and likewise for y
     const double* o = obs + size_t(sc.obs_off + i) * 6;
     const double ia = 1.0 / o[4], ib = 1.0 / o[5];
     sObs[2 * i] = make_float4(float(o[0] * ia), float(o[1] * ib), float(o[2] * ia * prm.dt),
                               float(o[3] * ib * prm.dt));
     sObs[2 * i + 1] = make_float4(float(ia), float(ib), float(o[4]), float(o[5]));
   }
+  for (int e = threadIdx.x; e < 2 * NC * NC; e += blockDim.x) {
+    const int ax_ = e / (NC * NC), k_ = (e / NC) % NC, i_ = e % NC;
+    sM[e] = c.pj32[size_t((N * 2 + ax_) * NC + k_) * (2 * NC + 3) + i_];
+  }
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp >= tile.count) return;
-  const int j = layout[tile.scene].off + tile.first + warp;   // global sample index
-  float* xbuf = sBuf + warp * 64;      // slot layout: xi_bar, then delta
+  const int grp = warp / WPS, wig = warp % WPS;
+  if (grp >= tile.count) return;
+  const int gl = wig * 32 + lane;                           // lane within the sample group
+  const int j = layout[tile.scene].off + tile.first + grp;  // global sample index
+  float* xbuf = sBuf + warp * 64;      // slot layout: xi_bar, then delta (per warp copy)
   float* vbuf = xbuf + 32;             // slot layout: lambda + rho w - delta
-  float* ref = sRef + warp * 6 * m;
+  float* part = sPart + grp * 2 * WPS * 32;
+  float* ref = sRef + warp * 6 * SLOTS * 32 + lane;   // ref[(q * SLOTS + s) * 32]
+  const int bar_id = 1 + grp;
 
   // ---- per-lane coefficient slot: Step 1 and the row of M
   const int axis = lane >> 4, kk = lane & 15;
   const bool valid = kk < NC;
-  float Mrow[NC];
+  const float* Mrow = sM + (axis * NC + (valid ? kk : 0)) * NC;
   float xb_l = 0.f;     // xi_bar of this lane's slot
-  {
-    if (valid) {
-      const float* row = c.pj32 + size_t((N * 2 + axis) * NC + kk) * (2 * NC + 3);
-#pragma unroll
-      for (int i = 0; i < NC; ++i) Mrow[i] = row[i];
-      // xi_bar = Gs p_axis + Hs b_axis (x uses the v_d entries, y the y_d entries)
-      const float* s1 = c.s1_32 + size_t(axis * NC + kk) * (ns + 3);
-      const double* pj = pin + size_t(j) * (2 * ns);
-      float xb = 0.f;
-      for (int q = 0; q < ns; ++q) xb = fmaf(s1[q], float(pj[(axis == 0 ? ns : 0) + q]), xb);
-      xb = fmaf(s1[ns], float(sc.ego[axis]), xb);
-      xb = fmaf(s1[ns + 1], float(sc.ego[axis + 2]), xb);
-      xb = fmaf(s1[ns + 2], float(sc.ego[axis + 4]), xb);
-      xb_l = xb;
-      xbuf[lane] = xb;
-    } else {
-#pragma unroll
-      for (int i = 0; i < NC; ++i) Mrow[i] = 0.f;
-    }
+  if (valid) {
+    // xi_bar = Gs p_axis + Hs b_axis (x uses the v_d entries, y the y_d entries)
+    const float* s1 = c.s1_32 + size_t(axis * NC + kk) * (ns + 3);
+    const double* pj = pin + size_t(j) * (2 * ns);
+    float xb = 0.f;
+    for (int q = 0; q < ns; ++q) xb = fmaf(s1[q], float(pj[(axis == 0 ? ns : 0) + q]), xb);
+    xb = fmaf(s1[ns], float(sc.ego[axis]), xb);
+    xb = fmaf(s1[ns + 1], float(sc.ego[axis + 2]), xb);
+    xb = fmaf(s1[ns + 2], float(sc.ego[axis + 4]), xb);
+    xb_l = xb;
+    xbuf[lane] = xb;
   }
   __syncwarp();
 
+  int tcl[SLOTS];     // clamped timestep (valid row address)
+  float act[SLOTS];   // 1 for t < m, else 0
+  float tt[SLOTS];    // timestep index as float (obstacle tables hold per-step rates)
+#pragma unroll
+  for (int s = 0; s < SLOTS; ++s) {
+    const int t = s * LPS + gl;
+    tcl[s] = min(t, m - 1);
+    act[s] = t < m ? 1.f : 0.f;
+    tt[s] = float(t);
+  }
+
   // ---- reference kinematics at xi_bar
-  float rk[kRefInRegs ? SLOTS : 1][6];
   {
     float xv[NC], yv[NC];
 #pragma unroll
     for (int i = 0; i < NC; ++i) { xv[i] = xbuf[i]; yv[i] = xbuf[16 + i]; }
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) {
-      const int t = s * 32 + lane;
-      float o[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      if (t < m) kin<NC>(sW + t * ST, xv, yv, o);
-      if constexpr (kRefInRegs) {
+      float o[6];
+      kin<NC>(sW + tcl[s] * ST, xv, yv, o);
 #pragma unroll
-        for (int q = 0; q < 6; ++q) rk[s][q] = o[q];
-      } else {
-        if (t < m) {
-#pragma unroll
-          for (int q = 0; q < 6; ++q) ref[q * m + t] = o[q];
-        }
-      }
+      for (int q = 0; q < 6; ++q) ref[(q * SLOTS + s) * 32] = o[q];
     }
   }
   __syncwarp();
@@ -196,10 +217,6 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   const float c_max = float(prm.c_max);
   const float kr = float(fabs(sc.kappa_road));
   const float y_lb = float(sc.y_lb), y_ub = float(sc.y_ub);
-
-  float tt[SLOTS];   // time index t (the obstacle table holds per-step velocities)
-#pragma unroll
-  for (int s = 0; s < SLOTS; ++s) tt[s] = float(s * 32 + lane);
 
   float da[SLOTS];
 #pragma unroll
@@ -218,19 +235,10 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     float px[SLOTS], py[SLOTS], vx[SLOTS], vy[SLOTS], ax[SLOTS], ay[SLOTS];
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) {
-      const int t = s * 32 + lane;
-      float o[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      float r6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      if (t < m) {
-        kin<NC>(sW + t * ST, xv, yv, o);
-        if constexpr (kRefInRegs) {
+      float o[6], r6[6];
+      kin<NC>(sW + tcl[s] * ST, xv, yv, o);
 #pragma unroll
-          for (int q = 0; q < 6; ++q) r6[q] = rk[s][q];
-        } else {
-#pragma unroll
-          for (int q = 0; q < 6; ++q) r6[q] = ref[q * m + t];
-        }
-      }
+      for (int q = 0; q < 6; ++q) r6[q] = ref[(q * SLOTS + s) * 32];
       px[s] = r6[0] + o[0]; py[s] = r6[1] + o[1];
       vx[s] = r6[2] + o[2]; vy[s] = r6[3] + o[3];
       ax[s] = r6[4] + o[4]; ay[s] = r6[5] + o[5];
@@ -238,25 +246,30 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
 
     if (it == prm.K) {
       // ---- scoring of xi^K (Alg. 1 line 9 and the Sec. V-A cost)
+      float coll[SLOTS];
 #pragma unroll
-      for (int s = 0; s < SLOTS; ++s) {
-        const int t = s * 32 + lane;
-        if (t >= m) continue;
-        float coll = 0.f;
-        for (int i = 0; i < N; ++i) {
-          const float4 o0 = sObs[2 * i], o1 = sObs[2 * i + 1];
+      for (int s = 0; s < SLOTS; ++s) coll[s] = 0.f;
+#pragma unroll 1
+      for (int i = 0; i < N; ++i) {
+        const float4 o0 = sObs[2 * i], o1 = sObs[2 * i + 1];
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) {
           const float sx = fmaf(px[s], o1.x, -fmaf(o0.z, tt[s], o0.x));
           const float sy = fmaf(py[s], o1.y, -fmaf(o0.w, tt[s], o0.y));
-          coll += fmaxf(0.f, 1.f - fmaf(sx, sx, sy * sy));
+          coll[s] += fmaxf(0.f, 1.f - fmaf(sx, sx, sy * sy));
         }
+      }
+#pragma unroll
+      for (int s = 0; s < SLOTS; ++s) {
         const float sp = fast_sqrt(fmaf(vx[s], vx[s], vy[s] * vy[s]));
         const float am = fast_sqrt(fmaf(ax[s], ax[s], ay[s] * ay[s]));
         const float kap = sp > 0.f ? __fdividef(ay[s] * vx[s] - ax[s] * vy[s], sp * sp * sp) : 0.f;
-        r_acc += coll + fmaxf(0.f, sp - v_max) + fmaxf(0.f, am - a_max) +
-                 fmaxf(0.f, fabsf(kap) - kmax) + fmaxf(0.f, vx[s] * vx[s] * kr - c_max) +
-                 fmaxf(0.f, py[s] - y_ub) + fmaxf(0.f, y_lb - py[s]);
+        const float rt = coll[s] + fmaxf(0.f, sp - v_max) + fmaxf(0.f, am - a_max) +
+                         fmaxf(0.f, fabsf(kap) - kmax) + fmaxf(0.f, vx[s] * vx[s] * kr - c_max) +
+                         fmaxf(0.f, py[s] - y_ub) + fmaxf(0.f, y_lb - py[s]);
         const float dv = sp - v_max;
-        cu_acc = fmaf(dv, dv, cu_acc);
+        r_acc = fmaf(act[s], rt, r_acc);
+        cu_acc = fmaf(act[s] * dv, dv, cu_acc);
       }
       break;
     }
@@ -265,21 +278,25 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     float ex[SLOTS], ey[SLOTS];
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) { ex[s] = 0.f; ey[s] = 0.f; }
+#pragma unroll 1
     for (int i = 0; i < N; ++i) {
       const float4 o0 = sObs[2 * i], o1 = sObs[2 * i + 1];
+      float sx[SLOTS], sy[SLOTS], d2[SLOTS];
+      bool any_in = false;
 #pragma unroll
       for (int s = 0; s < SLOTS; ++s) {
-        const float sx = fmaf(px[s], o1.x, -fmaf(o0.z, tt[s], o0.x));
-        const float sy = fmaf(py[s], o1.y, -fmaf(o0.w, tt[s], o0.y));
-        const float d2 = fmaf(sx, sx, sy * sy);
-        if (d2 < 1.f) {
-          if (d2 > 0.f) {
-            const float g = rsqrtf(d2) - 1.f;
-            ex[s] = fmaf(g * o1.z, sx, ex[s]);
-            ey[s] = fmaf(g * o1.w, sy, ey[s]);
-          } else {
-            ex[s] += o1.z;      // atan2(0, 0) = 0: h = (x_o + a, y_o)
-          }
+        sx[s] = fmaf(px[s], o1.x, -fmaf(o0.z, tt[s], o0.x));
+        sy[s] = fmaf(py[s], o1.y, -fmaf(o0.w, tt[s], o0.y));
+        d2[s] = fmaf(sx[s], sx[s], sy[s] * sy[s]);
+        any_in |= (d2[s] < 1.f) & (act[s] > 0.f);
+      }
+      if (__any_sync(kFull, any_in)) {
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) {
+          const bool in = d2[s] < 1.f, pos = d2[s] > 0.f;
+          const float g = (in && pos) ? rsqrtf(d2[s]) - 1.f : 0.f;
+          ex[s] = fmaf(g * o1.z, sx[s], ex[s]) + ((in && !pos) ? o1.z : 0.f);   // atan2(0,0) = 0
+          ey[s] = fmaf(g * o1.w, sy[s], ey[s]);
         }
       }
     }
@@ -290,14 +307,14 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     for (int k = 0; k < NC; ++k) { wx[k] = 0.f; wy[k] = 0.f; }
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) {
-      const int t = s * 32 + lane;
-      if (t >= m) continue;
       const float v2 = fmaf(vx[s], vx[s], vy[s] * vy[s]);
-      float cv = 1.f, sv = 0.f, sp = 0.f;
-      if (v2 > 0.f) { const float rv = rsqrtf(v2); cv = vx[s] * rv; sv = vy[s] * rv; sp = v2 * rv; }
+      const bool vp = v2 > 0.f;
+      const float rv = rsqrtf(v2);
+      const float cv = vp ? vx[s] * rv : 1.f, sv = vp ? vy[s] * rv : 0.f, sp = vp ? v2 * rv : 0.f;
       const float a2 = fmaf(ax[s], ax[s], ay[s] * ay[s]);
-      float ca = 1.f, sa = 0.f, am = 0.f;
-      if (a2 > 0.f) { const float ra = rsqrtf(a2); ca = ax[s] * ra; sa = ay[s] * ra; am = a2 * ra; }
+      const bool ap = a2 > 0.f;
+      const float ra = rsqrtf(a2);
+      const float ca = ap ? ax[s] * ra : 1.f, sa = ap ? ay[s] * ra : 0.f, am = ap ? a2 * ra : 0.f;
       const float S = fabsf(sa * cv - ca * sv);               // |sin(alpha_a - alpha_v)|
       const float dap = (it == 0) ? fminf(am, a_max) : da[s];
       const float vmin_b = fmaxf(v_min, fast_sqrt(dap * S * inv_kmax));
@@ -311,12 +328,14 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       const float amax_b = (S * a_max <= kd) ? a_max : __fdividef(kd, S);
       const float dan = fminf(am, amax_b);
       da[s] = dan;
-      const float evx = fmaf(dv, cv, -vx[s]), evy = fmaf(dv, sv, -vy[s]);
-      const float eax = fmaf(dan, ca, -ax[s]), eay = fmaf(dan, sa, -ay[s]);
+      const float A = act[s];
+      const float evx = A * fmaf(dv, cv, -vx[s]), evy = A * fmaf(dv, sv, -vy[s]);
+      const float eax = A * fmaf(dan, ca, -ax[s]), eay = A * fmaf(dan, sa, -ay[s]);
       const float ely = fminf(fmaxf(py[s], y_lb), y_ub) - py[s];
-      const float eoy = ey[s] + ely;
-      const float* row = sW + t * ST;
-      const float ex_[3] = {ex[s], evx, eax};
+      const float exs = A * ex[s];
+      const float eoy = A * (ey[s] + ely);
+      const float* row = sW + tcl[s] * ST;
+      const float ex_[3] = {exs, evx, eax};
       const float ey_[3] = {eoy, evy, eay};
 #pragma unroll
       for (int mat = 0; mat < 3; ++mat) {
@@ -336,7 +355,16 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     }
 
     // ---- D: reduce, multipliers, xi-step in increment form
-    const float wl = reduce_scatter<NC>(wx, wy, lane);
+    float wl = reduce_scatter<NC>(wx, wy, lane);
+    if constexpr (WPS > 1) {
+      float* pb = part + (it & 1) * WPS * 32;
+      pb[wig * 32 + lane] = wl;
+      group_barrier(bar_id, LPS);
+      float tot = 0.f;
+#pragma unroll
+      for (int w = 0; w < WPS; ++w) tot += pb[w * 32 + lane];
+      wl = tot;
+    }
     if (valid) {
       if (it > 0) lam = fmaf(hrho, wl, lam);
       vbuf[lane] = fmaf(rho, wl, lam) - dl;
@@ -344,10 +372,13 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     __syncwarp();
     if (valid) {
       const float* vb = vbuf + axis * 16;
-      float acc = 0.f;
+      float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll
-      for (int i = 0; i < NC; ++i) acc = fmaf(Mrow[i], vb[i], acc);
-      dl += acc;
+      for (int i = 0; i < NC; i += 2) {
+        acc0 = fmaf(Mrow[i], vb[i], acc0);
+        if (i + 1 < NC) acc1 = fmaf(Mrow[i + 1], vb[i + 1], acc1);
+      }
+      dl += acc0 + acc1;
       xbuf[lane] = dl;
     }
   }
@@ -358,64 +389,94 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     r_acc += __shfl_xor_sync(kFull, r_acc, o);
     cu_acc += __shfl_xor_sync(kFull, cu_acc, o);
   }
-  if (lane == 0) {
-    r_out[j] = double(r_acc);
-    cu_out[j] = double(cu_acc);
+  if constexpr (WPS > 1) {
+    float* sc2 = sScore + grp * WPS * 2;
+    if (lane == 0) { sc2[2 * wig] = r_acc; sc2[2 * wig + 1] = cu_acc; }
+    group_barrier(bar_id, LPS);
+    r_acc = 0.f;
+    cu_acc = 0.f;
+#pragma unroll
+    for (int w = 0; w < WPS; ++w) { r_acc += sc2[2 * w]; cu_acc += sc2[2 * w + 1]; }
   }
-  if (xi_out != nullptr && valid)
-    xi_out[size_t(j) * 2 * NC + axis * NC + kk] = double(xb_l) + double(dl);
+  if (wig == 0) {
+    if (lane == 0) {
+      r_out[j] = double(r_acc);
+      cu_out[j] = double(cu_acc);
+    }
+    if (xi_out != nullptr && valid)
+      xi_out[size_t(j) * 2 * NC + axis * NC + kk] = double(xb_l) + double(dl);
+  }
 }
 
-template <int NC, int SLOTS>
-size_t smem_bytes(const Params& prm, int warps) {
-  size_t f = size_t(prm.m) * basis32_stride(NC) + 8 * prm.max_obs + 64 * warps;
-  if (SLOTS > 4) f += size_t(6) * prm.m * warps;
+template <int NC, int SLOTS, int WPS>
+size_t smem_bytes(const Params& prm, int spc) {
+  const int warps = spc * WPS;
+  size_t f = size_t(prm.m) * basis32_stride(NC) + 8 * prm.max_obs + 64 * warps +
+             spc * 2 * WPS * 32 + spc * WPS * 2 + 2 * NC * NC + size_t(6) * SLOTS * 32 * warps;
   return f * sizeof(float);
 }
 
-template <int NC, int SLOTS>
+template <int NC, int SLOTS, int WPS>
 cudaError_t launch_t(const DevScene* scenes, const Layout* layout, const double* obs,
-                     const Tile* tiles, int n_tiles, int warps, const double* p, const Consts& c,
+                     const Tile* tiles, int n_tiles, int spc, const double* p, const Consts& c,
                      const Params& prm, double* xi, double* r, double* cu, cudaStream_t s) {
-  fused_kernel<NC, SLOTS><<<n_tiles, warps * 32, smem_bytes<NC, SLOTS>(prm, warps), s>>>(
+  fused_kernel<NC, SLOTS, WPS><<<n_tiles, spc * WPS * 32, smem_bytes<NC, SLOTS, WPS>(prm, spc), s>>>(
       scenes, layout, obs, tiles, p, c, prm, xi, r, cu);
   return cudaGetLastError();
 }
 
-template <int NC, int SLOTS>
+template <int NC, int SLOTS, int WPS>
 void set_attr() {
-  cudaFuncSetAttribute(fused_kernel<NC, SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(fused_kernel<NC, SLOTS, WPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        200 * 1024);
+}
+
+template <int NC>
+void set_attr_nc() {
+  set_attr<NC, 4, 1>(); set_attr<NC, 8, 1>();
+  set_attr<NC, 2, 2>(); set_attr<NC, 4, 2>();
+  set_attr<NC, 1, 4>(); set_attr<NC, 2, 4>();
+}
+
+template <int NC>
+cudaError_t launch_nc(int wps, const DevScene* scenes, const Layout* layout, const double* obs,
+                      const Tile* tiles, int n_tiles, int spc, const double* p, const Consts& c,
+                      const Params& prm, double* xi, double* r, double* cu, cudaStream_t s) {
+  const int m = prm.m;
+#define PLAN_L(SL, W) \
+  launch_t<NC, SL, W>(scenes, layout, obs, tiles, n_tiles, spc, p, c, prm, xi, r, cu, s)
+  if (wps == 1) return m <= 128 ? PLAN_L(4, 1) : PLAN_L(8, 1);
+  if (wps == 2) return m <= 128 ? PLAN_L(2, 2) : PLAN_L(4, 2);
+  if (wps == 4) return m <= 128 ? PLAN_L(1, 4) : PLAN_L(2, 4);
+#undef PLAN_L
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
 void fused_setup() {
-  set_attr<8, 4>(); set_attr<8, 8>();
-  set_attr<11, 4>(); set_attr<11, 8>();
-  set_attr<16, 4>(); set_attr<16, 8>();
+  set_attr_nc<8>();
+  set_attr_nc<11>();
+  set_attr_nc<16>();
 }
 
 bool fused_supported(int n, int m) {
   return (n == 8 || n == 11 || n == 16) && m >= 2 && m <= 256;
 }
 
+bool fused_shape_ok(int wps, int spc) {
+  return (wps == 1 || wps == 2 || wps == 4) && spc >= 1 && spc * wps <= 8;
+}
+
 cudaError_t launch_fused_f32(const DevScene* scenes, const Layout* layout, const double* obs,
-                             const Tile* tiles, int n_tiles, int warps, const double* p,
+                             const Tile* tiles, int n_tiles, int wps, int spc, const double* p,
                              const Consts& c, const Params& prm, double* xi, double* r,
                              double* cu, cudaStream_t s) {
   if (n_tiles == 0) return cudaSuccess;
-  const bool small = prm.m <= 128;
-#define PLAN_FUSED_CASE(NC_)                                                                \
-  if (prm.n == NC_)                                                                          \
-    return small ? launch_t<NC_, 4>(scenes, layout, obs, tiles, n_tiles, warps, p, c, prm,  \
-                                    xi, r, cu, s)                                            \
-                 : launch_t<NC_, 8>(scenes, layout, obs, tiles, n_tiles, warps, p, c, prm,  \
-                                    xi, r, cu, s);
-  PLAN_FUSED_CASE(8)
-  PLAN_FUSED_CASE(11)
-  PLAN_FUSED_CASE(16)
-#undef PLAN_FUSED_CASE
+  if (!fused_shape_ok(wps, spc)) return cudaErrorInvalidValue;
+  if (prm.n == 8) return launch_nc<8>(wps, scenes, layout, obs, tiles, n_tiles, spc, p, c, prm, xi, r, cu, s);
+  if (prm.n == 11) return launch_nc<11>(wps, scenes, layout, obs, tiles, n_tiles, spc, p, c, prm, xi, r, cu, s);
+  if (prm.n == 16) return launch_nc<16>(wps, scenes, layout, obs, tiles, n_tiles, spc, p, c, prm, xi, r, cu, s);
   return cudaErrorInvalidValue;
 }
 

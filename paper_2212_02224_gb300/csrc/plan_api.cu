@@ -1,6 +1,8 @@
 // C ABI of the planner: context, device arena, staging, launch sequences and
 // CUDA-graph capture of whole Alg. 1 runs.  See include/plan.h.
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -43,7 +45,7 @@ struct plan_ctx {
   Params prm{};
   Consts c{};
   int device = 0;
-  int fused_warps = 0;     // 0 = automatic
+  int tune_wps = 0, tune_spc = 0;   // fused-kernel shape; 0 = automatic
   cudaStream_t internal = nullptr;
   cudaStream_t capture = nullptr;
 
@@ -243,11 +245,21 @@ void make_tiles(const std::vector<int>& B, int warps, std::vector<Tile>* tiles,
   }
 }
 
-int pick_warps(const plan_ctx* ctx, int total_B) {
-  if (ctx->fused_warps > 0) return ctx->fused_warps;
-  // few samples: small CTAs so every SM gets work; many: 4 warps per CTA
-  return total_B <= 8192 ? 1 : 4;
+struct Shape {
+  int wps, spc;
+};
+
+// Fused-kernel shape: explicit tuning if set, else a heuristic that keeps
+// about 16 warps per SM busy for small batches.
+Shape pick_shape(const plan_ctx* ctx, int total_B) {
+  if (ctx->tune_wps > 0 && ctx->tune_spc > 0) return Shape{ctx->tune_wps, ctx->tune_spc};
+  const bool long_horizon = ctx->cfg.m > 128;
+  if (total_B <= 1024) return Shape{2, 1};
+  if (total_B <= 8192 || long_horizon) return Shape{2, 2};
+  return Shape{1, 4};
 }
+
+int pick_warps(const plan_ctx* ctx, int total_B) { return pick_shape(ctx, total_B).spc; }
 
 // Upload scenes (geometry + obstacles) and the layout of B into `set`.
 int upload(plan_ctx* ctx, SceneSet& set, const plan_scene* scenes, int S, const std::vector<int>* B,
@@ -294,11 +306,13 @@ int upload(plan_ctx* ctx, SceneSet& set, const plan_scene* scenes, int S, const 
 
 // Lower-level solve of all samples described by `set` (Alg. 1 lines 6-9).
 cudaError_t run_solve(plan_ctx* ctx, const SceneSet& set, const SceneSet& lay, int n_tiles,
-                      int warps, int total_B, const double* p, double* xi, double* r, double* cu,
+                      int total_B, const double* p, double* xi, double* r, double* cu,
                       cudaStream_t s) {
-  if (ctx->cfg.prec == PLAN_PREC_FP32)
-    return launch_fused_f32(set.scenes, lay.layout, set.obs, lay.tiles, n_tiles, warps, p, ctx->c,
-                            ctx->prm, xi, r, cu, s);
+  if (ctx->cfg.prec == PLAN_PREC_FP32) {
+    const Shape sh = pick_shape(ctx, total_B);
+    return launch_fused_f32(set.scenes, lay.layout, set.obs, lay.tiles, n_tiles, sh.wps, sh.spc,
+                            p, ctx->c, ctx->prm, xi, r, cu, s);
+  }
   return launch_plain64(set.scenes, lay.layout, lay.sample_scene, set.obs, total_B, p, ctx->c,
                         ctx->prm, ctx->pw, xi, r, cu, s);
 }
@@ -492,9 +506,8 @@ int plan_solve_batch(plan_ctx* ctx, const plan_scene* scenes, const int* B, int 
   if (!p || !resid || !cu) return fail(ctx, PLAN_EINVAL, "p, resid and cu must be non-NULL");
   CU(ctx, cudaSetDevice(ctx->device));
   TRY(upload(ctx, ctx->tr, scenes, S, &Bv, s, nullptr));
-  const int warps = pick_warps(ctx, int(total));
-  CU(ctx, run_solve(ctx, ctx->tr, ctx->tr, n_tiles_of(Bv, warps), warps, int(total), p, xi, resid,
-                    cu, s));
+  const int spc = pick_warps(ctx, int(total));
+  CU(ctx, run_solve(ctx, ctx->tr, ctx->tr, n_tiles_of(Bv, spc), int(total), p, xi, resid, cu, s));
   return PLAN_OK;
 }
 
@@ -603,8 +616,7 @@ int plan_step_resident(plan_ctx* ctx, const int* B, int S, void* stream) {
     TRY(dalloc(ctx, &e.set.sample_scene, size_t(total)));
     TRY(upload(ctx, e.set, nullptr, 0, &Bv, ctx->internal, nullptr));
     CU(ctx, cudaStreamSynchronize(ctx->internal));
-    const int warps = pick_warps(ctx, int(total));
-    const int nt = n_tiles_of(Bv, warps);
+    const int nt = n_tiles_of(Bv, pick_warps(ctx, int(total)));
     cudaGraph_t graph = nullptr;
     CU(ctx, cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal));
     cudaError_t ce = cudaSuccess;
@@ -612,7 +624,7 @@ int plan_step_resident(plan_ctx* ctx, const int* B, int S, void* stream) {
       ce = launch_sample(e.set.scenes, e.set.layout, ctx->cem, S, max_B, l, ctx->prm, ctx->p,
                          ctx->capture);
       if (ce == cudaSuccess)
-        ce = run_solve(ctx, e.set, e.set, nt, warps, int(total), ctx->p, ctx->xi, ctx->r, ctx->cu,
+        ce = run_solve(ctx, e.set, e.set, nt, int(total), ctx->p, ctx->xi, ctx->r, ctx->cu,
                        ctx->capture);
       if (ce == cudaSuccess)
         ce = launch_select_update(e.set.layout, ctx->cem, S, l, ctx->prm, ctx->p, ctx->xi, ctx->r,
@@ -703,6 +715,104 @@ int plan_sample(plan_ctx* ctx, const plan_scene* scene, const double* mu, const 
   CU(ctx, cudaMemcpyAsync(ctx->cem_tmp, ctx->stage, sizeof c, cudaMemcpyHostToDevice, s));
   TRY(stage_release(ctx, s));
   CU(ctx, launch_sample(ctx->tr.scenes, ctx->tr.layout, ctx->cem_tmp, 1, B, l, ctx->prm, p, s));
+  return PLAN_OK;
+}
+
+int plan_set_tuning(plan_ctx* ctx, int warps_per_sample, int samples_per_cta) {
+  if (!ctx) return PLAN_EINVAL;
+  const bool automatic = warps_per_sample == 0 && samples_per_cta == 0;
+  if (!automatic && !fused_shape_ok(warps_per_sample, samples_per_cta))
+    return fail(ctx, PLAN_EINVAL, "need warps_per_sample in {1,2,4} and wps * spc <= 8");
+  CU(ctx, cudaSetDevice(ctx->device));
+  CU(ctx, cudaStreamSynchronize(ctx->internal));
+  for (auto& g : ctx->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  ctx->graphs.clear();   // their layout buffers stay in the arena until plan_destroy
+  ctx->tune_wps = warps_per_sample;
+  ctx->tune_spc = samples_per_cta;
+  return PLAN_OK;
+}
+
+int plan_autotune(plan_ctx* ctx, const plan_scene* scene, int B, int* wps_out, int* spc_out,
+                  void* stream) {
+  if (!ctx) return PLAN_EINVAL;
+  if (!scene || !wps_out || !spc_out) return fail(ctx, PLAN_EINVAL, "NULL argument");
+  if (B < 1 || B > ctx->cfg.max_samples) return fail(ctx, PLAN_ECAPACITY, "B out of range");
+  TRY(check_scene(ctx, scene, 0));
+  *wps_out = 0;
+  *spc_out = 0;
+  if (ctx->cfg.prec != PLAN_PREC_FP32) return PLAN_OK;
+  const char* cache = std::getenv("PLAN_TUNE_CACHE");
+  if (cache && *cache) {
+    if (FILE* f = std::fopen(cache, "r")) {
+      int n, m, N, b, w, sp;
+      double ms;
+      int found_w = 0, found_s = 0;
+      while (std::fscanf(f, "%d %d %d %d %d %d %lf", &n, &m, &N, &b, &w, &sp, &ms) == 7)
+        if (n == ctx->cfg.n_coef && m == ctx->cfg.m && N == scene->n_obs && b == B &&
+            fused_shape_ok(w, sp)) { found_w = w; found_s = sp; }
+      std::fclose(f);
+      if (found_w) {
+        TRY(plan_set_tuning(ctx, found_w, found_s));
+        *wps_out = found_w;
+        *spc_out = found_s;
+        return PLAN_OK;
+      }
+    }
+  }
+  CU(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // samples from the uniform first-iteration distribution
+  plan_cem_state st{};
+  st.fresh = 1;
+  st.seed = 0x5eedull;
+  TRY(plan_sample(ctx, scene, nullptr, nullptr, 1, 1, st.seed, 0, B, ctx->p, stream));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CU(ctx, cudaEventCreate(&e0));
+  CU(ctx, cudaEventCreate(&e1));
+  const int cand[][2] = {{1, 1}, {1, 2}, {1, 4}, {1, 8}, {2, 1}, {2, 2}, {2, 4}, {4, 1}, {4, 2}};
+  const int save_w = ctx->tune_wps, save_s = ctx->tune_spc;
+  int best_w = 0, best_s = 0;
+  float best = 1e30f;
+  std::vector<int> Bv{B};
+  int st_code = PLAN_OK;
+  for (const auto& cnd : cand) {
+    ctx->tune_wps = cnd[0];
+    ctx->tune_spc = cnd[1];
+    st_code = upload(ctx, ctx->tr, scene, 1, &Bv, s, nullptr);
+    if (st_code != PLAN_OK) break;
+    const int nt = n_tiles_of(Bv, cnd[1]);
+    float times[3];
+    cudaError_t ce = run_solve(ctx, ctx->tr, ctx->tr, nt, B, ctx->p, nullptr, ctx->r, ctx->cu, s);
+    for (int rep = 0; rep < 3 && ce == cudaSuccess; ++rep) {
+      cudaEventRecord(e0, s);
+      ce = run_solve(ctx, ctx->tr, ctx->tr, nt, B, ctx->p, nullptr, ctx->r, ctx->cu, s);
+      cudaEventRecord(e1, s);
+      if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&times[rep], e0, e1);
+    }
+    if (ce != cudaSuccess) {
+      st_code = fail(ctx, PLAN_ECUDA, "autotune launch failed: %s", cudaGetErrorString(ce));
+      break;
+    }
+    std::sort(times, times + 3);
+    if (times[1] < best) { best = times[1]; best_w = cnd[0]; best_s = cnd[1]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->tune_wps = save_w;
+  ctx->tune_spc = save_s;
+  if (st_code != PLAN_OK) return st_code;
+  TRY(plan_set_tuning(ctx, best_w, best_s));
+  if (cache && *cache) {
+    if (FILE* f = std::fopen(cache, "a")) {
+      std::fprintf(f, "%d %d %d %d %d %d %.6f\n", ctx->cfg.n_coef, ctx->cfg.m, scene->n_obs, B, best_w,
+                   best_s, double(best));
+      std::fclose(f);
+    }
+  }
+  *wps_out = best_w;
+  *spc_out = best_s;
   return PLAN_OK;
 }
 

@@ -104,6 +104,13 @@ class Planner:
         return dict(p=list(r.p[:self.d_p]), xi=list(r.xi[:2 * self.n]), cost=r.cost, resid=r.resid,
                     cu=r.cu, index=r.index, mu=mu1, sigma=sg1, step=st.episode_step)
 
+    # -------------------------------------------------------------- tuning
+    def set_tuning(self, warps_per_sample: int, samples_per_cta: int):
+        B.plan_set_tuning(self.ctx, warps_per_sample, samples_per_cta)
+
+    def autotune(self, scene, Bn: int, stream=None):
+        return B.plan_autotune(self.ctx, scene, Bn, _stream(stream))
+
     # -------------------------------------------------------------- single stages
     def select_elites(self, r: torch.Tensor, cu: torch.Tensor, n_c: int, q: int, stream=None):
         Bn = r.shape[0]

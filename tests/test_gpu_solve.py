@@ -120,3 +120,53 @@ def test_capacity_and_argument_errors():
     xi, r, cu = pl.solve(sc, p[:0].contiguous())   # B = 0 is a no-op
     assert r.numel() == 0
     pl.close()
+
+
+SHAPES = [(1, 1), (1, 4), (2, 1), (2, 2), (4, 1), (4, 2)]
+
+
+@pytest.fixture(scope="module")
+def dense_case():
+    prm, sc, _ = sg.workload(1, inner_iters=60)
+    p = sg.make_samples(404, sc, 45, prm.n_seg)
+    return prm, sc, p, _oracle(prm, sc, p)
+
+
+@pytest.mark.parametrize("wps,spc", SHAPES)
+def test_fused_kernel_shapes(wps, spc, dense_case):
+    """Every warps-per-sample / samples-per-CTA shape gives oracle parity."""
+    prm, sc, p, ref = dense_case
+    pl = planner(prm, "fp32", max_obs=16, max_samples=len(p))
+    pl.set_tuning(wps, spc)
+    xi, r, cu = pl.solve(sc, to_dev(p))
+    torch.cuda.synchronize()
+    compare("fp32", prm, xi.cpu().numpy(), r.cpu().numpy(), cu.cpu().numpy(), *ref)
+    pl.close()
+
+
+@pytest.mark.parametrize("wps", [1, 2, 4])
+def test_long_and_ragged_horizons_per_shape(wps):
+    for m, n in ((37, 8), (200, 16)):
+        prm = sg.Params(m=m, n_coef=n, inner_iters=25)
+        sc = scene_with(40 + m, 4, 7, obs_x=(8.0, 60.0))
+        p = sg.make_samples(41, sc, 9, 1)
+        pl = planner(prm, "fp32", max_obs=8, max_samples=9)
+        pl.set_tuning(wps, 1)
+        xi, r, cu = pl.solve(sc, to_dev(p))
+        torch.cuda.synchronize()
+        compare("fp32", prm, xi.cpu().numpy(), r.cpu().numpy(), cu.cpu().numpy(), *_oracle(prm, sc, p))
+        pl.close()
+
+
+def test_autotune_returns_a_valid_shape(tmp_path, monkeypatch):
+    prm, sc, B = sg.workload(1, inner_iters=10)
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("PLAN_TUNE_CACHE", str(cache))
+    pl = planner(prm, "fp32", max_obs=16, max_samples=256)
+    w, s = pl.autotune(sc, 256)
+    assert (w, s) in {(1, 1), (1, 2), (1, 4), (1, 8), (2, 1), (2, 2), (2, 4), (4, 1), (4, 2)}
+    assert cache.read_text().split()[4:6] == [str(w), str(s)]
+    assert pl.autotune(sc, 256) == (w, s)          # served from the cache file
+    with pytest.raises(binding.PlanError):
+        pl.set_tuning(3, 1)
+    pl.close()
