@@ -168,6 +168,7 @@ def gpu_arm(args):
 
     # ---- value: resident inputs, graph-captured cycle
     pl = Planner(prm, prec="fp32", max_obs=16, max_samples=B)
+    shape = pl.autotune(sc, B)          # fused-kernel shape for this workload (setup, untimed)
     pl.upload([sc])
     pl.set_state(0, seed=1234 + rank)
     for _ in range(args.warmup):
@@ -269,7 +270,8 @@ def gpu_arm(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "parallelism": f"replicas{world}",
                        "l2": "flushed before every timed step (256 MiB write)",
-                       "graph": "whole cycle captured as one CUDA graph"},
+                       "graph": "whole cycle captured as one CUDA graph",
+                       "fused_shape": {"warps_per_sample": shape[0], "samples_per_cta": shape[1]}},
             "latency_ms": {"p50": statistics.median(step_ms),
                            "p99": float(np.percentile(step_ms, 99)),
                            "e2e_p50": statistics.median(e2e_ms),

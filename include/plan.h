@@ -216,10 +216,9 @@ int plan_step(plan_ctx* ctx, const plan_scene* scene, plan_cem_state* st, int B,
 
 /* ------------------------------------------------------------------- tuning */
 
-/* Shape of the fused FP32 kernel: warps_per_sample in {1, 2, 4} (the lanes
- * that share one sample's timesteps) and samples_per_cta with
- * warps_per_sample * samples_per_cta <= 8.  (0, 0) restores the built-in
- * choice.  Clears the captured graphs of plan_step_resident.  Not a stage of
+/* Shape of the fused FP32 kernel: warps_per_sample (the warps that share one
+ * sample's timesteps) and samples_per_cta; valid shapes are (1, 1..8), (2, 1)
+ * and (4, 1).  (0, 0) restores the built-in choice.  Clears the captured graphs of plan_step_resident.  Not a stage of
  * the paper's method: it only changes how the work is laid out on the GPU. */
 int plan_set_tuning(plan_ctx* ctx, int warps_per_sample, int samples_per_cta);
 

@@ -92,8 +92,11 @@ __device__ __forceinline__ void kin(const float* __restrict__ row, const float (
   }
 }
 
-__device__ __forceinline__ void group_barrier(int id, int nthreads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+// Barrier of the warps that share one sample.  With more than one warp per
+// sample a CTA holds exactly one sample group, so a fixed barrier id is used
+// (a run-time id would make the compiler reserve all 16 barriers per CTA).
+__device__ __forceinline__ void group_barrier(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
 // One sample per group of WPS warps (32 WPS lanes); a CTA holds blockDim.x /
@@ -162,7 +165,6 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   float* vbuf = xbuf + 32;             // slot layout: lambda + rho w - delta
   float* part = sPart + grp * 2 * WPS * 32;
   float* ref = sRef + warp * 6 * SLOTS * 32 + lane;   // ref[(q * SLOTS + s) * 32]
-  const int bar_id = 1 + grp;
 
   // ---- per-lane coefficient slot: Step 1 and the row of M
   const int axis = lane >> 4, kk = lane & 15;
@@ -359,7 +361,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     if constexpr (WPS > 1) {
       float* pb = part + (it & 1) * WPS * 32;
       pb[wig * 32 + lane] = wl;
-      group_barrier(bar_id, LPS);
+      group_barrier(LPS);
       float tot = 0.f;
 #pragma unroll
       for (int w = 0; w < WPS; ++w) tot += pb[w * 32 + lane];
@@ -392,7 +394,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   if constexpr (WPS > 1) {
     float* sc2 = sScore + grp * WPS * 2;
     if (lane == 0) { sc2[2 * wig] = r_acc; sc2[2 * wig + 1] = cu_acc; }
-    group_barrier(bar_id, LPS);
+    group_barrier(LPS);
     r_acc = 0.f;
     cu_acc = 0.f;
 #pragma unroll
@@ -429,6 +431,11 @@ template <int NC, int SLOTS, int WPS>
 void set_attr() {
   cudaFuncSetAttribute(fused_kernel<NC, SLOTS, WPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        200 * 1024);
+  // every CTA stages the basis: ask for the largest shared-memory carveout so
+  // that occupancy is bounded by registers, not by the L1 / shared split
+  cudaFuncSetAttribute(fused_kernel<NC, SLOTS, WPS>,
+                       cudaFuncAttributePreferredSharedMemoryCarveout,
+                       int(cudaSharedmemCarveoutMaxShared));
 }
 
 template <int NC>
@@ -465,7 +472,8 @@ bool fused_supported(int n, int m) {
 }
 
 bool fused_shape_ok(int wps, int spc) {
-  return (wps == 1 || wps == 2 || wps == 4) && spc >= 1 && spc * wps <= 8;
+  if (wps == 1) return spc >= 1 && spc <= 8;
+  return (wps == 2 || wps == 4) && spc == 1;
 }
 
 cudaError_t launch_fused_f32(const DevScene* scenes, const Layout* layout, const double* obs,
