@@ -73,11 +73,13 @@ class PlanError(RuntimeError):
         self.status = status
 
 
-def load(path: str = LIB_PATH) -> ctypes.CDLL:
-    """Load libplan.so (built by build.py); raises if it is missing."""
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libplan.so (built by build.py, or the file named by the environment
+    variable PLAN_LIBRARY); raises if it is missing."""
     global _lib
     if _lib is not None:
         return _lib
+    path = path or os.environ.get("PLAN_LIBRARY") or LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"planner CUDA library not built: {path} is missing "
                            "(run paper_2212_02224_gb300/build.py)")

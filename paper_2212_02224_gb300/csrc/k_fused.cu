@@ -132,8 +132,10 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   float* sW = smem;                                          // [m][ST]
   float4* sObs = reinterpret_cast<float4*>(smem + m * ST);   // [N][2]
   float* sBuf = reinterpret_cast<float*>(sObs + 2 * N);      // [warps][64]
-  float* sPart = sBuf + 64 * warps;                          // [groups][2][WPS][32]
-  float* sScore = sPart + groups * 2 * WPS * 32;             // [groups][WPS][2]
+  constexpr int RS = 32 * WPS + 4;                           // row stride of the reduction table
+  constexpr int RED = (WPS > 1 ? 2 : 1) * 2 * NC * RS;       // floats per sample group
+  float* sRedAll = sBuf + 64 * warps;                        // [groups][RED]
+  float* sScore = sRedAll + groups * RED;                    // [groups][WPS][2]
   float* sM = sScore + groups * WPS * 2;                     // [2][NC][NC] rows of M
   float* sRef = sM + 2 * NC * NC;                            // [warps][6][SLOTS][32]
 
@@ -163,7 +165,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   const int j = layout[tile.scene].off + tile.first + grp;  // global sample index
   float* xbuf = sBuf + warp * 64;      // slot layout: xi_bar, then delta (per warp copy)
   float* vbuf = xbuf + 32;             // slot layout: lambda + rho w - delta
-  float* part = sPart + grp * 2 * WPS * 32;
+  float* sRed = sRedAll + grp * RED;
   float* ref = sRef + warp * 6 * SLOTS * 32 + lane;   // ref[(q * SLOTS + s) * 32]
 
   // ---- per-lane coefficient slot: Step 1 and the row of M
@@ -231,7 +233,14 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     __syncwarp();
     float xv[NC], yv[NC];
 #pragma unroll
-    for (int i = 0; i < NC; ++i) { xv[i] = xbuf[i]; yv[i] = xbuf[16 + i]; }
+    for (int i4 = 0; i4 < NC; i4 += 4) {
+      const float4 a = *reinterpret_cast<const float4*>(xbuf + i4);
+      const float4 b = *reinterpret_cast<const float4*>(xbuf + 16 + i4);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i4 + u < NC) { xv[i4 + u] = av[u]; yv[i4 + u] = bv[u]; }
+    }
 
     // ---- A: kinematics at the lane's timesteps
     float px[SLOTS], py[SLOTS], vx[SLOTS], vy[SLOTS], ax[SLOTS], ay[SLOTS];
@@ -276,29 +285,52 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       break;
     }
 
-    // ---- B: obstacle projection, accumulated residual sum_i (h_o,i - p)
+    // ---- B: obstacle projection, accumulated residual sum_i (h_o,i - p).
+    // A branch-free pass marks, per slot, the obstacles whose ellipse holds the
+    // point (d < 1); only those get the correction (x - x_o, y - y_o)(1/d - 1).
     float ex[SLOTS], ey[SLOTS];
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) { ex[s] = 0.f; ey[s] = 0.f; }
-#pragma unroll 1
-    for (int i = 0; i < N; ++i) {
-      const float4 o0 = sObs[2 * i], o1 = sObs[2 * i + 1];
-      float sx[SLOTS], sy[SLOTS], d2[SLOTS];
-      bool any_in = false;
+    for (int i0 = 0; i0 < N; i0 += 32) {
+      const int nc = min(32, N - i0);
+      unsigned ins[SLOTS];
 #pragma unroll
-      for (int s = 0; s < SLOTS; ++s) {
-        sx[s] = fmaf(px[s], o1.x, -fmaf(o0.z, tt[s], o0.x));
-        sy[s] = fmaf(py[s], o1.y, -fmaf(o0.w, tt[s], o0.y));
-        d2[s] = fmaf(sx[s], sx[s], sy[s] * sy[s]);
-        any_in |= (d2[s] < 1.f) & (act[s] > 0.f);
-      }
-      if (__any_sync(kFull, any_in)) {
+      for (int s = 0; s < SLOTS; ++s) ins[s] = 0u;
+#pragma unroll 4
+      for (int ii = 0; ii < nc; ++ii) {
+        const float4 o0 = sObs[2 * (i0 + ii)], o1 = sObs[2 * (i0 + ii) + 1];
 #pragma unroll
         for (int s = 0; s < SLOTS; ++s) {
-          const bool in = d2[s] < 1.f, pos = d2[s] > 0.f;
-          const float g = (in && pos) ? rsqrtf(d2[s]) - 1.f : 0.f;
-          ex[s] = fmaf(g * o1.z, sx[s], ex[s]) + ((in && !pos) ? o1.z : 0.f);   // atan2(0,0) = 0
-          ey[s] = fmaf(g * o1.w, sy[s], ey[s]);
+          const float sx = fmaf(px[s], o1.x, -fmaf(o0.z, tt[s], o0.x));
+          const float sy = fmaf(py[s], o1.y, -fmaf(o0.w, tt[s], o0.y));
+          ins[s] |= (fmaf(sx, sx, sy * sy) < 1.f ? 1u : 0u) << ii;
+        }
+      }
+      unsigned any = 0u;
+#pragma unroll
+      for (int s = 0; s < SLOTS; ++s) {
+        ins[s] = act[s] > 0.f ? ins[s] : 0u;
+        any |= ins[s];
+      }
+      unsigned uni = __reduce_or_sync(kFull, any);
+      while (uni) {
+        const int ii = __ffs(uni) - 1;
+        uni &= uni - 1u;
+        const float4 o0 = sObs[2 * (i0 + ii)], o1 = sObs[2 * (i0 + ii) + 1];
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) {
+          if ((ins[s] >> ii) & 1u) {
+            const float sx = fmaf(px[s], o1.x, -fmaf(o0.z, tt[s], o0.x));
+            const float sy = fmaf(py[s], o1.y, -fmaf(o0.w, tt[s], o0.y));
+            const float d2 = fmaf(sx, sx, sy * sy);
+            if (d2 > 0.f) {
+              const float g = rsqrtf(d2) - 1.f;
+              ex[s] = fmaf(g * o1.z, sx, ex[s]);
+              ey[s] = fmaf(g * o1.w, sy, ey[s]);
+            } else {
+              ex[s] += o1.z;     // atan2(0, 0) = 0: h = (x_o + a, y_o)
+            }
+          }
         }
       }
     }
@@ -356,16 +388,28 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       }
     }
 
-    // ---- D: reduce, multipliers, xi-step in increment form
-    float wl = reduce_scatter<NC>(wx, wy, lane);
-    if constexpr (WPS > 1) {
-      float* pb = part + (it & 1) * WPS * 32;
-      pb[wig * 32 + lane] = wl;
-      group_barrier(LPS);
-      float tot = 0.f;
+    // ---- D: reduce over the sample's lanes through a shared-memory transpose,
+    // multipliers, xi-step in increment form
+    float wl;
+    {
+      float* rt = sRed + (WPS > 1 ? (it & 1) * 2 * NC * RS : 0);
 #pragma unroll
-      for (int w = 0; w < WPS; ++w) tot += pb[w * 32 + lane];
-      wl = tot;
+      for (int k = 0; k < NC; ++k) {
+        rt[k * RS + gl] = wx[k];
+        rt[(NC + k) * RS + gl] = wy[k];
+      }
+      if constexpr (WPS > 1) group_barrier(LPS); else __syncwarp();
+      wl = 0.f;
+      if (valid) {
+        const float4* row = reinterpret_cast<const float4*>(rt + (axis * NC + kk) * RS);
+        float4 a = row[0];
+#pragma unroll
+        for (int c4 = 1; c4 < 8 * WPS; ++c4) {
+          const float4 b = row[c4];
+          a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+        }
+        wl = (a.x + a.y) + (a.z + a.w);
+      }
     }
     if (valid) {
       if (it > 0) lam = fmaf(hrho, wl, lam);
@@ -413,8 +457,9 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
 template <int NC, int SLOTS, int WPS>
 size_t smem_bytes(const Params& prm, int spc) {
   const int warps = spc * WPS;
-  size_t f = size_t(prm.m) * basis32_stride(NC) + 8 * prm.max_obs + 64 * warps +
-             spc * 2 * WPS * 32 + spc * WPS * 2 + 2 * NC * NC + size_t(6) * SLOTS * 32 * warps;
+  const int red = (WPS > 1 ? 2 : 1) * 2 * NC * (32 * WPS + 4);
+  size_t f = size_t(prm.m) * basis32_stride(NC) + 8 * prm.max_obs + 64 * warps + spc * red +
+             spc * WPS * 2 + 2 * NC * NC + size_t(6) * SLOTS * 32 * warps;
   return f * sizeof(float);
 }
 
