@@ -131,8 +131,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
 
   float* sW = smem;                                          // [m][ST]
   float4* sObs = reinterpret_cast<float4*>(smem + m * ST);   // [N][2]
-  float2* sObsY = reinterpret_cast<float2*>(sObs + 2 * N);   // [N] y extent over the horizon, +-b
-  float* sBuf = reinterpret_cast<float*>(sObsY + ((N + 1) & ~1));   // [warps][64]
+  float* sBuf = reinterpret_cast<float*>(sObs + 2 * N);      // [warps][64]
   constexpr int RS = 32 * WPS + 4;                           // row stride of the reduction table
   constexpr int RED = (WPS > 1 ? 2 : 1) * 2 * NC * RS;       // floats per sample group
   float* sRedAll = sBuf + 64 * warps;                        // [groups][RED]
@@ -152,9 +151,6 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     sObs[2 * i] = make_float4(float(o[0] * ia), float(o[1] * ib), float(o[2] * ia * prm.dt),
                               float(o[3] * ib * prm.dt));
     sObs[2 * i + 1] = make_float4(float(ia), float(ib), float(o[4]), float(o[5]));
-    // a point can be inside the ellipse only if |y - y_o(t)| < b at that t
-    const double y1 = o[1] + o[3] * prm.dt * (m - 1);
-    sObsY[i] = make_float2(float(fmin(o[1], y1) - o[5]), float(fmax(o[1], y1) + o[5]));
   }
   for (int e = threadIdx.x; e < 2 * NC * NC; e += blockDim.x) {
     const int ax_ = e / (NC * NC), k_ = (e / NC) % NC, i_ = e % NC;
@@ -259,20 +255,6 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       ax[s] = r6[4] + o[4]; ay[s] = r6[5] + o[5];
     }
 
-    // y range of this warp's timesteps: obstacles whose y extent (+-b) misses
-    // it cannot contain any of these points and are skipped below
-    float ylo = 3.0e38f, yhi = -3.0e38f;
-#pragma unroll
-    for (int s = 0; s < SLOTS; ++s) {
-      ylo = fminf(ylo, act[s] > 0.f ? py[s] : 3.0e38f);
-      yhi = fmaxf(yhi, act[s] > 0.f ? py[s] : -3.0e38f);
-    }
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-      ylo = fminf(ylo, __shfl_xor_sync(kFull, ylo, o));
-      yhi = fmaxf(yhi, __shfl_xor_sync(kFull, yhi, o));
-    }
-
     if (it == prm.K) {
       // ---- scoring of xi^K (Alg. 1 line 9 and the Sec. V-A cost)
       float coll[SLOTS];
@@ -280,8 +262,6 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       for (int s = 0; s < SLOTS; ++s) coll[s] = 0.f;
 #pragma unroll 1
       for (int i = 0; i < N; ++i) {
-        const float2 yr = sObsY[i];
-        if (yhi <= yr.x || ylo >= yr.y) continue;     // warp-uniform: no point inside
         const float4 o0 = sObs[2 * i], o1 = sObs[2 * i + 1];
 #pragma unroll
         for (int s = 0; s < SLOTS; ++s) {
@@ -318,8 +298,6 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       for (int s = 0; s < SLOTS; ++s) ins[s] = 0u;
 #pragma unroll 4
       for (int ii = 0; ii < nc; ++ii) {
-        const float2 yr = sObsY[i0 + ii];
-        if (yhi <= yr.x || ylo >= yr.y) continue;     // warp-uniform: no point inside
         const float4 o0 = sObs[2 * (i0 + ii)], o1 = sObs[2 * (i0 + ii) + 1];
 #pragma unroll
         for (int s = 0; s < SLOTS; ++s) {
@@ -480,7 +458,7 @@ template <int NC, int SLOTS, int WPS>
 size_t smem_bytes(const Params& prm, int spc) {
   const int warps = spc * WPS;
   const int red = (WPS > 1 ? 2 : 1) * 2 * NC * (32 * WPS + 4);
-  size_t f = size_t(prm.m) * basis32_stride(NC) + 10 * prm.max_obs + 2 + 64 * warps + spc * red +
+  size_t f = size_t(prm.m) * basis32_stride(NC) + 8 * prm.max_obs + 64 * warps + spc * red +
              spc * WPS * 2 + 2 * NC * NC + size_t(6) * SLOTS * 32 * warps;
   return f * sizeof(float);
 }
