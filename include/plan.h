@@ -255,6 +255,38 @@ int plan_sample(plan_ctx* ctx, const plan_scene* scene, const double* mu,
                 const double* sigma, int fresh, int l, uint64_t seed,
                 uint64_t episode_step, int B, double* p, void* stream);
 
+/* ------------------------------------------------ allocation-free lower level */
+
+/* The float64 lower-level solve of plan_solve (same kernels, same results) for
+ * callers that cannot allocate device memory: code embedded in a host
+ * application that owns every device allocation (a fixed, pre-reserved pool
+ * that a cudaMalloc would fragment or exceed), and real-time control loops that
+ * after start-up must not enter an allocator, whose latency is unbounded and
+ * which may synchronise the device.  The paper has no counterpart; this is an
+ * integration entry point, not a step of the method.
+ *
+ * No context is needed and nothing is allocated: no cudaMalloc / cudaFree and
+ * no allocating library routine.  The basis, the KKT inverses, a copy of the
+ * scene and the per-iteration intermediates live in one fixed __device__ array
+ * of about 4.4 MB in the library, which every GPU that loads the library holds
+ * until the process exits.  Limits: B <= 256 samples, 8 <= m <= 128 timesteps,
+ * n_obs <= 32 obstacles, n_coef <= 16, n_seg <= 4; larger requests return
+ * PLAN_ECAPACITY.  Of `cfg` only m, n_coef, n_seg, inner_iters, dt, rho, the
+ * gains, the bounds and lane_margin are used (prec and the capacities are
+ * ignored; the arithmetic is float64).
+ *
+ *   p      device, B x d_p        xi     device, B x 2 n_coef, or NULL
+ *   resid  device, B              cu     device, B
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every call
+ * uses the same array and leaves its contents behind, so two calls whose work
+ * overlaps on the GPU (different streams, or concurrent threads) race and give
+ * wrong results; serialise them, e.g. on one stream.  Errors are described by
+ * plan_last_error(NULL, ...).  Asynchronous on `stream`. */
+int plan_solve_fp64_noalloc(const plan_config* cfg, const plan_scene* scene, const double* p,
+                            int B, double* xi, double* resid, double* cu, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

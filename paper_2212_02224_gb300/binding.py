@@ -62,7 +62,8 @@ class PlanResult(ctypes.Structure):
 EXPORTS = ("plan_init", "plan_destroy", "plan_status_str", "plan_last_error", "plan_solve",
            "plan_solve_batch", "plan_upload_scenes", "plan_set_state", "plan_get_state",
            "plan_step_resident", "plan_get_result", "plan_step", "plan_select_elites",
-           "plan_update_distribution", "plan_sample", "plan_set_tuning", "plan_autotune")
+           "plan_update_distribution", "plan_sample", "plan_set_tuning", "plan_autotune",
+           "plan_solve_fp64_noalloc")
 
 _lib = None
 
@@ -103,6 +104,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "plan_sample": (I, [V, P(PlanScene), V, V, I, I, U64, U64, I, V, V]),
         "plan_set_tuning": (I, [V, I, I]),
         "plan_autotune": (I, [V, P(PlanScene), I, P(I), P(I), V]),
+        "plan_solve_fp64_noalloc": (I, [P(PlanConfig), P(PlanScene), V, I, V, V, V, V]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -272,3 +274,11 @@ def plan_autotune(ctx, scene, B: int, stream: int = 0):
     w, s = ctypes.c_int(), ctypes.c_int()
     check(load().plan_autotune(ctx, arr, int(B), ctypes.byref(w), ctypes.byref(s), stream), ctx)
     return w.value, s.value
+
+
+def plan_solve_fp64_noalloc(cfg: PlanConfig, scene, p_ptr: int, B: int, xi_ptr, r_ptr: int,
+                            cu_ptr: int, stream: int = 0):
+    """Allocation-free float64 solve (no context; see include/plan.h)."""
+    arr, keep = make_scenes([scene])
+    check(load().plan_solve_fp64_noalloc(ctypes.byref(cfg), arr, p_ptr, int(B), xi_ptr, r_ptr,
+                                         cu_ptr, stream), None)

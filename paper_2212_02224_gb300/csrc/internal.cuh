@@ -115,6 +115,9 @@ cudaError_t launch_select_update(const Layout* layout, DevCem* cem, int S, int l
                                  const double* r, const double* cu, int* elite_out,
                                  cudaStream_t s);
 
+// Error message of a call that has no context (reported by plan_last_error(NULL)).
+void set_unbound_error(const char* msg);
+
 cudaError_t launch_select_only(const double* r, const double* cu, int B, int n_c, int q,
                                int* elite, cudaStream_t s);
 cudaError_t launch_update_only(const double* p_elite, const double* cost, int q, int d_p,

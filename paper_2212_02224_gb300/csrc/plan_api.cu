@@ -373,6 +373,8 @@ int make_cem(plan_ctx* ctx, const plan_cem_state* st, int n_lanes, double lane_w
 
 }  // namespace
 
+void plan::set_unbound_error(const char* msg) { g_init_err = msg; }
+
 extern "C" {
 
 const char* plan_status_str(int status) {

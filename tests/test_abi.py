@@ -21,7 +21,7 @@ def _lib():
 def _declared():
     hdr = open(os.path.join(ROOT, "include", "plan.h")).read()
     hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
-    return sorted(set(re.findall(r"\b(plan_[a-z_]+)\s*\(", hdr)))
+    return sorted(set(re.findall(r"\b(plan_[a-z0-9_]+)\s*\(", hdr)))
 
 
 def test_header_declares_the_binding_names():
