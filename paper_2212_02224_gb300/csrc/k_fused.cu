@@ -34,61 +34,36 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-template <int NC>
-__device__ __forceinline__ float reduce_scatter(const float (&wx)[NC], const float (&wy)[NC],
-                                                int lane) {
-  // Logical slots: x coefficient k -> k, y coefficient k -> 16 + k.  After
-  // five halving exchanges lane l holds the warp sum of slot l.
-  float v[16];
-  const bool up16 = lane & 16;
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    if (k < NC) {
-      float send = up16 ? wx[k] : wy[k];
-      float keep = up16 ? wy[k] : wx[k];
-      v[k] = keep + __shfl_xor_sync(kFull, send, 16);
-    } else {
-      v[k] = 0.f;
-    }
-  }
-#pragma unroll
-  for (int o = 8; o >= 1; o >>= 1) {
-    const bool up = lane & o;
-#pragma unroll
-    for (int k = 0; k < o; ++k) {
-      float send = up ? v[k] : v[k + o];
-      float keep = up ? v[k + o] : v[k];
-      v[k] = keep + __shfl_xor_sync(kFull, send, o);
-    }
-  }
-  return v[0];
-}
-
 // sqrt(x) for x >= 0 through the hardware reciprocal square root.
 __device__ __forceinline__ float fast_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
 
-// W[t] . a, Wd[t] . a, Wdd[t] . a for both axes: row pointer `row` holds the
-// three padded basis rows of timestep t.
+// Packed float32 pairs (two independent fma.rn per instruction on sm_100+).
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+// W[t] . a, Wd[t] . a, Wdd[t] . a for both axes, with coefficient pairs
+// (k, k+1) in packed registers: `row` holds the three zero-padded basis rows
+// of timestep t, xv / yv the padded coefficient pairs.
 template <int NC>
-__device__ __forceinline__ void kin(const float* __restrict__ row, const float (&xv)[NC],
-                                    const float (&yv)[NC], float (&o)[6]) {
+__device__ __forceinline__ void kin(const float* __restrict__ row,
+                                    const float2 (&xv)[basis32_ncp(NC) / 2],
+                                    const float2 (&yv)[basis32_ncp(NC) / 2], float (&o)[6]) {
   constexpr int NCP = basis32_ncp(NC);
 #pragma unroll
-  for (int q = 0; q < 6; ++q) o[q] = 0.f;
-#pragma unroll
   for (int mat = 0; mat < 3; ++mat) {
+    float2 ax = f2(0.f, 0.f), ay = f2(0.f, 0.f);
 #pragma unroll
     for (int k4 = 0; k4 < NCP; k4 += 4) {
       const float4 w = *reinterpret_cast<const float4*>(row + mat * NCP + k4);
-      const float wk[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (k4 + u < NC) {
-          o[2 * mat] = fmaf(wk[u], xv[k4 + u], o[2 * mat]);
-          o[2 * mat + 1] = fmaf(wk[u], yv[k4 + u], o[2 * mat + 1]);
-        }
-      }
+      const float2 w01 = f2(w.x, w.y), w23 = f2(w.z, w.w);
+      ax = fma2(w01, xv[k4 / 2], ax);
+      ay = fma2(w01, yv[k4 / 2], ay);
+      ax = fma2(w23, xv[k4 / 2 + 1], ax);
+      ay = fma2(w23, yv[k4 / 2 + 1], ay);
     }
+    o[2 * mat] = ax.x + ax.y;
+    o[2 * mat + 1] = ay.x + ay.y;
   }
 }
 
@@ -100,14 +75,14 @@ __device__ __forceinline__ void group_barrier(int nthreads) {
 }
 
 // One sample per group of WPS warps (32 WPS lanes); a CTA holds blockDim.x /
-// (32 WPS) groups, each on its own named barrier.  Timestep t = s * 32 WPS +
+// (32 WPS) groups (one group when WPS > 1).  Timestep t = s * 32 WPS +
 // (warp-in-group) * 32 + lane for slot s; lanes with t >= m compute on the
 // last timestep's data and contribute nothing.
 template <int SLOTS, int WPS>
 struct RegCap {
   // registers per thread: one timestep slot per 32 lanes needs about 70, the
   // rest is per-sample state; capped so that enough warps stay resident
-  static constexpr int value = SLOTS * WPS >= 8 ? 255 : (SLOTS >= 4 ? 208 : (SLOTS == 2 ? 144 : 96));
+  static constexpr int value = SLOTS * WPS >= 8 ? 255 : (SLOTS >= 4 ? 224 : (SLOTS == 2 ? 144 : 96));
 };
 
 template <int NC, int SLOTS, int WPS>
@@ -118,8 +93,10 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
              double* __restrict__ xi_out, double* __restrict__ r_out,
              double* __restrict__ cu_out) {
   constexpr int NCP = basis32_ncp(NC);
+  constexpr int NP = NCP / 2;              // coefficient pairs
   constexpr int ST = basis32_stride(NC);
   constexpr int LPS = 32 * WPS;
+  constexpr bool kPairSlots = SLOTS % 2 == 0;
   extern __shared__ __align__(16) float smem[];
   const int m = prm.m;
   const int ns = prm.n_seg;
@@ -130,8 +107,8 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   const int groups = warps / WPS;
 
   float* sW = smem;                                          // [m][ST]
-  float4* sObs = reinterpret_cast<float4*>(smem + m * ST);   // [N][2]
-  float* sBuf = reinterpret_cast<float*>(sObs + 2 * N);      // [warps][64]
+  float4* sObs = reinterpret_cast<float4*>(smem + m * ST);   // [N][4]
+  float* sBuf = reinterpret_cast<float*>(sObs + 4 * N);      // [warps][64]
   constexpr int RS = 32 * WPS + 4;                           // row stride of the reduction table
   constexpr int RED = (WPS > 1 ? 2 : 1) * 2 * NC * RS;       // floats per sample group
   float* sRedAll = sBuf + 64 * warps;                        // [groups][RED]
@@ -145,12 +122,16 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     for (int i = threadIdx.x; i < m * ST / 4; i += blockDim.x) dst[i] = src[i];
   }
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    // scaled trajectory x_o(t) / a = x0/a + (vx dt / a) t and likewise for y
+    // scaled trajectory: (x - x_o(t)) / a = x / a + (-x0/a) + (-vx dt / a) t,
+    // constants duplicated for packed pairs of timesteps
     const double* o = obs + size_t(sc.obs_off + i) * 6;
     const double ia = 1.0 / o[4], ib = 1.0 / o[5];
-    sObs[2 * i] = make_float4(float(o[0] * ia), float(o[1] * ib), float(o[2] * ia * prm.dt),
-                              float(o[3] * ib * prm.dt));
-    sObs[2 * i + 1] = make_float4(float(ia), float(ib), float(o[4]), float(o[5]));
+    const float nx0 = float(-o[0] * ia), nvx = float(-o[2] * ia * prm.dt);
+    const float ny0 = float(-o[1] * ib), nvy = float(-o[3] * ib * prm.dt);
+    sObs[4 * i + 0] = make_float4(nx0, nx0, nvx, nvx);
+    sObs[4 * i + 1] = make_float4(ny0, ny0, nvy, nvy);
+    sObs[4 * i + 2] = make_float4(float(ia), float(ia), float(ib), float(ib));
+    sObs[4 * i + 3] = make_float4(float(o[4]), float(o[5]), 0.f, 0.f);
   }
   for (int e = threadIdx.x; e < 2 * NC * NC; e += blockDim.x) {
     const int ax_ = e / (NC * NC), k_ = (e / NC) % NC, i_ = e % NC;
@@ -183,8 +164,8 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     xb = fmaf(s1[ns + 1], float(sc.ego[axis + 2]), xb);
     xb = fmaf(s1[ns + 2], float(sc.ego[axis + 4]), xb);
     xb_l = xb;
-    xbuf[lane] = xb;
   }
+  xbuf[lane] = xb_l;     // padding slots hold 0: they meet zero basis columns
   __syncwarp();
 
   int tcl[SLOTS];     // clamped timestep (valid row address)
@@ -198,11 +179,20 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     tt[s] = float(t);
   }
 
+  auto load_iterate = [&](float2 (&xv)[NP], float2 (&yv)[NP]) {
+#pragma unroll
+    for (int i4 = 0; i4 < NCP; i4 += 4) {
+      const float4 a = *reinterpret_cast<const float4*>(xbuf + i4);
+      const float4 b = *reinterpret_cast<const float4*>(xbuf + 16 + i4);
+      xv[i4 / 2] = f2(a.x, a.y); xv[i4 / 2 + 1] = f2(a.z, a.w);
+      yv[i4 / 2] = f2(b.x, b.y); yv[i4 / 2 + 1] = f2(b.z, b.w);
+    }
+  };
+
   // ---- reference kinematics at xi_bar
   {
-    float xv[NC], yv[NC];
-#pragma unroll
-    for (int i = 0; i < NC; ++i) { xv[i] = xbuf[i]; yv[i] = xbuf[16 + i]; }
+    float2 xv[NP], yv[NP];
+    load_iterate(xv, yv);
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) {
       float o[6];
@@ -212,7 +202,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     }
   }
   __syncwarp();
-  if (valid) xbuf[lane] = 0.f;    // delta^0 = 0
+  xbuf[lane] = 0.f;    // delta^0 = 0
 
   const float rho = float(prm.rho);
   const float hrho = 0.5f * rho;
@@ -231,16 +221,8 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
 
   for (int it = 0;; ++it) {
     __syncwarp();
-    float xv[NC], yv[NC];
-#pragma unroll
-    for (int i4 = 0; i4 < NC; i4 += 4) {
-      const float4 a = *reinterpret_cast<const float4*>(xbuf + i4);
-      const float4 b = *reinterpret_cast<const float4*>(xbuf + 16 + i4);
-      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (i4 + u < NC) { xv[i4 + u] = av[u]; yv[i4 + u] = bv[u]; }
-    }
+    float2 xv[NP], yv[NP];
+    load_iterate(xv, yv);
 
     // ---- A: kinematics at the lane's timesteps
     float px[SLOTS], py[SLOTS], vx[SLOTS], vy[SLOTS], ax[SLOTS], ay[SLOTS];
@@ -262,11 +244,11 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       for (int s = 0; s < SLOTS; ++s) coll[s] = 0.f;
 #pragma unroll 1
       for (int i = 0; i < N; ++i) {
-        const float4 o0 = sObs[2 * i], o1 = sObs[2 * i + 1];
+        const float4 q0 = sObs[4 * i], q1 = sObs[4 * i + 1], q2 = sObs[4 * i + 2];
 #pragma unroll
         for (int s = 0; s < SLOTS; ++s) {
-          const float sx = fmaf(px[s], o1.x, -fmaf(o0.z, tt[s], o0.x));
-          const float sy = fmaf(py[s], o1.y, -fmaf(o0.w, tt[s], o0.y));
+          const float sx = fmaf(px[s], q2.x, fmaf(q0.z, tt[s], q0.x));
+          const float sy = fmaf(py[s], q2.z, fmaf(q1.z, tt[s], q1.x));
           coll[s] += fmaxf(0.f, 1.f - fmaf(sx, sx, sy * sy));
         }
       }
@@ -298,12 +280,27 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       for (int s = 0; s < SLOTS; ++s) ins[s] = 0u;
 #pragma unroll 4
       for (int ii = 0; ii < nc; ++ii) {
-        const float4 o0 = sObs[2 * (i0 + ii)], o1 = sObs[2 * (i0 + ii) + 1];
+        const float4 q0 = sObs[4 * (i0 + ii)], q1 = sObs[4 * (i0 + ii) + 1];
+        const float4 q2 = sObs[4 * (i0 + ii) + 2];
+        if constexpr (kPairSlots) {
 #pragma unroll
-        for (int s = 0; s < SLOTS; ++s) {
-          const float sx = fmaf(px[s], o1.x, -fmaf(o0.z, tt[s], o0.x));
-          const float sy = fmaf(py[s], o1.y, -fmaf(o0.w, tt[s], o0.y));
-          ins[s] |= (fmaf(sx, sx, sy * sy) < 1.f ? 1u : 0u) << ii;
+          for (int s = 0; s < SLOTS; s += 2) {
+            const float2 tp = f2(tt[s], tt[s + 1]);
+            const float2 sx = fma2(f2(px[s], px[s + 1]), f2(q2.x, q2.y),
+                                   fma2(f2(q0.z, q0.w), tp, f2(q0.x, q0.y)));
+            const float2 sy = fma2(f2(py[s], py[s + 1]), f2(q2.z, q2.w),
+                                   fma2(f2(q1.z, q1.w), tp, f2(q1.x, q1.y)));
+            const float2 d2 = fma2(sx, sx, mul2(sy, sy));
+            ins[s] |= (d2.x < 1.f ? 1u : 0u) << ii;
+            ins[s + 1] |= (d2.y < 1.f ? 1u : 0u) << ii;
+          }
+        } else {
+#pragma unroll
+          for (int s = 0; s < SLOTS; ++s) {
+            const float sx = fmaf(px[s], q2.x, fmaf(q0.z, tt[s], q0.x));
+            const float sy = fmaf(py[s], q2.z, fmaf(q1.z, tt[s], q1.x));
+            ins[s] |= (fmaf(sx, sx, sy * sy) < 1.f ? 1u : 0u) << ii;
+          }
         }
       }
       unsigned any = 0u;
@@ -316,19 +313,20 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       while (uni) {
         const int ii = __ffs(uni) - 1;
         uni &= uni - 1u;
-        const float4 o0 = sObs[2 * (i0 + ii)], o1 = sObs[2 * (i0 + ii) + 1];
+        const float4 q0 = sObs[4 * (i0 + ii)], q1 = sObs[4 * (i0 + ii) + 1];
+        const float4 q2 = sObs[4 * (i0 + ii) + 2], q3 = sObs[4 * (i0 + ii) + 3];
 #pragma unroll
         for (int s = 0; s < SLOTS; ++s) {
           if ((ins[s] >> ii) & 1u) {
-            const float sx = fmaf(px[s], o1.x, -fmaf(o0.z, tt[s], o0.x));
-            const float sy = fmaf(py[s], o1.y, -fmaf(o0.w, tt[s], o0.y));
+            const float sx = fmaf(px[s], q2.x, fmaf(q0.z, tt[s], q0.x));
+            const float sy = fmaf(py[s], q2.z, fmaf(q1.z, tt[s], q1.x));
             const float d2 = fmaf(sx, sx, sy * sy);
             if (d2 > 0.f) {
               const float g = rsqrtf(d2) - 1.f;
-              ex[s] = fmaf(g * o1.z, sx, ex[s]);
-              ey[s] = fmaf(g * o1.w, sy, ey[s]);
+              ex[s] = fmaf(g * q3.x, sx, ex[s]);
+              ey[s] = fmaf(g * q3.y, sy, ey[s]);
             } else {
-              ex[s] += o1.z;     // atan2(0, 0) = 0: h = (x_o + a, y_o)
+              ex[s] += q3.x;     // atan2(0, 0) = 0: h = (x_o + a, y_o)
             }
           }
         }
@@ -336,9 +334,9 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     }
 
     // ---- C: velocity / acceleration / lane rows and the transposed contraction
-    float wx[NC], wy[NC];
+    float2 wx[NP], wy[NP];
 #pragma unroll
-    for (int k = 0; k < NC; ++k) { wx[k] = 0.f; wy[k] = 0.f; }
+    for (int k = 0; k < NP; ++k) { wx[k] = f2(0.f, 0.f); wy[k] = f2(0.f, 0.f); }
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) {
       const float v2 = fmaf(vx[s], vx[s], vy[s] * vy[s]);
@@ -369,21 +367,18 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       const float exs = A * ex[s];
       const float eoy = A * (ey[s] + ely);
       const float* row = sW + tcl[s] * ST;
-      const float ex_[3] = {exs, evx, eax};
-      const float ey_[3] = {eoy, evy, eay};
+      const float2 ex_[3] = {f2(exs, exs), f2(evx, evx), f2(eax, eax)};
+      const float2 ey_[3] = {f2(eoy, eoy), f2(evy, evy), f2(eay, eay)};
 #pragma unroll
       for (int mat = 0; mat < 3; ++mat) {
 #pragma unroll
         for (int k4 = 0; k4 < NCP; k4 += 4) {
           const float4 w = *reinterpret_cast<const float4*>(row + mat * NCP + k4);
-          const float wk[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (k4 + u < NC) {
-              wx[k4 + u] = fmaf(wk[u], ex_[mat], wx[k4 + u]);
-              wy[k4 + u] = fmaf(wk[u], ey_[mat], wy[k4 + u]);
-            }
-          }
+          const float2 w01 = f2(w.x, w.y), w23 = f2(w.z, w.w);
+          wx[k4 / 2] = fma2(w01, ex_[mat], wx[k4 / 2]);
+          wy[k4 / 2] = fma2(w01, ey_[mat], wy[k4 / 2]);
+          wx[k4 / 2 + 1] = fma2(w23, ex_[mat], wx[k4 / 2 + 1]);
+          wy[k4 / 2 + 1] = fma2(w23, ey_[mat], wy[k4 / 2 + 1]);
         }
       }
     }
@@ -395,17 +390,17 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       float* rt = sRed + (WPS > 1 ? (it & 1) * 2 * NC * RS : 0);
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
-        rt[k * RS + gl] = wx[k];
-        rt[(NC + k) * RS + gl] = wy[k];
+        rt[k * RS + gl] = (k & 1) ? wx[k / 2].y : wx[k / 2].x;
+        rt[(NC + k) * RS + gl] = (k & 1) ? wy[k / 2].y : wy[k / 2].x;
       }
       if constexpr (WPS > 1) group_barrier(LPS); else __syncwarp();
       wl = 0.f;
       if (valid) {
-        const float4* row = reinterpret_cast<const float4*>(rt + (axis * NC + kk) * RS);
-        float4 a = row[0];
+        const float4* rrow = reinterpret_cast<const float4*>(rt + (axis * NC + kk) * RS);
+        float4 a = rrow[0];
 #pragma unroll
         for (int c4 = 1; c4 < 8 * WPS; ++c4) {
-          const float4 b = row[c4];
+          const float4 b = rrow[c4];
           a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
         }
         wl = (a.x + a.y) + (a.z + a.w);
@@ -458,7 +453,7 @@ template <int NC, int SLOTS, int WPS>
 size_t smem_bytes(const Params& prm, int spc) {
   const int warps = spc * WPS;
   const int red = (WPS > 1 ? 2 : 1) * 2 * NC * (32 * WPS + 4);
-  size_t f = size_t(prm.m) * basis32_stride(NC) + 8 * prm.max_obs + 64 * warps + spc * red +
+  size_t f = size_t(prm.m) * basis32_stride(NC) + 16 * prm.max_obs + 64 * warps + spc * red +
              spc * WPS * 2 + 2 * NC * NC + size_t(6) * SLOTS * 32 * warps;
   return f * sizeof(float);
 }
