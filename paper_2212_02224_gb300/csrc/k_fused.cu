@@ -155,15 +155,17 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   const float* Mrow = sM + (axis * NC + (valid ? kk : 0)) * NC;
   float xb_l = 0.f;     // xi_bar of this lane's slot
   if (valid) {
-    // xi_bar = Gs p_axis + Hs b_axis (x uses the v_d entries, y the y_d entries)
-    const float* s1 = c.s1_32 + size_t(axis * NC + kk) * (ns + 3);
+    // xi_bar = Gs p_axis + Hs b_axis (x uses the v_d entries, y the y_d entries),
+    // applied in float64: at high polynomial degree the Step-1 map has entries
+    // of order 1e3 whose products cancel to the coefficients' size
+    const double* s1 = c.s1_64 + size_t(axis * NC + kk) * (ns + 3);
     const double* pj = pin + size_t(j) * (2 * ns);
-    float xb = 0.f;
-    for (int q = 0; q < ns; ++q) xb = fmaf(s1[q], float(pj[(axis == 0 ? ns : 0) + q]), xb);
-    xb = fmaf(s1[ns], float(sc.ego[axis]), xb);
-    xb = fmaf(s1[ns + 1], float(sc.ego[axis + 2]), xb);
-    xb = fmaf(s1[ns + 2], float(sc.ego[axis + 4]), xb);
-    xb_l = xb;
+    double xb = 0.0;
+    for (int q = 0; q < ns; ++q) xb = fma(s1[q], pj[(axis == 0 ? ns : 0) + q], xb);
+    xb = fma(s1[ns], sc.ego[axis], xb);
+    xb = fma(s1[ns + 1], sc.ego[axis + 2], xb);
+    xb = fma(s1[ns + 2], sc.ego[axis + 4], xb);
+    xb_l = float(xb);
   }
   xbuf[lane] = xb_l;     // padding slots hold 0: they meet zero basis columns
   __syncwarp();
