@@ -7,7 +7,7 @@
 #include <cstdio>
 #include <mutex>
 
-#include "../../include/plan.h"
+#include "plan.h"
 #include "internal.cuh"
 
 namespace plan {

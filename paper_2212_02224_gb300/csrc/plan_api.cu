@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/plan.h"
+#include "plan.h"
 #include "internal.cuh"
 
 namespace plan {
