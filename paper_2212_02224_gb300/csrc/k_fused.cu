@@ -115,6 +115,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   float* sScore = sRedAll + groups * RED;                    // [groups][WPS][2]
   float* sM = sScore + groups * WPS * 2;                     // [2][NC][NC] rows of M
   float* sRef = sM + 2 * NC * NC;                            // [warps][6][SLOTS][32]
+  float* sThr = sRef + warps * 6 * SLOTS * 32;               // [warps][N] obstacle re-test levels
 
   {
     const float4* src = reinterpret_cast<const float4*>(c.basis32);
@@ -148,6 +149,24 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   float* vbuf = xbuf + 32;             // slot layout: lambda + rho w - delta
   float* sRed = sRedAll + grp * RED;
   float* ref = sRef + warp * 6 * SLOTS * 32 + lane;   // ref[(q * SLOTS + s) * 32]
+  // Obstacle i can hold a point of this warp's timesteps only once the
+  // trajectory has moved by (scaled) thr[i] - moved - 1 since it was last
+  // tested: positions are convex combinations of the coefficients (Bernstein
+  // rows are nonnegative and sum to one), so no point moves further than the
+  // largest coefficient change.  Skipped obstacles contribute exactly zero.
+  float* thr = sThr + warp * N;
+  for (int i = lane; i < N; i += 32) thr[i] = -3.0e38f;
+  float ia_max = 0.f, ib_max = 0.f;
+  for (int i = lane; i < N; i += 32) {
+    ia_max = fmaxf(ia_max, sObs[4 * i + 2].x);
+    ib_max = fmaxf(ib_max, sObs[4 * i + 2].z);
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    ia_max = fmaxf(ia_max, __shfl_xor_sync(kFull, ia_max, o));
+    ib_max = fmaxf(ib_max, __shfl_xor_sync(kFull, ib_max, o));
+  }
+  float moved = 0.f;   // bound on the scaled movement of any point since iteration 0
 
   // ---- per-lane coefficient slot: Step 1 and the row of M
   const int axis = lane >> 4, kk = lane & 15;
@@ -280,10 +299,14 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       unsigned ins[SLOTS];
 #pragma unroll
       for (int s = 0; s < SLOTS; ++s) ins[s] = 0u;
-#pragma unroll 4
-      for (int ii = 0; ii < nc; ++ii) {
+      // obstacles that may be within reach (warp-uniform mask)
+      unsigned near = __ballot_sync(kFull, lane < nc && thr[i0 + lane] - moved <= 1.001f);
+      while (near) {
+        const int ii = __ffs(near) - 1;
+        near &= near - 1u;
         const float4 q0 = sObs[4 * (i0 + ii)], q1 = sObs[4 * (i0 + ii) + 1];
         const float4 q2 = sObs[4 * (i0 + ii) + 2];
+        float dmin = 3.0e38f;
         if constexpr (kPairSlots) {
 #pragma unroll
           for (int s = 0; s < SLOTS; s += 2) {
@@ -295,15 +318,21 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
             const float2 d2 = fma2(sx, sx, mul2(sy, sy));
             ins[s] |= (d2.x < 1.f ? 1u : 0u) << ii;
             ins[s + 1] |= (d2.y < 1.f ? 1u : 0u) << ii;
+            dmin = fminf(dmin, fminf(act[s] > 0.f ? d2.x : 3.0e38f, act[s + 1] > 0.f ? d2.y : 3.0e38f));
           }
         } else {
 #pragma unroll
           for (int s = 0; s < SLOTS; ++s) {
             const float sx = fmaf(px[s], q2.x, fmaf(q0.z, tt[s], q0.x));
             const float sy = fmaf(py[s], q2.z, fmaf(q1.z, tt[s], q1.x));
-            ins[s] |= (fmaf(sx, sx, sy * sy) < 1.f ? 1u : 0u) << ii;
+            const float d2 = fmaf(sx, sx, sy * sy);
+            ins[s] |= (d2 < 1.f ? 1u : 0u) << ii;
+            dmin = fminf(dmin, act[s] > 0.f ? d2 : 3.0e38f);
           }
         }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) dmin = fminf(dmin, __shfl_xor_sync(kFull, dmin, o));
+        if (lane == 0) thr[i0 + ii] = fast_sqrt(dmin) + moved;
       }
       unsigned any = 0u;
 #pragma unroll
@@ -413,6 +442,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       vbuf[lane] = fmaf(rho, wl, lam) - dl;
     }
     __syncwarp();
+    float acc_step = 0.f;
     if (valid) {
       const float* vb = vbuf + axis * 16;
       float acc0 = 0.f, acc1 = 0.f;
@@ -421,8 +451,16 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
         acc0 = fmaf(Mrow[i], vb[i], acc0);
         if (i + 1 < NC) acc1 = fmaf(Mrow[i + 1], vb[i + 1], acc1);
       }
-      dl += acc0 + acc1;
+      acc_step = acc0 + acc1;
+      dl += acc_step;
       xbuf[lane] = dl;
+    }
+    {
+      // scaled bound on how far any point moves in this step
+      float mv = valid ? fabsf(acc_step) * (axis ? ib_max : ia_max) : 0.f;
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) mv = fmaxf(mv, __shfl_xor_sync(kFull, mv, o));
+      moved += 1.41422f * mv;
     }
   }
 
@@ -456,7 +494,7 @@ size_t smem_bytes(const Params& prm, int spc) {
   const int warps = spc * WPS;
   const int red = (WPS > 1 ? 2 : 1) * 2 * NC * (32 * WPS + 4);
   size_t f = size_t(prm.m) * basis32_stride(NC) + 16 * prm.max_obs + 64 * warps + spc * red +
-             spc * WPS * 2 + 2 * NC * NC + size_t(6) * SLOTS * 32 * warps;
+             spc * WPS * 2 + 2 * NC * NC + size_t(6) * SLOTS * 32 * warps + size_t(warps) * prm.max_obs;
   return f * sizeof(float);
 }
 
