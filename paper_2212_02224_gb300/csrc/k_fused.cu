@@ -330,8 +330,8 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
             dmin = fminf(dmin, act[s] > 0.f ? d2 : 3.0e38f);
           }
         }
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) dmin = fminf(dmin, __shfl_xor_sync(kFull, dmin, o));
+        // warp minimum of a nonnegative float: integer order of its bits
+        dmin = __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(dmin)));
         if (lane == 0) thr[i0 + ii] = fast_sqrt(dmin) + moved;
       }
       unsigned any = 0u;
@@ -457,10 +457,8 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     }
     {
       // scaled bound on how far any point moves in this step
-      float mv = valid ? fabsf(acc_step) * (axis ? ib_max : ia_max) : 0.f;
-#pragma unroll
-      for (int o = 16; o >= 1; o >>= 1) mv = fmaxf(mv, __shfl_xor_sync(kFull, mv, o));
-      moved += 1.41422f * mv;
+      const float mv = valid ? fabsf(acc_step) * (axis ? ib_max : ia_max) : 0.f;
+      moved += 1.41422f * __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(mv)));
     }
   }
 
