@@ -214,6 +214,75 @@ int plan_get_result(plan_ctx* ctx, int slot, plan_result* out, void* stream);
 int plan_step(plan_ctx* ctx, const plan_scene* scene, plan_cem_state* st, int B,
               plan_result* out, void* stream);
 
+/* ------------------------------------------------------ MPC receding horizon */
+
+/* Advance one MPC cycle (Sec. V-A, MPC-Bi-Level: the ego executes the first
+ * `steps` elements of the plan, then replans): the new ego state is the
+ * trajectory xi (2 n_coef coefficients, host) at t = steps dt, obstacles move
+ * on at constant velocity, and the frame is shifted so that the ego is again at
+ * x = 0.  out->obs points to out_obs (host, in->n_obs entries, caller-owned).
+ * Host-only arithmetic in float64; no device work. */
+int plan_advance(const plan_config* cfg, const plan_scene* in, const double* xi, int steps,
+                 plan_scene* out, plan_obstacle* out_obs);
+
+/* ------------------------------------------------------------------ serving */
+
+/* A serving loop batches planning requests of many scenes continuously: a
+ * library thread admits pending requests into waves of executors (one planner
+ * context per horizon m, own stream and arena) as scene slots and samples free
+ * up, creates executors while `device_budget` bytes and `max_executors` allow,
+ * and runs waves of different executors concurrently.  Each request is one
+ * MPC cycle (Alg. 1, outer_iters iterations) of an episode; the episode's
+ * sampling distribution stays in a device table between its cycles (the
+ * warm start of Sec. V-A / Alg. 1 line 2).  A scene's result does not depend
+ * on the other scenes of its wave: every sample, selection and update is per
+ * scene, and the kernel shape is fixed per executor.
+ * The configuration's max_samples / max_scenes / max_obs are the capacities
+ * of one executor's wave. */
+typedef struct plan_server plan_server;
+
+typedef struct {
+    plan_scene scene;     /* host; copied at submission                          */
+    int B;                /* samples, 1..max_samples                             */
+    int m;                /* horizon in timesteps; 0 = the configuration's m     */
+    uint64_t episode;     /* warm-start key; a new key starts a fresh episode    */
+    uint64_t seed;        /* Philox key of a fresh episode                       */
+    int fresh;            /* restart a known episode from the uniform draw       */
+    int reserved0;
+} plan_request;
+
+typedef struct {
+    int executors, busy, pending, max_wave;
+    uint64_t waves, completed;
+    size_t device_bytes;
+} plan_server_stats;
+
+/* Create a serving loop on the current device.  Errors: EINVAL (bad config),
+ * ENOMEM (budget below one executor or allocation failure). */
+int plan_server_create(const plan_config* cfg, int max_executors, size_t device_budget,
+                       int max_episodes, plan_server** out);
+
+/* Stop the loop, wait for work in flight, release everything.  NULL accepted. */
+int plan_server_destroy(plan_server* srv);
+
+/* Queue one request; returns at once with a ticket.  Requests of one episode
+ * must be submitted one at a time (after the previous one was polled).
+ * Errors: ECAPACITY (B, n_obs or the episode table), EINVAL. */
+int plan_submit(plan_server* srv, const plan_request* req, uint64_t* ticket);
+
+/* Wait up to timeout_us for a ticket.  OK: *out holds the best pair and
+ * *latency_us (may be NULL) the time from submission to completion; the ticket
+ * is released.  ETIMEOUT: not done yet (poll again).  ENONFINITE / ECUDA: the
+ * request failed.  EINVAL: unknown ticket. */
+int plan_poll(plan_server* srv, uint64_t ticket, plan_result* out, double* latency_us,
+              int timeout_us);
+
+/* Release an episode's warm-start row (no request of it may be pending). */
+int plan_end_episode(plan_server* srv, uint64_t episode);
+
+/* Counters of the loop. */
+int plan_server_info(plan_server* srv, plan_server_stats* out);
+
 /* ------------------------------------------------------------------- tuning */
 
 /* Shape of the fused FP32 kernel: warps_per_sample (the warps that share one

@@ -53,6 +53,18 @@ class PlanCemState(ctypes.Structure):
                 ("fresh", ctypes.c_int), ("reserved0", ctypes.c_int)]
 
 
+class PlanRequest(ctypes.Structure):
+    _fields_ = [("scene", PlanScene), ("B", ctypes.c_int), ("m", ctypes.c_int),
+                ("episode", ctypes.c_uint64), ("seed", ctypes.c_uint64),
+                ("fresh", ctypes.c_int), ("reserved0", ctypes.c_int)]
+
+
+class PlanServerStats(ctypes.Structure):
+    _fields_ = [("executors", ctypes.c_int), ("busy", ctypes.c_int), ("pending", ctypes.c_int),
+                ("max_wave", ctypes.c_int), ("waves", ctypes.c_uint64),
+                ("completed", ctypes.c_uint64), ("device_bytes", ctypes.c_size_t)]
+
+
 class PlanResult(ctypes.Structure):
     _fields_ = [("p", ctypes.c_double * 8), ("xi", ctypes.c_double * 32),
                 ("cost", ctypes.c_double), ("resid", ctypes.c_double), ("cu", ctypes.c_double),
@@ -63,7 +75,8 @@ EXPORTS = ("plan_init", "plan_destroy", "plan_status_str", "plan_last_error", "p
            "plan_solve_batch", "plan_upload_scenes", "plan_set_state", "plan_get_state",
            "plan_step_resident", "plan_get_result", "plan_step", "plan_select_elites",
            "plan_update_distribution", "plan_sample", "plan_set_tuning", "plan_autotune",
-           "plan_solve_fp64_noalloc")
+           "plan_solve_fp64_noalloc", "plan_advance", "plan_server_create", "plan_server_destroy",
+           "plan_submit", "plan_poll", "plan_end_episode", "plan_server_info")
 
 _lib = None
 
@@ -105,6 +118,13 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "plan_set_tuning": (I, [V, I, I]),
         "plan_autotune": (I, [V, P(PlanScene), I, P(I), P(I), V]),
         "plan_solve_fp64_noalloc": (I, [P(PlanConfig), P(PlanScene), V, I, V, V, V, V]),
+        "plan_advance": (I, [P(PlanConfig), P(PlanScene), P(D), I, P(PlanScene), P(PlanObstacle)]),
+        "plan_server_create": (I, [P(PlanConfig), I, ctypes.c_size_t, I, P(V)]),
+        "plan_server_destroy": (I, [V]),
+        "plan_submit": (I, [V, P(PlanRequest), P(U64)]),
+        "plan_poll": (I, [V, U64, P(PlanResult), P(D), I]),
+        "plan_end_episode": (I, [V, U64]),
+        "plan_server_info": (I, [V, P(PlanServerStats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -282,3 +302,73 @@ def plan_solve_fp64_noalloc(cfg: PlanConfig, scene, p_ptr: int, B: int, xi_ptr, 
     arr, keep = make_scenes([scene])
     check(load().plan_solve_fp64_noalloc(ctypes.byref(cfg), arr, p_ptr, int(B), xi_ptr, r_ptr,
                                          cu_ptr, stream), None)
+
+
+class SceneView:
+    """Plain scene record (ego, n_lanes, lane_width, kappa_road, obstacles)."""
+
+    def __init__(self, ego, n_lanes, lane_width, kappa_road, obstacles):
+        self.ego, self.n_lanes, self.lane_width = list(ego), n_lanes, lane_width
+        self.kappa_road, self.obstacles = kappa_road, [list(o) for o in obstacles]
+
+    @property
+    def n_obs(self):
+        return len(self.obstacles)
+
+
+def plan_advance(cfg: PlanConfig, scene, xi, steps: int):
+    """MPC advance (see include/plan.h); returns the next scene as a SceneView."""
+    arr, keep = make_scenes([scene])
+    n_obs = arr[0].n_obs
+    xi_c = (ctypes.c_double * len(xi))(*[float(v) for v in xi])
+    out = PlanScene()
+    out_obs = (PlanObstacle * max(n_obs, 1))()
+    check(load().plan_advance(ctypes.byref(cfg), arr, xi_c, int(steps), ctypes.byref(out),
+                              out_obs), None)
+    e = out.ego
+    obs = [[out_obs[i].x0, out_obs[i].y0, out_obs[i].vx, out_obs[i].vy, out_obs[i].a, out_obs[i].b]
+           for i in range(n_obs)]
+    return SceneView([e.x, e.y, e.vx, e.vy, e.ax, e.ay], out.n_lanes, out.lane_width,
+                     out.kappa_road, obs)
+
+
+def plan_server_create(cfg: PlanConfig, max_executors: int, device_budget: int, max_episodes: int):
+    srv = ctypes.c_void_p()
+    check(load().plan_server_create(ctypes.byref(cfg), int(max_executors), int(device_budget),
+                                    int(max_episodes), ctypes.byref(srv)), None)
+    return srv
+
+
+def plan_server_destroy(srv):
+    check(load().plan_server_destroy(srv), None)
+
+
+def plan_submit(srv, scene, B: int, m: int = 0, episode: int = 0, seed: int = 0, fresh: int = 0):
+    arr, keep = make_scenes([scene])
+    req = PlanRequest()
+    req.scene = arr[0]
+    req.B, req.m, req.episode, req.seed, req.fresh = int(B), int(m), int(episode), int(seed), int(fresh)
+    t = ctypes.c_uint64()
+    check(load().plan_submit(srv, ctypes.byref(req), ctypes.byref(t)), None)
+    return t.value
+
+
+def plan_poll(srv, ticket: int, timeout_us: int):
+    """(status, PlanResult, latency_us); status PLAN_ETIMEOUT means not ready."""
+    out = PlanResult()
+    lat = ctypes.c_double()
+    st = load().plan_poll(srv, ctypes.c_uint64(ticket), ctypes.byref(out), ctypes.byref(lat),
+                          int(timeout_us))
+    if st not in (PLAN_OK, PLAN_ETIMEOUT):
+        check(st, None)
+    return st, out, lat.value
+
+
+def plan_end_episode(srv, episode: int):
+    check(load().plan_end_episode(srv, ctypes.c_uint64(episode)), None)
+
+
+def plan_server_info(srv):
+    st = PlanServerStats()
+    check(load().plan_server_info(srv, ctypes.byref(st)), None)
+    return {f: getattr(st, f) for f, _ in PlanServerStats._fields_}

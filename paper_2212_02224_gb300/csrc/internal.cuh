@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "plan.h"
+
 namespace plan {
 
 constexpr int kMaxCoef = 16;     // coefficients per axis
@@ -115,6 +117,11 @@ cudaError_t launch_select_update(const Layout* layout, DevCem* cem, int S, int l
                                  const double* r, const double* cu, int* elite_out,
                                  cudaStream_t s);
 
+static_assert(sizeof(DevCem) % sizeof(unsigned long long) == 0, "DevCem is copied in 8-byte words");
+
+cudaError_t launch_cem_copy(DevCem* dst, const DevCem* src, const int* idx, int S, bool scatter,
+                            cudaStream_t s);
+
 // Error message of a call that has no context (reported by plan_last_error(NULL)).
 void set_unbound_error(const char* msg);
 
@@ -124,4 +131,20 @@ cudaError_t launch_update_only(const double* p_elite, const double* cost, int q,
                                double gamma, double eta, double* mu, double* sigma,
                                cudaStream_t s);
 
+}  // namespace plan
+
+struct plan_ctx;
+namespace plan {
+// Hooks of the serving loop into a context (plan_api.cu).
+size_t ctx_bytes(const plan_ctx* ctx);
+const char* ctx_error(const plan_ctx* ctx);
+int ctx_make_state(plan_ctx* ctx, const plan_cem_state* st, int n_lanes, double lane_width,
+                   DevCem* out);
+// One Alg. 1 run over S scenes, launched directly (no graph) on `s`: scene
+// slots, states init[s] (or table[gather[s]] where gather[s] >= 0), L outer
+// iterations, then table[scatter[s]] = final state and results (pinned host,
+// S entries) = final states.
+int ctx_wave(plan_ctx* ctx, const plan_scene* scenes, const int* B, int S, const DevCem* init,
+             const int* gather, const int* scatter, DevCem* table, DevCem* results,
+             cudaStream_t s);
 }  // namespace plan

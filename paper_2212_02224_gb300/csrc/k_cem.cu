@@ -342,7 +342,29 @@ update_only_kernel(const double* p_elite, const double* cost, int q, int d_p, do
   update_moments(p_e, c_e, cmin, q, d_p, gamma, eta, mu, sigma, d_p, sh);
 }
 
+// Per-slot states from / to a table of episode states: dst[s] = src[idx[s]]
+// for idx[s] >= 0 (gather) or dst[idx[s]] = src[s] (scatter).
+__global__ void cem_copy_kernel(DevCem* dst, const DevCem* src, const int* idx, int S, int scatter) {
+  constexpr int W = sizeof(DevCem) / sizeof(unsigned long long);
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= S * W) return;
+  const int s = e / W, w = e % W;
+  const int r = idx[s];
+  if (r < 0) return;
+  const unsigned long long* a = reinterpret_cast<const unsigned long long*>(scatter ? src + s : src + r);
+  unsigned long long* b = reinterpret_cast<unsigned long long*>(scatter ? dst + r : dst + s);
+  b[w] = a[w];
+}
+
 }  // namespace
+
+cudaError_t launch_cem_copy(DevCem* dst, const DevCem* src, const int* idx, int S, bool scatter,
+                            cudaStream_t s) {
+  if (S == 0) return cudaSuccess;
+  constexpr int W = sizeof(DevCem) / sizeof(unsigned long long);
+  cem_copy_kernel<<<(S * W + 255) / 256, 256, 0, s>>>(dst, src, idx, S, scatter ? 1 : 0);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_sample(const DevScene* scenes, const Layout* layout, const DevCem* cem, int S,
                           int max_B, int l, const Params& prm, double* p, cudaStream_t s) {

@@ -51,6 +51,8 @@ struct plan_ctx {
 
   // arena
   std::vector<void*> allocs;
+  size_t arena_bytes = 0;
+  int* rows = nullptr;     // [2][max_scenes] gather / scatter rows of the serving loop
   SceneSet tr;             // transient scenes (plan_solve)
   SceneSet res;            // resident scene slots (plan_step_resident)
   DevCem* cem = nullptr;   // [max_scenes]
@@ -111,6 +113,7 @@ int dalloc(plan_ctx* ctx, T** ptr, size_t count) {
                 cudaGetErrorString(e));
   }
   ctx->allocs.push_back(p);
+  ctx->arena_bytes += count * sizeof(T);
   *ptr = static_cast<T*>(p);
   return PLAN_OK;
 }
@@ -375,6 +378,55 @@ int make_cem(plan_ctx* ctx, const plan_cem_state* st, int n_lanes, double lane_w
 
 void plan::set_unbound_error(const char* msg) { g_init_err = msg; }
 
+// ----------------------------------------------------------------- serving hooks
+
+size_t plan::ctx_bytes(const plan_ctx* ctx) { return ctx->arena_bytes; }
+
+const char* plan::ctx_error(const plan_ctx* ctx) { return ctx->err.c_str(); }
+
+int plan::ctx_make_state(plan_ctx* ctx, const plan_cem_state* st, int n_lanes, double lane_width,
+                         DevCem* out) {
+  return make_cem(ctx, st, n_lanes, lane_width, out);
+}
+
+int plan::ctx_wave(plan_ctx* ctx, const plan_scene* scenes, const int* B, int S,
+                   const DevCem* init, const int* gather, const int* scatter, DevCem* table,
+                   DevCem* results, cudaStream_t s) {
+  if (S < 1 || S > ctx->cfg.max_scenes) return fail(ctx, PLAN_ECAPACITY, "wave of %d scenes", S);
+  std::vector<int> Bv(B, B + S);
+  long long total = 0;
+  int max_B = 0;
+  for (int i = 0; i < S; ++i) {
+    if (Bv[i] < 1) return fail(ctx, PLAN_EINVAL, "B[%d] must be >= 1", i);
+    total += Bv[i];
+    max_B = std::max(max_B, Bv[i]);
+    TRY(check_scene(ctx, &scenes[i], i));
+  }
+  if (total > ctx->cfg.max_samples) return fail(ctx, PLAN_ECAPACITY, "wave exceeds max_samples");
+  CU(ctx, cudaSetDevice(ctx->device));
+  TRY(upload(ctx, ctx->res, scenes, S, &Bv, s, &ctx->res_host));
+  ctx->n_uploaded = S;
+  const size_t nb = sizeof(DevCem) * S, ni = sizeof(int) * S;
+  TRY(stage_acquire(ctx, nb + 2 * ni));
+  std::memcpy(ctx->stage, init, nb);
+  std::memcpy(ctx->stage + nb, gather, ni);
+  std::memcpy(ctx->stage + nb + ni, scatter, ni);
+  CU(ctx, cudaMemcpyAsync(ctx->cem, ctx->stage, nb, cudaMemcpyHostToDevice, s));
+  CU(ctx, cudaMemcpyAsync(ctx->rows, ctx->stage + nb, 2 * ni, cudaMemcpyHostToDevice, s));
+  TRY(stage_release(ctx, s));
+  CU(ctx, launch_cem_copy(ctx->cem, table, ctx->rows, S, false, s));
+  const int nt = n_tiles_of(Bv, pick_warps(ctx, int(total)));
+  for (int l = 1; l <= ctx->cfg.outer_iters; ++l) {
+    CU(ctx, launch_sample(ctx->res.scenes, ctx->res.layout, ctx->cem, S, max_B, l, ctx->prm, ctx->p, s));
+    CU(ctx, run_solve(ctx, ctx->res, ctx->res, nt, int(total), ctx->p, ctx->xi, ctx->r, ctx->cu, s));
+    CU(ctx, launch_select_update(ctx->res.layout, ctx->cem, S, l, ctx->prm, ctx->p, ctx->xi,
+                                 ctx->r, ctx->cu, ctx->elite, s));
+  }
+  CU(ctx, launch_cem_copy(table, ctx->cem, ctx->rows + S, S, true, s));
+  CU(ctx, cudaMemcpyAsync(results, ctx->cem, nb, cudaMemcpyDeviceToHost, s));
+  return PLAN_OK;
+}
+
 extern "C" {
 
 const char* plan_status_str(int status) {
@@ -467,6 +519,7 @@ int plan_init(const plan_config* cfg, plan_ctx** out) {
   A(dalloc(ctx, &ctx->r, B));
   A(dalloc(ctx, &ctx->cu, B));
   A(dalloc(ctx, &ctx->elite, size_t(c.max_scenes) * c.n_elite));
+  A(dalloc(ctx, &ctx->rows, size_t(2) * c.max_scenes));
   if (c.prec == PLAN_PREC_FP64) {
     A(dalloc(ctx, &ctx->pw.xibarp, B * 32));
     A(dalloc(ctx, &ctx->pw.xi, B * 32));
@@ -814,6 +867,52 @@ int plan_autotune(plan_ctx* ctx, const plan_scene* scene, int B, int* wps_out, i
   }
   *wps_out = best_w;
   *spc_out = best_s;
+  return PLAN_OK;
+}
+
+int plan_advance(const plan_config* cfg, const plan_scene* in, const double* xi, int steps,
+                 plan_scene* out, plan_obstacle* out_obs) {
+  if (!cfg || !in || !xi || !out || (in->n_obs > 0 && (!in->obs || !out_obs)))
+    return fail(nullptr, PLAN_EINVAL, "NULL argument");
+  if (cfg->m < 2 || cfg->n_coef < 2 || cfg->n_coef > kMaxCoef || !(cfg->dt > 0))
+    return fail(nullptr, PLAN_EINVAL, "invalid m, n_coef or dt");
+  if (steps < 0 || steps >= cfg->m) return fail(nullptr, PLAN_EINVAL, "steps must be in [0, m)");
+  // Bernstein polynomial of degree n-1 and its first two derivatives at
+  // tau = steps / (m - 1), through de Casteljau differences of the coefficients
+  const int n = cfg->n_coef, deg = n - 1;
+  const double tf = (cfg->m - 1) * cfg->dt, tau = double(steps) / (cfg->m - 1);
+  double st[6];
+  for (int axis = 0; axis < 2; ++axis) {
+    const double* c = xi + axis * n;
+    double d0[kMaxCoef], d1[kMaxCoef], d2[kMaxCoef];
+    for (int k = 0; k < n; ++k) d0[k] = c[k];
+    for (int k = 0; k + 1 < n; ++k) d1[k] = deg * (c[k + 1] - c[k]);
+    for (int k = 0; k + 2 < n; ++k) d2[k] = (deg - 1) * (d1[k + 1] - d1[k]);
+    auto casteljau = [&](double* b, int len) {
+      for (int r = 1; r < len; ++r)
+        for (int k = 0; k + r < len; ++k) b[k] = (1.0 - tau) * b[k] + tau * b[k + 1];
+      return len > 0 ? b[0] : 0.0;
+    };
+    st[axis] = casteljau(d0, n);
+    st[2 + axis] = casteljau(d1, n - 1) / tf;
+    st[4 + axis] = n > 2 ? casteljau(d2, n - 2) / (tf * tf) : 0.0;
+  }
+  const double t = steps * cfg->dt;
+  plan_scene o = *in;
+  o.ego.x = 0.0;
+  o.ego.y = st[1];
+  o.ego.vx = st[2];
+  o.ego.vy = st[3];
+  o.ego.ax = st[4];
+  o.ego.ay = st[5];
+  for (int i = 0; i < in->n_obs; ++i) {
+    plan_obstacle ob = in->obs[i];
+    ob.x0 = ob.x0 + ob.vx * t - st[0];
+    ob.y0 = ob.y0 + ob.vy * t;
+    out_obs[i] = ob;
+  }
+  o.obs = in->n_obs > 0 ? out_obs : nullptr;
+  *out = o;
   return PLAN_OK;
 }
 

@@ -136,3 +136,60 @@ class Planner:
         B.plan_sample(self.ctx, scene, mu, sigma, int(mu is None), l, seed, step, Bn, _ptr(p),
                       _stream(stream))
         return p
+
+
+class Server:
+    """Continuous-batching serving loop over the C ABI (plan_server_*).
+
+    Each request is one MPC cycle of an episode; episodes keep their sampling
+    distribution on the device between cycles."""
+
+    def __init__(self, params, prec: str = "fp32", max_obs: int = 32, max_samples: int = 8192,
+                 max_scenes: int = 32, max_executors: int = 4, device_budget: int = 4 << 30,
+                 max_episodes: int = 1024):
+        p = {"fp32": B.PLAN_PREC_FP32, "fp64": B.PLAN_PREC_FP64}[prec]
+        self.cfg = B.make_config(params, p, max_obs, max_samples, max_scenes)
+        self.srv = B.plan_server_create(self.cfg, max_executors, device_budget, max_episodes)
+        self.n, self.d_p = params.n_coef, 2 * params.n_seg
+
+    def submit(self, scene, Bn: int, m: int = 0, episode: int = 0, seed: int = 0, fresh: int = 0):
+        return B.plan_submit(self.srv, scene, Bn, m, episode, seed, fresh)
+
+    def poll(self, ticket: int, timeout_us: int = 1_000_000):
+        st, r, lat = B.plan_poll(self.srv, ticket, timeout_us)
+        if st == B.PLAN_ETIMEOUT:
+            return None
+        return dict(p=list(r.p[:self.d_p]), xi=list(r.xi[:2 * self.n]), cost=r.cost,
+                    resid=r.resid, cu=r.cu, index=r.index, latency_us=lat)
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        import time
+        t_end = time.time() + timeout_s
+        while time.time() < t_end:
+            r = self.poll(ticket, 100_000)
+            if r is not None:
+                return r
+        raise TimeoutError(f"ticket {ticket} not done in {timeout_s} s")
+
+    def end_episode(self, episode: int):
+        B.plan_end_episode(self.srv, episode)
+
+    def info(self):
+        return B.plan_server_info(self.srv)
+
+    def close(self):
+        if self.srv is not None:
+            B.plan_server_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def advance(params, scene, xi, steps: int = 5):
+    """Next MPC scene after executing `steps` elements of plan xi (plan_advance)."""
+    cfg = B.make_config(params, B.PLAN_PREC_FP32, 0, 1)
+    return B.plan_advance(cfg, scene, xi, steps)

@@ -1,0 +1,140 @@
+"""The serving loop (continuous batching of MPC cycles) and MPC episodes.
+
+* A request's result is the same alone and in a mix of other scenes admitted
+  into the same waves (the kernel shape is fixed per executor and every
+  sample, selection and update is per scene, so the equality is exact).
+* An episode of several cycles through the server (warm starts kept in the
+  device table, scenes advanced with plan_advance) matches the same episode
+  through plan_step, and on the FP64 path matches the oracle's episode.
+* Many requests of mixed horizons and sizes all complete; the loop batches
+  them into fewer waves than requests.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mpc
+from paper_2212_02224_gb300 import binding, scenegen as sg
+from paper_2212_02224_gb300.planner import Planner, Server, advance
+
+from gpu_common import FP32_POS_M, positions
+
+pytestmark = pytest.mark.gpu
+
+
+def _prm(**kw):
+    prm, _, _ = sg.workload(1, inner_iters=25, outer_iters=2, n_elite_c=60, n_elite=20)
+    for k, v in kw.items():
+        setattr(prm, k, v)
+    return prm
+
+
+def _scene(i, n_obs=None):
+    s = sg.Stream(900 + i)
+    n = int(s.integers(4, 16, 1)[0]) if n_obs is None else n_obs
+    return sg.make_scene(1000 + i, n_lanes=4, n_obs=n)
+
+
+def test_result_same_alone_and_in_the_mix():
+    prm = _prm()
+    target = _scene(0)
+    srv = Server(prm, max_obs=24, max_samples=4096, max_scenes=16, max_executors=2)
+    t = srv.submit(target, 300, episode=77, seed=5)
+    alone = srv.wait(t)
+    srv.close()
+
+    srv = Server(prm, max_obs=24, max_samples=4096, max_scenes=16, max_executors=2)
+    rng = np.random.default_rng(3)
+    tickets = []
+    for i in range(1, 12):
+        tickets.append(srv.submit(_scene(i), int(rng.integers(100, 600)), episode=i, seed=i))
+        if i == 6:
+            tt = srv.submit(target, 300, episode=77, seed=5)
+    mixed = srv.wait(tt)
+    others = [srv.wait(x) for x in tickets]
+    info = srv.info()
+    srv.close()
+    assert all(np.isfinite(o["cost"]) for o in others)
+    assert info["waves"] < 12           # requests shared waves
+    for key in ("p", "xi", "cost", "resid", "cu", "index"):
+        assert mixed[key] == alone[key], key
+
+
+def test_server_episode_matches_plan_step():
+    """Three cycles through the server vs three plan_step calls with the
+    distribution carried by the caller."""
+    prm = _prm()
+    sc0 = _scene(21, n_obs=10)
+    srv = Server(prm, max_obs=16, max_samples=2048, max_scenes=4, max_executors=1)
+    pl = Planner(prm, prec="fp32", max_obs=16, max_samples=2048)
+    pl.set_tuning(1, 4)                       # the executors' fixed shape
+    sc_s, sc_p = sc0, sc0
+    mu = sigma = None
+    for c in range(3):
+        r_s = srv.wait(srv.submit(sc_s, 400, episode=5, seed=11))
+        r_p = pl.step(sc_p, 400, mu=mu, sigma=sigma, seed=11, step=c)
+        mu, sigma = r_p["mu"], r_p["sigma"]
+        xs, ys = positions(np.array([r_s["xi"]]), prm)
+        xp, yp = positions(np.array([r_p["xi"]]), prm)
+        assert max(np.abs(xs - xp).max(), np.abs(ys - yp).max()) <= FP32_POS_M
+        assert abs(r_s["cost"] - r_p["cost"]) <= 1e-4 * abs(r_p["cost"]) + 1e-3
+        sc_s = advance(prm, sc_s, r_s["xi"])
+        sc_p = advance(prm, sc_p, r_p["xi"])
+    srv.close()
+    pl.close()
+
+
+def test_fp64_episode_matches_oracle_episode():
+    """Receding horizon on the FP64 path (plan_step + plan_advance) against the
+    oracle's episode (upper.plan with warm starts + mpc.advance)."""
+    prm, sc, B = sg.workload(0, inner_iters=20, outer_iters=2)
+    ref, _ = mpc.episode(sc, prm, 3, B, seed=9)
+    pl = Planner(prm, prec="fp64", max_obs=8, max_samples=B)
+    cur = sc
+    mu = sigma = None
+    for c in range(3):
+        r = pl.step(cur, B, mu=mu, sigma=sigma, seed=9, step=c)
+        assert r["index"] == ref[c]["best"]
+        np.testing.assert_allclose(r["xi"], ref[c]["xi"], rtol=1e-6, atol=1e-6)
+        np.testing.assert_allclose(r["mu"], ref[c]["mu"], rtol=1e-6, atol=1e-6)
+        mu, sigma = r["mu"], r["sigma"]
+        cur = advance(prm, cur, r["xi"])
+    pl.close()
+
+
+def test_mixed_horizons_and_sizes_complete():
+    prm = _prm()
+    srv = Server(prm, max_obs=24, max_samples=6000, max_scenes=24, max_executors=4)
+    rng = np.random.default_rng(8)
+    tickets = []
+    for i in range(40):
+        m = int(rng.choice([80, 100, 120]))
+        tickets.append(srv.submit(_scene(100 + i), int(rng.integers(64, 900)), m=m,
+                                  episode=1000 + i, seed=i))
+    res = [srv.wait(t) for t in tickets]
+    info = srv.info()
+    srv.close()
+    assert all(np.isfinite(r["cost"]) and r["latency_us"] > 0 for r in res)
+    assert info["completed"] == 40 and info["waves"] < 40 and info["executors"] >= 3
+
+
+def test_server_errors():
+    prm = _prm()
+    srv = Server(prm, max_obs=4, max_samples=512, max_scenes=4, max_executors=1, max_episodes=2)
+    with pytest.raises(binding.PlanError) as e:
+        srv.submit(_scene(1, n_obs=8), 100, episode=1)
+    assert e.value.status == binding.PLAN_ECAPACITY
+    with pytest.raises(binding.PlanError) as e:
+        srv.submit(_scene(1, n_obs=2), 513, episode=1)
+    assert e.value.status == binding.PLAN_ECAPACITY
+    srv.wait(srv.submit(_scene(1, n_obs=2), 100, episode=1))
+    srv.wait(srv.submit(_scene(2, n_obs=2), 100, episode=2))
+    with pytest.raises(binding.PlanError) as e:
+        srv.submit(_scene(3, n_obs=2), 100, episode=3)      # episode table full
+    assert e.value.status == binding.PLAN_ECAPACITY
+    srv.end_episode(1)
+    srv.wait(srv.submit(_scene(3, n_obs=2), 100, episode=3))
+    with pytest.raises(binding.PlanError) as e:
+        binding.plan_poll(srv.srv, 123456, 0)                # unknown ticket
+    assert e.value.status == binding.PLAN_EINVAL
+    srv.close()
