@@ -43,11 +43,13 @@ def test_result_same_alone_and_in_the_mix():
     alone = srv.wait(t)
     srv.close()
 
-    srv = Server(prm, max_obs=24, max_samples=4096, max_scenes=16, max_executors=2)
+    srv = Server(prm, max_obs=24, max_samples=4096, max_scenes=16, max_executors=1)
     rng = np.random.default_rng(3)
+    scenes = [_scene(i) for i in range(1, 12)]      # made up front: submissions come in a burst
+    sizes = [int(rng.integers(100, 600)) for _ in scenes]
     tickets = []
-    for i in range(1, 12):
-        tickets.append(srv.submit(_scene(i), int(rng.integers(100, 600)), episode=i, seed=i))
+    for i, (sc, b) in enumerate(zip(scenes, sizes), start=1):
+        tickets.append(srv.submit(sc, b, episode=i, seed=i))
         if i == 6:
             tt = srv.submit(target, 300, episode=77, seed=5)
     mixed = srv.wait(tt)
@@ -106,11 +108,9 @@ def test_mixed_horizons_and_sizes_complete():
     prm = _prm()
     srv = Server(prm, max_obs=24, max_samples=6000, max_scenes=24, max_executors=4)
     rng = np.random.default_rng(8)
-    tickets = []
-    for i in range(40):
-        m = int(rng.choice([80, 100, 120]))
-        tickets.append(srv.submit(_scene(100 + i), int(rng.integers(64, 900)), m=m,
-                                  episode=1000 + i, seed=i))
+    reqs = [(_scene(100 + i), int(rng.integers(64, 900)), int(rng.choice([80, 100, 120])))
+            for i in range(40)]
+    tickets = [srv.submit(sc, b, m=m, episode=1000 + i, seed=i) for i, (sc, b, m) in enumerate(reqs)]
     res = [srv.wait(t) for t in tickets]
     info = srv.info()
     srv.close()
