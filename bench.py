@@ -321,6 +321,157 @@ def reference_arm(args):
     print(json.dumps(line))
 
 
+# ----------------------------------------------------------------------------- other workloads
+
+def _timed(fn, reps, flush, stream):
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def batched_arm(args):
+    """Many scenes per MPC cycle: 256 scenes, N ~ U{4..20}, B ~ U{256..2048},
+    one graph-captured Alg. 1 run over all of them per step."""
+    import torch
+    from paper_2212_02224_gb300 import scenegen as sg
+    from paper_2212_02224_gb300.planner import Planner
+    prm, scenes, Bs = sg.batched_workload(S=256)
+    tot = sum(Bs)
+    pl = Planner(prm, prec="fp32", max_obs=20, max_samples=tot, max_scenes=len(scenes))
+    pl.set_tuning(1, 2)
+    pl.upload(scenes)
+    for i in range(len(scenes)):
+        pl.set_state(i, seed=100 + i)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        pl.step_resident(Bs)
+    with ClockSampler(0) as clk:
+        ms = _timed(lambda: pl.step_resident(Bs), args.steps, flush, stream)
+    units = tot * prm.inner_iters * prm.outer_iters
+    print(json.dumps({
+        "metric": METRIC, "workload": "batched", "value": units * len(ms) / (sum(ms) / 1e3),
+        "unit": UNIT, "scenes_per_s": len(scenes) * len(ms) / (sum(ms) / 1e3),
+        "ms_per_step": statistics.mean(ms), "p50_ms": statistics.median(ms),
+        "steps": args.steps, "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "256 scenes, N~U{4..20}, B~U{256..2048} (total %d), m=100, n=11, "
+                               "K=100, L=5, one CUDA graph per step" % tot},
+        "clocks": clk.summary()}))
+    pl.close()
+
+
+def scale_arm(args):
+    """One scene, 6 lanes, 30 obstacles, m=200, n=16, B from 1k to 32k."""
+    import torch
+    from paper_2212_02224_gb300 import scenegen as sg
+    from paper_2212_02224_gb300.planner import Planner
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    rows = []
+    for B in (1024, 2048, 4096, 8192, 16384, 32768):
+        prm, sc, _ = sg.workload(4, B=B)
+        pl = Planner(prm, prec="fp32", max_obs=32, max_samples=B)
+        pl.autotune(sc, B)
+        pl.upload([sc])
+        pl.set_state(0, seed=7)
+        for _ in range(args.warmup):
+            pl.step_resident([B])
+        ms = _timed(lambda: pl.step_resident([B]), max(3, args.steps // 4), flush, stream)
+        p = torch.tensor(sg.make_samples(3, sc, B, prm.n_seg), device="cuda")
+        ks = _timed(lambda: pl.solve(sc, p, want_xi=False), 5, flush, stream)
+        flops = algorithmic_flops_per_sample_iter(prm.m, prm.n_coef, sc.n_obs) * B * prm.inner_iters
+        rows.append({"B": B, "ms_per_cycle": statistics.median(ms),
+                     "sample_iters_per_s": B * prm.inner_iters * prm.outer_iters / (statistics.median(ms) / 1e3),
+                     "solve_ms": statistics.median(ks),
+                     "solve_tflops": flops / (statistics.median(ks) * 1e-3) / 1e12})
+        pl.close()
+    print(json.dumps({"metric": METRIC, "workload": "scale", "unit": UNIT, "dtype": "f32",
+                      "config": {"workload": "6 lanes, N=30, m=200, n=16, K=100, L=5"},
+                      "rows": rows}))
+
+
+def serving_arm(args):
+    """Served MPC loop: Poisson arrivals of cycle requests at `rate` per second
+    over rolling 50-cycle episodes (N 4..24, B 512..2048, horizon in
+    {80, 100, 125, 150}); each episode advances its scene by plan_advance after
+    every result.  Latency = submission to completion inside the server."""
+    import numpy as np
+    from paper_2212_02224_gb300 import scenegen as sg
+    from paper_2212_02224_gb300.planner import Server, advance
+    prm, _, _ = sg.workload(1)
+    srv = Server(prm, max_obs=24, max_samples=16384, max_scenes=32, max_executors=8,
+                 device_budget=16 << 30, max_episodes=4096)
+    rng = np.random.default_rng(11)
+    s = sg.Stream(4242)
+    n_ep = 64
+    eps = []
+    for e in range(n_ep):
+        sc = sg.make_scene(50000 + e, n_lanes=4, n_obs=int(s.integers(4, 24, 1)[0]))
+        eps.append(dict(id=e, scene=sc, B=int(s.integers(512, 2048, 1)[0]),
+                        m=int(rng.choice([80, 100, 125, 150])), cycle=0, busy=False, ticket=None))
+    # warm the executors (one per horizon) before timing
+    for m in (80, 100, 125, 150):
+        srv.wait(srv.submit(eps[0]["scene"], 512, m=m, episode=10**9 + m, seed=1))
+        srv.end_episode(10**9 + m)
+    lat, done_units = [], 0
+    t0 = time.perf_counter()
+    next_arrival = t0
+    duration = args.serve_seconds
+    submitted = completed = dropped = 0
+    next_ep_id = n_ep
+    while True:
+        now = time.perf_counter()
+        if now - t0 > duration and all(not e["busy"] for e in eps):
+            break
+        if now >= next_arrival and now - t0 <= duration:
+            idle = [e for e in eps if not e["busy"]]
+            if idle:
+                e = idle[rng.integers(len(idle))]
+                e["ticket"] = srv.submit(e["scene"], e["B"], m=e["m"], episode=e["id"], seed=e["id"])
+                e["busy"] = True
+                submitted += 1
+            else:
+                dropped += 1
+            next_arrival += rng.exponential(1.0 / args.rate)
+        for e in eps:
+            if e["busy"]:
+                r = srv.poll(e["ticket"], 0)
+                if r is not None:
+                    e["busy"] = False
+                    completed += 1
+                    lat.append(r["latency_us"] / 1e3)
+                    done_units += e["B"] * prm.inner_iters * prm.outer_iters
+                    e["cycle"] += 1
+                    if e["cycle"] >= 50:              # episode over: a new vehicle takes the slot
+                        srv.end_episode(e["id"])
+                        e["id"], e["cycle"] = next_ep_id, 0
+                        next_ep_id += 1
+                        e["scene"] = sg.make_scene(60000 + e["id"], n_lanes=4,
+                                                   n_obs=int(s.integers(4, 24, 1)[0]))
+                    else:
+                        e["scene"] = advance(prm, e["scene"], r["xi"])
+    wall = time.perf_counter() - t0
+    info = srv.info()
+    srv.close()
+    print(json.dumps({
+        "metric": METRIC, "workload": "serving", "rate_req_s": args.rate,
+        "achieved_req_s": completed / wall, "value": done_units / wall, "unit": UNIT,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "mean": float(np.mean(lat))},
+        "submitted": submitted, "completed": completed,
+        "arrivals_without_idle_episode": dropped, "waves": info["waves"],
+        "max_wave": info["max_wave"], "executors": info["executors"], "dtype": "f32",
+        "config": {"workload": "Poisson arrivals over 64 rolling 50-cycle episodes, N 4..24, "
+                               "B 512..2048, m in {80,100,125,150}, K=100, L=5, elites 150/50"}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -329,9 +480,18 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--workload", default="dense", choices=["dense", "batched", "scale", "serving"])
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: requests per second")
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "batched":
+        batched_arm(args)
+    elif args.workload == "scale":
+        scale_arm(args)
+    elif args.workload == "serving":
+        serving_arm(args)
     else:
         gpu_arm(args)
 
