@@ -115,7 +115,7 @@ cudaError_t launch_sample(const DevScene* scenes, const Layout* layout, const De
 cudaError_t launch_select_update(const Layout* layout, DevCem* cem, int S, int l,
                                  const Params& prm, const double* p, const double* xi,
                                  const double* r, const double* cu, int* elite_out,
-                                 cudaStream_t s);
+                                 int max_B, cudaStream_t s);
 
 static_assert(sizeof(DevCem) % sizeof(unsigned long long) == 0, "DevCem is copied in 8-byte words");
 

@@ -342,6 +342,200 @@ update_only_kernel(const double* p_elite, const double* cost, int q, int d_p, do
   update_moments(p_e, c_e, cmin, q, d_p, gamma, eta, mu, sigma, d_p, sh);
 }
 
+// ---------------------------------------------------------------------------
+// Warp-per-scene selection for B <= kWarpMaxB: the same ConstraintEliteSet /
+// EliteSet and distribution update as the block kernels above, with only
+// warp-level synchronisation.  Keys live in shared memory (per warp).
+constexpr int kWarpMaxB = 2048;
+constexpr int kWarpMaxC = 1024;
+constexpr int kWarpsPerCta = 4;
+
+struct WarpSel {
+  unsigned long long key[kWarpMaxB];   // order keys of r, then of the candidates' costs
+  int cand[kWarpMaxC];
+  unsigned hist[256];
+  double sw[kWarpMaxC];
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ConstraintEliteSet of one scene into ws.cand[0..n_c) (increasing index order).
+__device__ void warp_constraint_set(const double* r, int B, int n_c, WarpSel& ws) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < B; i += 32) ws.key[i] = ord_key(r[i]);
+  __syncwarp();
+  unsigned long long prefix = 0ull;
+  int need = n_c;
+  for (int shift = 56; shift >= 0; shift -= 8) {
+    for (int d = lane; d < 256; d += 32) ws.hist[d] = 0u;
+    __syncwarp();
+    for (int i = lane; i < B; i += 32) {
+      const unsigned long long k = ws.key[i];
+      if (shift == 56 || ((k ^ prefix) >> (shift + 8)) == 0ull)
+        atomicAdd(&ws.hist[(k >> shift) & 255ull], 1u);
+    }
+    __syncwarp();
+    unsigned loc = 0;
+    for (int d = 0; d < 8; ++d) loc += ws.hist[8 * lane + d];
+    unsigned incl = loc;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const unsigned hit = __ballot_sync(0xffffffffu, incl >= unsigned(need));
+    const int first = __ffs(hit) - 1;
+    int digit = 0, cum = 0;
+    if (lane == first) {
+      unsigned c = incl - loc;
+      int d = 8 * lane;
+      for (; d < 8 * lane + 7; ++d) {
+        if (c + ws.hist[d] >= unsigned(need)) break;
+        c += ws.hist[d];
+      }
+      digit = d;
+      cum = int(c);
+    }
+    digit = __shfl_sync(0xffffffffu, digit, first < 0 ? 0 : first);
+    cum = __shfl_sync(0xffffffffu, cum, first < 0 ? 0 : first);
+    need -= cum;
+    prefix |= static_cast<unsigned long long>(digit) << shift;
+    __syncwarp();
+  }
+  const unsigned long long T = prefix;
+  const unsigned lt = (1u << lane) - 1u;
+  int ties = 0, sel = 0;
+  for (int base = 0; base < B; base += 32) {
+    const int i = base + lane;
+    const unsigned long long k = i < B ? ws.key[i] : ~0ull;
+    const bool less = i < B && k < T, eq = i < B && k == T;
+    const unsigned em = __ballot_sync(0xffffffffu, eq);
+    const bool take = less || (eq && ties + __popc(em & lt) < need);
+    const unsigned tm = __ballot_sync(0xffffffffu, take);
+    const int pos = sel + __popc(tm & lt);
+    if (take && pos < n_c) ws.cand[pos] = i;
+    ties += __popc(em);
+    sel += __popc(tm);
+  }
+  __syncwarp();
+}
+
+// EliteSet: the candidates sorted by (cu + r, index) into ws.cand[0..n_c).
+__device__ void warp_elite_sort(const double* r, const double* cu, int B, int n_c, WarpSel& ws) {
+  const int lane = threadIdx.x & 31;
+  int P = 1;
+  while (P < n_c) P <<= 1;
+  for (int i = lane; i < P; i += 32) {
+    const int id = i < n_c ? ws.cand[i] : -1;
+    if (id >= 0 && id < B) {
+      ws.key[i] = ord_key(cu[id] + r[id]);
+    } else {
+      ws.key[i] = ~0ull;
+      ws.cand[i] = 0x7fffffff;
+    }
+  }
+  __syncwarp();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int i = lane; i < P; i += 32) {
+        const int ixj = i ^ jj;
+        if (ixj > i) {
+          const bool asc = (i & k) == 0;
+          const unsigned long long ka = ws.key[i], kb = ws.key[ixj];
+          const int ia = ws.cand[i], ib = ws.cand[ixj];
+          const bool gt = (ka > kb) || (ka == kb && ia > ib);
+          if (gt == asc) {
+            ws.key[i] = kb; ws.key[ixj] = ka;
+            ws.cand[i] = ib; ws.cand[ixj] = ia;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(32 * kWarpsPerCta)
+select_update_warp_kernel(const Layout* layout, DevCem* cem, int S, int l, Params prm,
+                          const double* p, const double* xi, const double* r, const double* cu,
+                          int* elite_out) {
+  extern __shared__ __align__(16) unsigned char shraw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.x * kWarpsPerCta + warp;
+  if (s >= S) return;
+  WarpSel& ws = reinterpret_cast<WarpSel*>(shraw)[warp];
+  const Layout lay = layout[s];
+  DevCem& st = cem[s];
+  const int B = lay.B;
+  if (B <= 0) return;
+  const double* rs = r + lay.off;
+  const double* cs = cu + lay.off;
+  const int n_c = min(prm.n_c > 0 ? prm.n_c : 3 * prm.q, B);
+  const int q = min(prm.q, n_c);
+  warp_constraint_set(rs, B, n_c, ws);
+  warp_elite_sort(rs, cs, B, n_c, ws);
+  const int d_p = prm.d_p;
+  const double* ps = p + size_t(lay.off) * d_p;
+  auto id_of = [&](int e) { const int id = ws.cand[e]; return (id >= 0 && id < B) ? id : 0; };
+  // Eqs. (mean_update, cov_update, s_formula), lanes over elites
+  const double cmin = cs[id_of(0)] + rs[id_of(0)];
+  for (int e = lane; e < q; e += 32) {
+    const int id = id_of(e);
+    ws.sw[e] = exp(-(cs[id] + rs[id] - cmin) / prm.gamma);
+  }
+  __syncwarp();
+  double part = 0.0;
+  for (int e = lane; e < q; e += 32) part += ws.sw[e];
+  const double Ssum = warp_sum(part);
+  double mu_new[kMaxDp];
+  for (int a = 0; a < d_p; ++a) {
+    double v = 0.0;
+    for (int e = lane; e < q; e += 32) v += ws.sw[e] * ps[size_t(id_of(e)) * d_p + a];
+    mu_new[a] = (1.0 - prm.eta) * st.mu[a] + prm.eta * warp_sum(v) / Ssum;
+  }
+  double sg_new[kMaxDp * kMaxDp];
+  for (int a = 0; a < d_p; ++a) {
+    for (int b = 0; b < d_p; ++b) {
+      double v = 0.0;
+      for (int e = lane; e < q; e += 32) {
+        const double* pe = ps + size_t(id_of(e)) * d_p;
+        v += ws.sw[e] * (pe[a] - mu_new[a]) * (pe[b] - mu_new[b]);
+      }
+      sg_new[a * kMaxDp + b] = (1.0 - prm.eta) * st.sigma[a * kMaxDp + b] + prm.eta * warp_sum(v) / Ssum;
+    }
+  }
+  __syncwarp();
+  const int best = id_of(0);
+  if (lane == 0) {
+    for (int a = 0; a < d_p; ++a) {
+      st.mu[a] = mu_new[a];
+      for (int b = 0; b < d_p; ++b) st.sigma[a * kMaxDp + b] = sg_new[a * kMaxDp + b];
+    }
+    cholesky(st.sigma, prm.cov_eps, d_p, st.chol);
+    st.best_index = best;
+    st.best_r = rs[best];
+    st.best_cu = cs[best];
+    st.best_cost = cs[best] + rs[best];
+    if (l == prm.L) { st.fresh = 0; st.step += 1ull; }
+  }
+  for (int a = lane; a < d_p; a += 32) st.best_p[a] = ps[size_t(best) * d_p + a];
+  for (int a = lane; a < 2 * prm.n; a += 32) st.best_xi[a] = xi[size_t(lay.off + best) * 2 * prm.n + a];
+  if (elite_out != nullptr)
+    for (int e = lane; e < q; e += 32) elite_out[size_t(s) * prm.q + e] = ws.cand[e];
+}
+
+__global__ void __launch_bounds__(32)
+select_only_warp_kernel(const double* r, const double* cu, int B, int n_c, int q, int* elite) {
+  extern __shared__ __align__(16) unsigned char shraw[];
+  WarpSel& ws = *reinterpret_cast<WarpSel*>(shraw);
+  warp_constraint_set(r, B, n_c, ws);
+  warp_elite_sort(r, cu, B, n_c, ws);
+  for (int e = threadIdx.x; e < q; e += 32) elite[e] = ws.cand[e];
+}
+
 // Per-slot states from / to a table of episode states: dst[s] = src[idx[s]]
 // for idx[s] >= 0 (gather) or dst[idx[s]] = src[s] (scatter).
 __global__ void cem_copy_kernel(DevCem* dst, const DevCem* src, const int* idx, int S, int scatter) {
@@ -383,15 +577,25 @@ static void sel_attr() {
                        int(sizeof(SelShared)));
   cudaFuncSetAttribute(update_only_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        int(sizeof(SelShared)));
+  cudaFuncSetAttribute(select_update_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       int(sizeof(WarpSel) * kWarpsPerCta));
+  cudaFuncSetAttribute(select_only_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       int(sizeof(WarpSel)));
   g_sel_attr = true;
 }
 
 cudaError_t launch_select_update(const Layout* layout, DevCem* cem, int S, int l,
                                  const Params& prm, const double* p, const double* xi,
                                  const double* r, const double* cu, int* elite_out,
-                                 cudaStream_t s) {
+                                 int max_B, cudaStream_t s) {
   if (S == 0) return cudaSuccess;
   sel_attr();
+  if (max_B <= kWarpMaxB && (prm.n_c > 0 ? prm.n_c : 3 * prm.q) <= kWarpMaxC) {
+    select_update_warp_kernel<<<(S + kWarpsPerCta - 1) / kWarpsPerCta, 32 * kWarpsPerCta,
+                                sizeof(WarpSel) * kWarpsPerCta, s>>>(layout, cem, S, l, prm, p, xi,
+                                                                     r, cu, elite_out);
+    return cudaGetLastError();
+  }
   select_update_kernel<<<S, kSelThreads, sizeof(SelShared), s>>>(layout, cem, l, prm, p, xi, r, cu,
                                                                  elite_out);
   return cudaGetLastError();
@@ -400,6 +604,10 @@ cudaError_t launch_select_update(const Layout* layout, DevCem* cem, int S, int l
 cudaError_t launch_select_only(const double* r, const double* cu, int B, int n_c, int q,
                                int* elite, cudaStream_t s) {
   sel_attr();
+  if (B <= kWarpMaxB && n_c <= kWarpMaxC) {
+    select_only_warp_kernel<<<1, 32, sizeof(WarpSel), s>>>(r, cu, B, n_c, q, elite);
+    return cudaGetLastError();
+  }
   select_only_kernel<<<1, kSelThreads, sizeof(SelShared), s>>>(r, cu, B, n_c, q, elite);
   return cudaGetLastError();
 }

@@ -420,7 +420,7 @@ int plan::ctx_wave(plan_ctx* ctx, const plan_scene* scenes, const int* B, int S,
     CU(ctx, launch_sample(ctx->res.scenes, ctx->res.layout, ctx->cem, S, max_B, l, ctx->prm, ctx->p, s));
     CU(ctx, run_solve(ctx, ctx->res, ctx->res, nt, int(total), ctx->p, ctx->xi, ctx->r, ctx->cu, s));
     CU(ctx, launch_select_update(ctx->res.layout, ctx->cem, S, l, ctx->prm, ctx->p, ctx->xi,
-                                 ctx->r, ctx->cu, ctx->elite, s));
+                                 ctx->r, ctx->cu, ctx->elite, max_B, s));
   }
   CU(ctx, launch_cem_copy(table, ctx->cem, ctx->rows + S, S, true, s));
   CU(ctx, cudaMemcpyAsync(results, ctx->cem, nb, cudaMemcpyDeviceToHost, s));
@@ -682,7 +682,7 @@ int plan_step_resident(plan_ctx* ctx, const int* B, int S, void* stream) {
                        ctx->capture);
       if (ce == cudaSuccess)
         ce = launch_select_update(e.set.layout, ctx->cem, S, l, ctx->prm, ctx->p, ctx->xi, ctx->r,
-                                  ctx->cu, ctx->elite, ctx->capture);
+                                  ctx->cu, ctx->elite, max_B, ctx->capture);
     }
     cudaError_t ee = cudaStreamEndCapture(ctx->capture, &graph);
     if (ce != cudaSuccess || ee != cudaSuccess) {
