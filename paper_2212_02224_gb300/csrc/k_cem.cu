@@ -229,33 +229,52 @@ __device__ void select_elite_set(const double* r, const double* cu, int B, int n
 }
 
 // Eqs. (mean_update, cov_update, s_formula) over the q elites p_e(e), costs c_e(e).
+// The elite rows are staged into shared memory (`stage`, `cap` doubles) with
+// one parallel load per chunk; every sum still runs over e in increasing order
+// in one thread, so the result does not depend on the chunking.
 template <class PE, class CE>
 __device__ void update_moments(PE p_e, CE c_e, double cmin, int q, int d_p, double gamma,
-                               double eta, double* mu, double* sigma, int ld, SelShared& sh) {
+                               double eta, double* mu, double* sigma, int ld, double* sw,
+                               double* accum, double* stage, int cap) {
   const int tid = threadIdx.x;
-  for (int e = tid; e < q; e += blockDim.x) sh.sw[e] = exp(-(c_e(e) - cmin) / gamma);
+  for (int e = tid; e < q; e += blockDim.x) sw[e] = exp(-(c_e(e) - cmin) / gamma);
   __syncthreads();
-  double* mu_new = sh.acc;
-  double* ssum = sh.acc + kMaxDp;
+  double* mu_new = accum;
+  double* ssum = accum + kMaxDp;
   if (tid == 0) {
     double S = 0.0;
-    for (int e = 0; e < q; ++e) S += sh.sw[e];
+    for (int e = 0; e < q; ++e) S += sw[e];
     *ssum = S;
   }
-  __syncthreads();
-  if (tid < d_p) {
-    double a = 0.0;
-    for (int e = 0; e < q; ++e) a += sh.sw[e] * p_e(e, tid);
-    mu_new[tid] = (1.0 - eta) * mu[tid] + eta * a / *ssum;
+  const int ch = cap / d_p;                 // elites per staged chunk
+  const bool resident = q <= ch;            // one chunk holds them all
+  auto load = [&](int e0, int ne) {
+    for (int t = tid; t < ne * d_p; t += blockDim.x) stage[t] = p_e(e0 + t / d_p, t % d_p);
+  };
+  double acc_mu = 0.0;
+  for (int e0 = 0; e0 < q; e0 += ch) {
+    const int ne = min(ch, q - e0);
+    load(e0, ne);
+    __syncthreads();
+    if (tid < d_p)
+      for (int e = 0; e < ne; ++e) acc_mu += sw[e0 + e] * stage[e * d_p + tid];
+    __syncthreads();
   }
-  __syncthreads();
-  if (tid < d_p * d_p) {
-    const int a = tid / d_p, b = tid % d_p;
-    double acc = 0.0;
-    for (int e = 0; e < q; ++e)
-      acc += sh.sw[e] * (p_e(e, a) - mu_new[a]) * (p_e(e, b) - mu_new[b]);
+  if (tid < d_p) mu_new[tid] = (1.0 - eta) * mu[tid] + eta * acc_mu / *ssum;
+  if (!resident) __syncthreads();
+  const int a = tid / d_p, b = tid % d_p;
+  double acc = 0.0;
+  for (int e0 = 0; e0 < q; e0 += ch) {
+    const int ne = min(ch, q - e0);
+    if (!resident) load(e0, ne);
+    __syncthreads();
+    if (tid < d_p * d_p)
+      for (int e = 0; e < ne; ++e)
+        acc += sw[e0 + e] * (stage[e * d_p + a] - mu_new[a]) * (stage[e * d_p + b] - mu_new[b]);
+    if (!resident) __syncthreads();
+  }
+  if (tid < d_p * d_p)
     sigma[a * ld + b] = (1.0 - eta) * sigma[a * ld + b] + eta * acc / *ssum;
-  }
   __syncthreads();
   if (tid < d_p) mu[tid] = mu_new[tid];
   __syncthreads();
@@ -299,7 +318,9 @@ select_update_kernel(const Layout* layout, DevCem* cem, int l, Params prm, const
   auto id_of = [&](int e) { const int id = sh.idx[e]; return (id >= 0 && id < B) ? id : 0; };
   auto p_e = [&](int e, int a) { return ps[size_t(id_of(e)) * d_p + a]; };
   auto c_e = [&](int e) { return cs[id_of(e)] + rs[id_of(e)]; };
-  update_moments(p_e, c_e, c_e(0), q, d_p, prm.gamma, prm.eta, st.mu, st.sigma, kMaxDp, sh);
+  // the order keys are no longer needed: their space stages the elite rows
+  update_moments(p_e, c_e, c_e(0), q, d_p, prm.gamma, prm.eta, st.mu, st.sigma, kMaxDp, sh.sw,
+                 sh.acc, reinterpret_cast<double*>(sh.key), int(sizeof(sh.key) / sizeof(double)));
   const int best = id_of(0);
   if (threadIdx.x == 0) {
     cholesky(st.sigma, prm.cov_eps, d_p, st.chol);
@@ -339,134 +360,198 @@ update_only_kernel(const double* p_elite, const double* cost, int q, int d_p, do
   __syncthreads();
   auto p_e = [&](int e, int a) { return p_elite[size_t(e) * d_p + a]; };
   auto c_e = [&](int e) { return cost[e]; };
-  update_moments(p_e, c_e, cmin, q, d_p, gamma, eta, mu, sigma, d_p, sh);
+  update_moments(p_e, c_e, cmin, q, d_p, gamma, eta, mu, sigma, d_p, sh.sw, sh.acc,
+                 reinterpret_cast<double*>(sh.key), int(sizeof(sh.key) / sizeof(double)));
 }
 
 // ---------------------------------------------------------------------------
-// Warp-per-scene selection for B <= kWarpMaxB: the same ConstraintEliteSet /
-// EliteSet and distribution update as the block kernels above, with only
-// warp-level synchronisation.  Keys live in shared memory (per warp).
-constexpr int kWarpMaxB = 2048;
-constexpr int kWarpMaxC = 1024;
-constexpr int kWarpsPerCta = 4;
+// Selection for B <= kSmallMaxB, one 256-thread block per scene, the order
+// keys staged in shared memory once.  Same sets as above: ConstraintEliteSet
+// (n_c lowest r) and EliteSet (q lowest cu + r among them, sorted), ties to
+// the lower sample index.
+constexpr int kSmallMaxB = 2048;
+constexpr int kSmallMaxC = 1024;
+constexpr int kSmallThreads = 256;
 
-struct WarpSel {
-  unsigned long long key[kWarpMaxB];   // order keys of r, then of the candidates' costs
-  int cand[kWarpMaxC];
+struct SmallSel {
+  unsigned long long key[kSmallMaxB];    // order keys of r
+  unsigned long long ckey[kSmallMaxC];   // order keys of cu + r of the candidates
+  int cand[kSmallMaxC];                  // ConstraintEliteSet, increasing sample index
+  int idx[kSmallMaxC];                   // EliteSet, sorted by (cost, index)
   unsigned hist[256];
-  double sw[kWarpMaxC];
+  unsigned wl[32], we[32];
+  unsigned long long gkey[32];
+  int gidx[32];
+  unsigned long long prefix, tk;
+  int need, gc, gcount, ti;
+  double sw[kSmallMaxC];
+  double acc[kMaxDp * kMaxDp + kMaxDp + 1];
 };
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// ConstraintEliteSet of one scene into ws.cand[0..n_c) (increasing index order).
-__device__ void warp_constraint_set(const double* r, int B, int n_c, WarpSel& ws) {
-  const int lane = threadIdx.x & 31;
-  for (int i = lane; i < B; i += 32) ws.key[i] = ord_key(r[i]);
-  __syncwarp();
-  unsigned long long prefix = 0ull;
-  int need = n_c;
-  for (int shift = 56; shift >= 0; shift -= 8) {
-    for (int d = lane; d < 256; d += 32) ws.hist[d] = 0u;
-    __syncwarp();
-    for (int i = lane; i < B; i += 32) {
-      const unsigned long long k = ws.key[i];
-      if (shift == 56 || ((k ^ prefix) >> (shift + 8)) == 0ull)
-        atomicAdd(&ws.hist[(k >> shift) & 255ull], 1u);
-    }
-    __syncwarp();
-    unsigned loc = 0;
-    for (int d = 0; d < 8; ++d) loc += ws.hist[8 * lane + d];
-    unsigned incl = loc;
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    const unsigned hit = __ballot_sync(0xffffffffu, incl >= unsigned(need));
-    const int first = __ffs(hit) - 1;
-    int digit = 0, cum = 0;
-    if (lane == first) {
-      unsigned c = incl - loc;
-      int d = 8 * lane;
-      for (; d < 8 * lane + 7; ++d) {
-        if (c + ws.hist[d] >= unsigned(need)) break;
-        c += ws.hist[d];
-      }
-      digit = d;
-      cum = int(c);
-    }
-    digit = __shfl_sync(0xffffffffu, digit, first < 0 ? 0 : first);
-    cum = __shfl_sync(0xffffffffu, cum, first < 0 ? 0 : first);
-    need -= cum;
-    prefix |= static_cast<unsigned long long>(digit) << shift;
-    __syncwarp();
-  }
-  const unsigned long long T = prefix;
+// The k smallest of key[0..count) by (key, position), written as positions to
+// out[0..k) in increasing order.  Radix select on 8-bit digits (shared-memory
+// counts, one atomic per distinct digit within a warp) that stops as soon as
+// the group sharing the selected prefix is either taken whole or has at most
+// 32 members (ranked directly); then an ordered compaction.
+__device__ void small_select(const unsigned long long* key, int count, int k, int* out,
+                             SmallSel& sh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  int ties = 0, sel = 0;
-  for (int base = 0; base < B; base += 32) {
+  if (k >= count) {
+    for (int i = tid; i < count; i += blockDim.x) out[i] = i;
+    __syncthreads();
+    return;
+  }
+  unsigned long long P = 0ull;
+  int need = k, gc = count, shift = 56;
+  if (tid == 0) sh.gcount = 0;
+  for (shift = 56;; shift -= 8) {
+    for (int d = tid; d < 256; d += blockDim.x) sh.hist[d] = 0u;
+    __syncthreads();
+    for (int base = 0; base < count; base += blockDim.x) {
+      const int i = base + tid;
+      bool in = false;
+      unsigned dig = 256u + lane;              // distinct for lanes that count nothing
+      if (i < count) {
+        const unsigned long long kk = key[i];
+        in = shift == 56 || ((kk ^ P) >> (shift + 8)) == 0ull;
+        if (in) dig = unsigned((kk >> shift) & 255ull);
+      }
+      const unsigned grp = __match_any_sync(0xffffffffu, dig);
+      if (in && (__ffs(grp) - 1) == lane) atomicAdd(&sh.hist[dig], unsigned(__popc(grp)));
+    }
+    __syncthreads();
+    if (warp == 0) {
+      unsigned loc = 0;
+      for (int d = 0; d < 8; ++d) loc += sh.hist[8 * lane + d];
+      unsigned incl = loc;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const unsigned hit = __ballot_sync(0xffffffffu, incl >= unsigned(need));
+      const int first = hit ? __ffs(hit) - 1 : 31;
+      if (lane == first) {
+        unsigned c = incl - loc;
+        int d = 8 * lane;
+        for (; d < 8 * lane + 7; ++d) {
+          if (c + sh.hist[d] >= unsigned(need)) break;
+          c += sh.hist[d];
+        }
+        sh.prefix = P | (static_cast<unsigned long long>(d) << shift);
+        sh.need = need - int(c);
+        sh.gc = int(sh.hist[d]);
+      }
+    }
+    __syncthreads();
+    P = sh.prefix;
+    need = sh.need;
+    gc = sh.gc;
+    if (gc == need || gc <= 32 || shift == 0) break;
+  }
+  // mode 2: the whole prefix group is taken; mode 1: threshold (tk, ti) of the
+  // group's need-th member; mode 0: key < P, then ties of P in position order.
+  int mode = gc == need ? 2 : (gc <= 32 ? 1 : 0);
+  unsigned long long tk = 0ull;
+  int ti = 0;
+  if (mode == 1) {
+    for (int base = 0; base < count; base += blockDim.x) {
+      const int i = base + tid;
+      const bool g = i < count && ((key[i] ^ P) >> shift) == 0ull;
+      const unsigned gm = __ballot_sync(0xffffffffu, g);
+      int at = 0;
+      if (lane == 0 && gm) at = atomicAdd(&sh.gcount, __popc(gm));
+      at = __shfl_sync(0xffffffffu, at, 0);
+      if (g) {
+        const int pos = at + __popc(gm & lt);
+        if (pos < 32) { sh.gkey[pos] = key[i]; sh.gidx[pos] = i; }
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const int n = min(gc, 32);
+      if (lane < n) {
+        const unsigned long long kg = sh.gkey[lane];
+        const int ig = sh.gidx[lane];
+        int rank = 0;
+        for (int h = 0; h < n; ++h) {
+          const unsigned long long kh = sh.gkey[h];
+          rank += (kh < kg || (kh == kg && sh.gidx[h] < ig)) ? 1 : 0;
+        }
+        if (rank == need - 1) { sh.tk = kg; sh.ti = ig; }
+      }
+    }
+    __syncthreads();
+    tk = sh.tk;
+    ti = sh.ti;
+  }
+  const int per = ((count + 32 * nw - 1) / (32 * nw)) * 32;
+  const int lo = warp * per, hi = min(count, lo + per);
+  auto flags = [&](int i, bool& less, bool& eq) {
+    less = eq = false;
+    if (i >= hi) return;
+    const unsigned long long kk = key[i];
+    if (mode == 2) less = (kk >> shift) <= (P >> shift);
+    else if (mode == 1) less = kk < tk || (kk == tk && i <= ti);
+    else { less = kk < P; eq = kk == P; }
+  };
+  unsigned cl = 0, ce = 0;
+  for (int base = lo; base < hi; base += 32) {
+    bool less, eq;
+    flags(base + lane, less, eq);
+    cl += __popc(__ballot_sync(0xffffffffu, less));
+    ce += __popc(__ballot_sync(0xffffffffu, eq));
+  }
+  if (lane == 0) { sh.wl[warp] = cl; sh.we[warp] = ce; }
+  __syncthreads();
+  int lb = 0, eb = 0;
+  for (int w = 0; w < warp; ++w) { lb += int(sh.wl[w]); eb += int(sh.we[w]); }
+  int sel = lb + min(eb, need), ties = eb;
+  for (int base = lo; base < hi; base += 32) {
     const int i = base + lane;
-    const unsigned long long k = i < B ? ws.key[i] : ~0ull;
-    const bool less = i < B && k < T, eq = i < B && k == T;
+    bool less, eq;
+    flags(i, less, eq);
     const unsigned em = __ballot_sync(0xffffffffu, eq);
     const bool take = less || (eq && ties + __popc(em & lt) < need);
     const unsigned tm = __ballot_sync(0xffffffffu, take);
     const int pos = sel + __popc(tm & lt);
-    if (take && pos < n_c) ws.cand[pos] = i;
+    if (take && pos < k) out[pos] = i;
     ties += __popc(em);
     sel += __popc(tm);
   }
-  __syncwarp();
+  __syncthreads();
 }
 
-// EliteSet: the candidates sorted by (cu + r, index) into ws.cand[0..n_c).
-__device__ void warp_elite_sort(const double* r, const double* cu, int B, int n_c, WarpSel& ws) {
-  const int lane = threadIdx.x & 31;
-  int P = 1;
-  while (P < n_c) P <<= 1;
-  for (int i = lane; i < P; i += 32) {
-    const int id = i < n_c ? ws.cand[i] : -1;
-    if (id >= 0 && id < B) {
-      ws.key[i] = ord_key(cu[id] + r[id]);
-    } else {
-      ws.key[i] = ~0ull;
-      ws.cand[i] = 0x7fffffff;
-    }
+// ConstraintEliteSet into sh.cand[0..n_c), EliteSet sorted into sh.idx[0..q).
+__device__ void small_elites(const double* r, const double* cu, int B, int n_c, int q,
+                             SmallSel& sh) {
+  for (int i = threadIdx.x; i < B; i += blockDim.x) sh.key[i] = ord_key(r[i]);
+  __syncthreads();
+  small_select(sh.key, B, n_c, sh.cand, sh);
+  for (int c = threadIdx.x; c < n_c; c += blockDim.x) {
+    const int id = sh.cand[c];
+    sh.ckey[c] = ord_key(cu[id] + r[id]);
   }
-  __syncwarp();
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int jj = k >> 1; jj > 0; jj >>= 1) {
-      for (int i = lane; i < P; i += 32) {
-        const int ixj = i ^ jj;
-        if (ixj > i) {
-          const bool asc = (i & k) == 0;
-          const unsigned long long ka = ws.key[i], kb = ws.key[ixj];
-          const int ia = ws.cand[i], ib = ws.cand[ixj];
-          const bool gt = (ka > kb) || (ka == kb && ia > ib);
-          if (gt == asc) {
-            ws.key[i] = kb; ws.key[ixj] = ka;
-            ws.cand[i] = ib; ws.cand[ixj] = ia;
-          }
-        }
-      }
-      __syncwarp();
+  __syncthreads();
+  // candidates are in increasing sample index: rank by (cost key, position)
+  for (int c = threadIdx.x; c < n_c; c += blockDim.x) {
+    const unsigned long long kc = sh.ckey[c];
+    int rank = 0;
+    for (int h = 0; h < n_c; ++h) {
+      const unsigned long long kh = sh.ckey[h];
+      rank += (kh < kc || (kh == kc && h < c)) ? 1 : 0;
     }
+    if (rank < q) sh.idx[rank] = sh.cand[c];
   }
+  __syncthreads();
 }
 
-__global__ void __launch_bounds__(32 * kWarpsPerCta)
-select_update_warp_kernel(const Layout* layout, DevCem* cem, int S, int l, Params prm,
-                          const double* p, const double* xi, const double* r, const double* cu,
-                          int* elite_out) {
+__global__ void __launch_bounds__(kSmallThreads)
+select_update_small_kernel(const Layout* layout, DevCem* cem, int l, Params prm, const double* p,
+                           const double* xi, const double* r, const double* cu, int* elite_out) {
   extern __shared__ __align__(16) unsigned char shraw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = blockIdx.x * kWarpsPerCta + warp;
-  if (s >= S) return;
-  WarpSel& ws = reinterpret_cast<WarpSel*>(shraw)[warp];
+  SmallSel& sh = *reinterpret_cast<SmallSel*>(shraw);
+  const int s = blockIdx.x;
   const Layout lay = layout[s];
   DevCem& st = cem[s];
   const int B = lay.B;
@@ -475,45 +560,17 @@ select_update_warp_kernel(const Layout* layout, DevCem* cem, int S, int l, Param
   const double* cs = cu + lay.off;
   const int n_c = min(prm.n_c > 0 ? prm.n_c : 3 * prm.q, B);
   const int q = min(prm.q, n_c);
-  warp_constraint_set(rs, B, n_c, ws);
-  warp_elite_sort(rs, cs, B, n_c, ws);
+  small_elites(rs, cs, B, n_c, q, sh);
   const int d_p = prm.d_p;
   const double* ps = p + size_t(lay.off) * d_p;
-  auto id_of = [&](int e) { const int id = ws.cand[e]; return (id >= 0 && id < B) ? id : 0; };
-  // Eqs. (mean_update, cov_update, s_formula), lanes over elites
-  const double cmin = cs[id_of(0)] + rs[id_of(0)];
-  for (int e = lane; e < q; e += 32) {
-    const int id = id_of(e);
-    ws.sw[e] = exp(-(cs[id] + rs[id] - cmin) / prm.gamma);
-  }
-  __syncwarp();
-  double part = 0.0;
-  for (int e = lane; e < q; e += 32) part += ws.sw[e];
-  const double Ssum = warp_sum(part);
-  double mu_new[kMaxDp];
-  for (int a = 0; a < d_p; ++a) {
-    double v = 0.0;
-    for (int e = lane; e < q; e += 32) v += ws.sw[e] * ps[size_t(id_of(e)) * d_p + a];
-    mu_new[a] = (1.0 - prm.eta) * st.mu[a] + prm.eta * warp_sum(v) / Ssum;
-  }
-  double sg_new[kMaxDp * kMaxDp];
-  for (int a = 0; a < d_p; ++a) {
-    for (int b = 0; b < d_p; ++b) {
-      double v = 0.0;
-      for (int e = lane; e < q; e += 32) {
-        const double* pe = ps + size_t(id_of(e)) * d_p;
-        v += ws.sw[e] * (pe[a] - mu_new[a]) * (pe[b] - mu_new[b]);
-      }
-      sg_new[a * kMaxDp + b] = (1.0 - prm.eta) * st.sigma[a * kMaxDp + b] + prm.eta * warp_sum(v) / Ssum;
-    }
-  }
-  __syncwarp();
+  auto id_of = [&](int e) { const int id = sh.idx[e]; return (id >= 0 && id < B) ? id : 0; };
+  auto p_e = [&](int e, int a) { return ps[size_t(id_of(e)) * d_p + a]; };
+  auto c_e = [&](int e) { return cs[id_of(e)] + rs[id_of(e)]; };
+  // the order keys are no longer needed: their space stages the elite rows
+  update_moments(p_e, c_e, c_e(0), q, d_p, prm.gamma, prm.eta, st.mu, st.sigma, kMaxDp, sh.sw,
+                 sh.acc, reinterpret_cast<double*>(sh.key), int(sizeof(sh.key) / sizeof(double)));
   const int best = id_of(0);
-  if (lane == 0) {
-    for (int a = 0; a < d_p; ++a) {
-      st.mu[a] = mu_new[a];
-      for (int b = 0; b < d_p; ++b) st.sigma[a * kMaxDp + b] = sg_new[a * kMaxDp + b];
-    }
+  if (threadIdx.x == 0) {
     cholesky(st.sigma, prm.cov_eps, d_p, st.chol);
     st.best_index = best;
     st.best_r = rs[best];
@@ -521,19 +578,19 @@ select_update_warp_kernel(const Layout* layout, DevCem* cem, int S, int l, Param
     st.best_cost = cs[best] + rs[best];
     if (l == prm.L) { st.fresh = 0; st.step += 1ull; }
   }
-  for (int a = lane; a < d_p; a += 32) st.best_p[a] = ps[size_t(best) * d_p + a];
-  for (int a = lane; a < 2 * prm.n; a += 32) st.best_xi[a] = xi[size_t(lay.off + best) * 2 * prm.n + a];
+  for (int a = threadIdx.x; a < d_p; a += blockDim.x) st.best_p[a] = ps[size_t(best) * d_p + a];
+  for (int a = threadIdx.x; a < 2 * prm.n; a += blockDim.x)
+    st.best_xi[a] = xi[size_t(lay.off + best) * 2 * prm.n + a];
   if (elite_out != nullptr)
-    for (int e = lane; e < q; e += 32) elite_out[size_t(s) * prm.q + e] = ws.cand[e];
+    for (int e = threadIdx.x; e < q; e += blockDim.x) elite_out[size_t(s) * prm.q + e] = sh.idx[e];
 }
 
-__global__ void __launch_bounds__(32)
-select_only_warp_kernel(const double* r, const double* cu, int B, int n_c, int q, int* elite) {
+__global__ void __launch_bounds__(kSmallThreads)
+select_only_small_kernel(const double* r, const double* cu, int B, int n_c, int q, int* elite) {
   extern __shared__ __align__(16) unsigned char shraw[];
-  WarpSel& ws = *reinterpret_cast<WarpSel*>(shraw);
-  warp_constraint_set(r, B, n_c, ws);
-  warp_elite_sort(r, cu, B, n_c, ws);
-  for (int e = threadIdx.x; e < q; e += 32) elite[e] = ws.cand[e];
+  SmallSel& sh = *reinterpret_cast<SmallSel*>(shraw);
+  small_elites(r, cu, B, n_c, q, sh);
+  for (int e = threadIdx.x; e < q; e += blockDim.x) elite[e] = sh.idx[e];
 }
 
 // Per-slot states from / to a table of episode states: dst[s] = src[idx[s]]
@@ -577,10 +634,10 @@ static void sel_attr() {
                        int(sizeof(SelShared)));
   cudaFuncSetAttribute(update_only_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        int(sizeof(SelShared)));
-  cudaFuncSetAttribute(select_update_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       int(sizeof(WarpSel) * kWarpsPerCta));
-  cudaFuncSetAttribute(select_only_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       int(sizeof(WarpSel)));
+  cudaFuncSetAttribute(select_update_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       int(sizeof(SmallSel)));
+  cudaFuncSetAttribute(select_only_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       int(sizeof(SmallSel)));
   g_sel_attr = true;
 }
 
@@ -590,10 +647,9 @@ cudaError_t launch_select_update(const Layout* layout, DevCem* cem, int S, int l
                                  int max_B, cudaStream_t s) {
   if (S == 0) return cudaSuccess;
   sel_attr();
-  if (max_B <= kWarpMaxB && (prm.n_c > 0 ? prm.n_c : 3 * prm.q) <= kWarpMaxC) {
-    select_update_warp_kernel<<<(S + kWarpsPerCta - 1) / kWarpsPerCta, 32 * kWarpsPerCta,
-                                sizeof(WarpSel) * kWarpsPerCta, s>>>(layout, cem, S, l, prm, p, xi,
-                                                                     r, cu, elite_out);
+  if (max_B <= kSmallMaxB && (prm.n_c > 0 ? prm.n_c : 3 * prm.q) <= kSmallMaxC) {
+    select_update_small_kernel<<<S, kSmallThreads, sizeof(SmallSel), s>>>(layout, cem, l, prm, p,
+                                                                          xi, r, cu, elite_out);
     return cudaGetLastError();
   }
   select_update_kernel<<<S, kSelThreads, sizeof(SelShared), s>>>(layout, cem, l, prm, p, xi, r, cu,
@@ -604,8 +660,8 @@ cudaError_t launch_select_update(const Layout* layout, DevCem* cem, int S, int l
 cudaError_t launch_select_only(const double* r, const double* cu, int B, int n_c, int q,
                                int* elite, cudaStream_t s) {
   sel_attr();
-  if (B <= kWarpMaxB && n_c <= kWarpMaxC) {
-    select_only_warp_kernel<<<1, 32, sizeof(WarpSel), s>>>(r, cu, B, n_c, q, elite);
+  if (B <= kSmallMaxB && n_c <= kSmallMaxC) {
+    select_only_small_kernel<<<1, kSmallThreads, sizeof(SmallSel), s>>>(r, cu, B, n_c, q, elite);
     return cudaGetLastError();
   }
   select_only_kernel<<<1, kSelThreads, sizeof(SelShared), s>>>(r, cu, B, n_c, q, elite);

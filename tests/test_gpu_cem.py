@@ -15,10 +15,17 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("B,n_c,q,ties", [(1, 1, 1, False), (7, 5, 2, True), (1000, 150, 50, True),
                                           (1000, 150, 50, False), (5000, 2048, 700, True),
-                                          (40000, 150, 50, True), (64, 64, 64, True)])
+                                          (40000, 150, 50, True), (64, 64, 64, True),
+                                          (2048, 1024, 300, False), (2048, 1000, 1000, True),
+                                          (2049, 1024, 300, False), (100, 40, 10, "group")])
 def test_select_elites_bit_exact(B, n_c, q, ties):
     s = sg.Stream(B * 31 + n_c)
-    if ties:
+    if ties == "group":
+        # exactly n_c zeros: the prefix group of the n_c-th key is taken whole
+        r = np.concatenate([np.zeros(n_c), s.uniform(0.5, 3.0, B - n_c)])
+        r = r[np.argsort(s.uniform(0.0, 1.0, B))]
+        cu = s.uniform(100.0, 2000.0, B)
+    elif ties:
         r = s.integers(0, 6, B).astype(float) * 0.25      # many exact ties, many zeros
         cu = s.integers(0, 9, B).astype(float)
     else:
