@@ -137,6 +137,56 @@ class ClockSampler:
                     reasons=reasons, samples=len(rows))
 
 
+# ----------------------------------------------------------------------------- replicas
+
+class Ranks:
+    """One process per GPU (torchrun environment): rank, world size, barrier and
+    the max-over-ranks reduction of a timing.  Replicas run independent scenes,
+    so the only collectives are this barrier and this reduction."""
+
+    def __init__(self, backend="nccl", device="cuda"):
+        import torch
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.device = device
+        self.dist = None
+        if device == "cuda":
+            torch.cuda.set_device(self.local)
+        if self.world > 1:
+            import torch.distributed as dist
+            kw = {"device_id": torch.device("cuda", self.local)} if device == "cuda" else {}
+            dist.init_process_group(backend, **kw)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+        if self.device == "cuda":
+            import torch
+            torch.cuda.synchronize()
+
+    def max(self, x: float) -> float:
+        if self.dist is None:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64,
+                         device=self.device if self.device == "cpu" else f"cuda:{self.local}")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def replica_value(units_per_step: float, steps: int, slowest_s: float, world: int) -> float:
+    """Whole-job throughput: every replica processes units_per_step per step;
+    the job takes as long as its slowest rank."""
+    return world * units_per_step * steps / slowest_s
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def gpu_arm(args):
@@ -146,25 +196,15 @@ def gpu_arm(args):
     from paper_2212_02224_gb300 import scenegen as sg
     from paper_2212_02224_gb300.planner import Planner
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    ranks = Ranks("nccl", "cuda")
+    world, rank, local = ranks.world, ranks.rank, ranks.local
+    barrier = ranks.barrier
 
     prm, sc, B = sg.workload(1)
     K, L = prm.inner_iters, prm.outer_iters
     units = B * K * L
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
 
     # ---- value: resident inputs, graph-captured cycle
     pl = Planner(prm, prec="fp32", max_obs=16, max_samples=B)
@@ -185,12 +225,8 @@ def gpu_arm(args):
             ends[i].record(stream)
         barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_s = sum(step_ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([total_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * units * args.steps / total_s
+    total_s = ranks.max(sum(step_ms) / 1e3)
+    value = replica_value(units, args.steps, total_s, world)
     clocks = clk.summary()
 
     # ---- e2e: through host buffers (plan_step), wall clock per cycle
@@ -204,12 +240,8 @@ def gpu_arm(args):
         dt_ms = (time.perf_counter() - t0) * 1e3
         if i >= args.warmup:
             e2e_ms.append(dt_ms)
-    e2e_total = sum(e2e_ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([e2e_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * units * len(e2e_ms) / e2e_total
+    e2e_total = ranks.max(sum(e2e_ms) / 1e3)
+    e2e_value = replica_value(units, len(e2e_ms), e2e_total, world)
     dev_scene = 96 + 48 * sc.n_obs
     dev_cem = 1464
     h2d = dev_scene + dev_cem
@@ -283,7 +315,8 @@ def gpu_arm(args):
             "speedup_vs_plain_fp64": (value / plain["value"]) if plain else None,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "fused_kernel<11,4> (one lower-level solve, B=1000, K=100)",
+                         "kernel": f"fused_kernel (n=11, {shape[0]} warp(s)/sample, "
+                                   f"{shape[1]} sample(s)/CTA; one lower-level solve, B=1000, K=100)",
                          "kernel_ms": kern_ms,
                          "peak_basis": f"FP32 FMA pipe: {sms} SMs x 128 lanes x 2 flop x "
                                        f"{peak_clock:.0f} MHz"},
@@ -291,8 +324,7 @@ def gpu_arm(args):
             "clocks": clocks,
         }
         print(json.dumps(line))
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
 
 
 # ----------------------------------------------------------------------------- reference arm
