@@ -58,10 +58,20 @@ typedef enum {
 /* Arithmetic of the lower-level solve.  FP64: one kernel per step of Alg. 2
  * with intermediates in HBM, float64 throughout (the reference GPU path).
  * FP32: the fused multi-iteration kernel, float32 projections and
- * contractions with constants formed and inverted in float64. */
+ * contractions with constants formed and inverted in float64.
+ * TF32, BF16, TF32X3: the fused iteration with the two n-wide contractions of
+ * Alg. 2 (the forward evaluation W xi of Eq. param and the transposed
+ * contraction F^T h, G^T (e - s) of the xi-step, Eq. split_xy) on the tensor
+ * cores with float32 accumulation; the projections stay float32.  TF32 and
+ * BF16 round the operands once (about 2^-11 and 2^-8 relative); TF32X3
+ * splits every operand into a TF32 head and tail and sums three products,
+ * which is float32-level accuracy.  These modes need m <= 128. */
 typedef enum {
     PLAN_PREC_FP64 = 0,
-    PLAN_PREC_FP32 = 1
+    PLAN_PREC_FP32 = 1,
+    PLAN_PREC_TF32 = 2,
+    PLAN_PREC_BF16 = 3,
+    PLAN_PREC_TF32X3 = 4
 } plan_prec;
 
 /* Planner configuration (plan_init).  Symbols follow the paper.

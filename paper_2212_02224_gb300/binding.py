@@ -23,6 +23,11 @@ PLAN_ENONFINITE = -7
 
 PLAN_PREC_FP64 = 0
 PLAN_PREC_FP32 = 1
+PLAN_PREC_TF32 = 2
+PLAN_PREC_BF16 = 3
+PLAN_PREC_TF32X3 = 4
+PRECISIONS = {"fp64": PLAN_PREC_FP64, "fp32": PLAN_PREC_FP32, "tf32": PLAN_PREC_TF32,
+              "bf16": PLAN_PREC_BF16, "tf32x3": PLAN_PREC_TF32X3}
 
 
 class PlanConfig(ctypes.Structure):

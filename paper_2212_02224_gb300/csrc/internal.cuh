@@ -94,6 +94,16 @@ cudaError_t launch_fused_f32(const DevScene* scenes, const Layout* layout, const
                              const Consts& c, const Params& prm, double* xi, double* r,
                              double* cu, cudaStream_t s);
 
+// Tensor-core modes (PLAN_PREC_TF32, _BF16, _TF32X3): tiles of
+// tc_samples_per_cta() samples; err is set to 1 if a wait timed out.
+bool tc_supported(int n, int m, int max_obs);
+void tc_setup();
+int tc_samples_per_cta();
+cudaError_t launch_tc(int prec, const DevScene* scenes, const Layout* layout, const double* obs,
+                      const Tile* tiles, int n_tiles, const double* p, const Consts& c,
+                      const Params& prm, double* xi, double* r, double* cu, int* err,
+                      cudaStream_t s);
+
 struct Plain64Work {   // HBM intermediates of the FP64 path
   double* xibarp;  // [B][32] M xi_bar + C b
   double* xi;      // [B][32]

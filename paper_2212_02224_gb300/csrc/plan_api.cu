@@ -61,6 +61,7 @@ struct plan_ctx {
   double* r = nullptr;
   double* cu = nullptr;
   int* elite = nullptr;    // [max_scenes][q]
+  int* tc_err = nullptr;   // timeout flag of the tensor-core kernel
   Plain64Work pw{};
   DevCem* cem_tmp = nullptr;   // single-stage sampling
   Layout* layout_tmp = nullptr;
@@ -149,9 +150,11 @@ int validate_config(const plan_config* cfg, std::string* why) {
   if (cfg->n_elite_c > kMaxEliteC || (cfg->n_elite_c <= 0 && 3 * cfg->n_elite > kMaxEliteC))
     return bad("n_elite_c must be <= 2048");
   if (cfg->n_elite_c > 0 && cfg->n_elite > cfg->n_elite_c) return bad("n_elite must be <= n_elite_c");
-  if (cfg->prec != PLAN_PREC_FP64 && cfg->prec != PLAN_PREC_FP32) return bad("unknown prec");
+  if (cfg->prec < PLAN_PREC_FP64 || cfg->prec > PLAN_PREC_TF32X3) return bad("unknown prec");
   if (cfg->prec == PLAN_PREC_FP32 && !fused_supported(cfg->n_coef, cfg->m))
     return bad("the FP32 fused kernel supports n_coef in {8, 11, 16}");
+  if (cfg->prec >= PLAN_PREC_TF32 && !tc_supported(cfg->n_coef, cfg->m, cfg->max_obs))
+    return bad("the tensor-core modes support n_coef in {8, 11, 16} and m <= 128");
   if (cfg->max_obs < 0 || cfg->max_obs > kMaxObs) return bad("max_obs must be in [0, 64]");
   if (cfg->max_samples < 1 || cfg->max_samples > (1 << 24)) return bad("max_samples must be in [1, 2^24]");
   if (cfg->max_scenes < 1 || cfg->max_scenes > 65535) return bad("max_scenes must be in [1, 65535]");
@@ -255,6 +258,7 @@ struct Shape {
 // Fused-kernel shape: explicit tuning if set, else a heuristic that keeps
 // about 16 warps per SM busy for small batches.
 Shape pick_shape(const plan_ctx* ctx, int total_B) {
+  if (ctx->cfg.prec >= PLAN_PREC_TF32) return Shape{1, tc_samples_per_cta()};
   if (ctx->tune_wps > 0 && ctx->tune_spc > 0) return Shape{ctx->tune_wps, ctx->tune_spc};
   const bool long_horizon = ctx->cfg.m > 128;
   if (total_B <= 1024 || long_horizon) return Shape{2, 1};
@@ -315,6 +319,9 @@ cudaError_t run_solve(plan_ctx* ctx, const SceneSet& set, const SceneSet& lay, i
     return launch_fused_f32(set.scenes, lay.layout, set.obs, lay.tiles, n_tiles, sh.wps, sh.spc,
                             p, ctx->c, ctx->prm, xi, r, cu, s);
   }
+  if (ctx->cfg.prec >= PLAN_PREC_TF32)
+    return launch_tc(ctx->cfg.prec, set.scenes, lay.layout, set.obs, lay.tiles, n_tiles, p, ctx->c,
+                     ctx->prm, xi, r, cu, ctx->tc_err, s);
   return launch_plain64(set.scenes, lay.layout, lay.sample_scene, set.obs, total_B, p, ctx->c,
                         ctx->prm, ctx->pw, xi, r, cu, s);
 }
@@ -520,6 +527,7 @@ int plan_init(const plan_config* cfg, plan_ctx** out) {
   A(dalloc(ctx, &ctx->cu, B));
   A(dalloc(ctx, &ctx->elite, size_t(c.max_scenes) * c.n_elite));
   A(dalloc(ctx, &ctx->rows, size_t(2) * c.max_scenes));
+  A(dalloc(ctx, &ctx->tc_err, 1));
   if (c.prec == PLAN_PREC_FP64) {
     A(dalloc(ctx, &ctx->pw.xibarp, B * 32));
     A(dalloc(ctx, &ctx->pw.xi, B * 32));
@@ -532,8 +540,10 @@ int plan_init(const plan_config* cfg, plan_ctx** out) {
   if (st != PLAN_OK) return bail(st);
   cem_setup();
   fused_setup();
+  if (c.prec >= PLAN_PREC_TF32) tc_setup();
   if (build_constants(k, p, ctx->internal) != cudaSuccess ||
       cudaMemsetAsync(ctx->cem, 0, sizeof(DevCem) * c.max_scenes, ctx->internal) != cudaSuccess ||
+      cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), ctx->internal) != cudaSuccess ||
       cudaStreamSynchronize(ctx->internal) != cudaSuccess) {
     cudaGetLastError();
     return bail(PLAN_ECUDA);
@@ -601,12 +611,17 @@ int plan_get_state(plan_ctx* ctx, int slot, plan_cem_state* st, void* stream) {
   if (!ctx) return PLAN_EINVAL;
   if (!st || slot < 0 || slot >= ctx->cfg.max_scenes) return fail(ctx, PLAN_EINVAL, "bad slot/state");
   CU(ctx, cudaSetDevice(ctx->device));
-  TRY(stage_acquire(ctx, sizeof(DevCem)));
+  TRY(stage_acquire(ctx, sizeof(DevCem) + sizeof(int)));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CU(ctx, cudaMemcpyAsync(ctx->stage, ctx->cem + slot, sizeof(DevCem), cudaMemcpyDeviceToHost, s));
+  CU(ctx, cudaMemcpyAsync(ctx->stage + sizeof(DevCem), ctx->tc_err, sizeof(int),
+                          cudaMemcpyDeviceToHost, s));
   CU(ctx, cudaStreamSynchronize(s));
   DevCem c;
   std::memcpy(&c, ctx->stage, sizeof c);
+  int tc_timeout = 0;
+  std::memcpy(&tc_timeout, ctx->stage + sizeof c, sizeof tc_timeout);
+  if (tc_timeout) return fail(ctx, PLAN_ETIMEOUT, "a tensor-core wait of the solve timed out");
   const int d = 2 * ctx->cfg.n_seg;
   std::memset(st, 0, sizeof *st);
   for (int a = 0; a < d; ++a) {
@@ -623,12 +638,17 @@ int plan_get_result(plan_ctx* ctx, int slot, plan_result* out, void* stream) {
   if (!ctx) return PLAN_EINVAL;
   if (!out || slot < 0 || slot >= ctx->cfg.max_scenes) return fail(ctx, PLAN_EINVAL, "bad slot/out");
   CU(ctx, cudaSetDevice(ctx->device));
-  TRY(stage_acquire(ctx, sizeof(DevCem)));
+  TRY(stage_acquire(ctx, sizeof(DevCem) + sizeof(int)));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CU(ctx, cudaMemcpyAsync(ctx->stage, ctx->cem + slot, sizeof(DevCem), cudaMemcpyDeviceToHost, s));
+  CU(ctx, cudaMemcpyAsync(ctx->stage + sizeof(DevCem), ctx->tc_err, sizeof(int),
+                          cudaMemcpyDeviceToHost, s));
   CU(ctx, cudaStreamSynchronize(s));
   DevCem c;
   std::memcpy(&c, ctx->stage, sizeof c);
+  int tc_timeout = 0;
+  std::memcpy(&tc_timeout, ctx->stage + sizeof c, sizeof tc_timeout);
+  if (tc_timeout) return fail(ctx, PLAN_ETIMEOUT, "a tensor-core wait of the solve timed out");
   std::memset(out, 0, sizeof *out);
   for (int a = 0; a < 2 * ctx->cfg.n_seg; ++a) out->p[a] = c.best_p[a];
   for (int a = 0; a < 2 * ctx->cfg.n_coef; ++a) out->xi[a] = c.best_xi[a];

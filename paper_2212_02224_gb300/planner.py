@@ -30,7 +30,8 @@ class Planner:
     """One planner context on the current CUDA device.
 
     params: object with the planner parameters (see scenegen.Params);
-    prec: "fp32" (fused kernel) or "fp64" (plain reference path).
+    prec: "fp32" (fused kernel), "fp64" (plain reference path), or a
+          tensor-core mode "tf32", "bf16", "tf32x3" (contractions on tcgen05).
     """
 
     def __init__(self, params, prec: str = "fp32", max_obs: int = 32, max_samples: int = 4096,
@@ -38,7 +39,7 @@ class Planner:
         if not torch.cuda.is_available():
             raise RuntimeError("the planner runs on a CUDA GPU; none is available")
         self.prm = params
-        self.prec = {"fp32": B.PLAN_PREC_FP32, "fp64": B.PLAN_PREC_FP64}[prec]
+        self.prec = B.PRECISIONS[prec]
         self.cfg = B.make_config(params, self.prec, max_obs, max_samples, max_scenes)
         self.ctx = B.plan_init(self.cfg)
         self.n = params.n_coef
@@ -147,7 +148,7 @@ class Server:
     def __init__(self, params, prec: str = "fp32", max_obs: int = 32, max_samples: int = 8192,
                  max_scenes: int = 32, max_executors: int = 4, device_budget: int = 4 << 30,
                  max_episodes: int = 1024):
-        p = {"fp32": B.PLAN_PREC_FP32, "fp64": B.PLAN_PREC_FP64}[prec]
+        p = B.PRECISIONS[prec]
         self.cfg = B.make_config(params, p, max_obs, max_samples, max_scenes)
         self.srv = B.plan_server_create(self.cfg, max_executors, device_budget, max_episodes)
         self.n, self.d_p = params.n_coef, 2 * params.n_seg

@@ -76,3 +76,22 @@ def test_null_context_is_rejected():
     lib = _lib()
     assert lib.plan_solve(None, None, None, 0, None, None, None, None) == binding.PLAN_EINVAL
     assert lib.plan_destroy(None) == binding.PLAN_OK
+
+
+@pytest.mark.parametrize("prec", [binding.PLAN_PREC_TF32, binding.PLAN_PREC_BF16,
+                                  binding.PLAN_PREC_TF32X3])
+def test_tensor_core_modes_need_short_horizons(prec):
+    lib = _lib()
+    prm = scenegen.Params(m=200)
+    cfg = binding.make_config(prm, prec, 8, 64)
+    ctx = ctypes.c_void_p()
+    assert lib.plan_init(ctypes.byref(cfg), ctypes.byref(ctx)) == binding.PLAN_EINVAL
+    assert "m <= 128" in binding.last_error(None)
+
+
+def test_unknown_precision_is_rejected():
+    lib = _lib()
+    cfg = binding.make_config(scenegen.Params(), 5, 8, 64)
+    ctx = ctypes.c_void_p()
+    assert lib.plan_init(ctypes.byref(cfg), ctypes.byref(ctx)) == binding.PLAN_EINVAL
+    assert "prec" in binding.last_error(None)
