@@ -189,6 +189,58 @@ def replica_value(units_per_step: float, steps: int, slowest_s: float, world: in
 
 # ----------------------------------------------------------------------------- GPU arm
 
+def precision_modes(prm, sc, p, flush, stream, reps=10):
+    """Solve time of each arithmetic mode on the same samples (CUDA events, L2
+    flushed) and the error of its results against the plain FP64 GPU path:
+    largest trajectory-position difference (m), residual difference and
+    relative cost difference over all samples."""
+    import numpy as np
+    import torch
+
+    from paper_2212_02224_gb300.planner import Planner
+
+    B = p.shape[0]
+    n, m = prm.n_coef, prm.m
+    # Bernstein rows W[t][k] of the positions, in float64 on the host
+    from math import comb
+    tau = np.arange(m) / (m - 1)
+    W = np.stack([comb(n - 1, k) * tau ** k * (1 - tau) ** (n - 1 - k) for k in range(n)], axis=1)
+
+    def solve(prec):
+        pl = Planner(prm, prec=prec, max_obs=16, max_samples=B)
+        for _ in range(3):
+            pl.solve(sc, p, want_xi=False)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            pl.solve(sc, p, want_xi=False)
+            b.record(stream)
+        xi, r, cu = pl.solve(sc, p)
+        torch.cuda.synchronize()
+        ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+        out = xi.cpu().numpy(), r.cpu().numpy(), cu.cpu().numpy()
+        pl.close()
+        return ms, out
+
+    ms64, ref = solve("fp64")
+    res = {"reference": "plain FP64 GPU path (itself within 1e-6 of the FP64 oracle)",
+           "fp64": {"solve_ms": ms64}}
+    for prec in ("fp32", "tf32x3", "tf32", "bf16"):
+        ms, (xi, r, cu) = solve(prec)
+        pos = max(np.abs((xi[:, :n] - ref[0][:, :n]) @ W.T).max(),
+                  np.abs((xi[:, n:] - ref[0][:, n:]) @ W.T).max())
+        res[prec] = {"solve_ms": ms, "max_pos_err_m": float(pos),
+                     "max_resid_err": float(np.abs(r - ref[1]).max()),
+                     "max_cost_rel_err": float((np.abs(cu - ref[2]) /
+                                                np.maximum(1e-12, np.abs(ref[2]))).max()),
+                     "contractions": "CUDA-core FP32 FMA" if prec == "fp32" else
+                                     f"tcgen05 kind::{'f16 (bf16)' if prec == 'bf16' else 'tf32'}"
+                                     f"{' x3 split' if prec == 'tf32x3' else ''}, FP32 accumulate"}
+    return res
+
+
 def gpu_arm(args):
     import numpy as np
     import torch
@@ -268,6 +320,10 @@ def gpu_arm(args):
     achieved = flops / (kern_ms * 1e-3) / 1e12
     pl.close()
 
+    # ---- precision modes: one lower-level solve of the same B = 1000 samples per
+    # mode, timed alone, and its error against the plain FP64 GPU path
+    precision = precision_modes(prm, sc, p, flush, stream) if not args.skip_fp64 else None
+
     # ---- plain FP64 path, same cycle
     plain = None
     if not args.skip_fp64:
@@ -322,6 +378,7 @@ def gpu_arm(args):
                                        f"{peak_clock:.0f} MHz"},
             "cpu_baseline": cpu,
             "clocks": clocks,
+            "precision": precision,
         }
         print(json.dumps(line))
     ranks.close()

@@ -4,8 +4,9 @@ C ABI against the FP64 oracle.
 TF32X3 splits every operand into a TF32 head and tail and is held to the
 FP32 bar (positions within 1e-3 m, residual within 1e-3, cost within 1e-4
 relative).  TF32 and BF16 round every operand once; their bars are the
-stated per-result tolerances of those modes (about three times the largest
-error measured on the dense-traffic scene)."""
+stated per-result tolerances of those modes, about three times the largest
+error measured over all B = 1000 samples of the dense-traffic scene (TF32:
+0.045 m, 0.028, 1.2e-3; BF16: 0.093 m, 0.16, 3.7e-3)."""
 import numpy as np
 import pytest
 import torch
@@ -20,8 +21,8 @@ pytestmark = pytest.mark.gpu
 
 # (positions m, residual, relative cost) per mode
 BARS = {"tf32x3": (FP32_POS_M, FP32_RESID, FP32_COST_REL),
-        "tf32": (5e-2, 5e-2, 1e-3),
-        "bf16": (2.5e-1, 5e-1, 1e-2)}
+        "tf32": (1.5e-1, 1e-1, 4e-3),
+        "bf16": (3e-1, 5e-1, 1.2e-2)}
 MODES = list(BARS)
 
 
