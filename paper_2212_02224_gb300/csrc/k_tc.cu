@@ -194,7 +194,7 @@ tc_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ layout
   __shared__ uint32_t tslot;
   __shared__ float sXb[16][17];           // xi_bar[c][k]
   __shared__ float sG[16][17];            // g[c][k] of the transpose
-  __shared__ float sM[2][kMaxCoef][kMaxCoef];
+  __shared__ float sM[2][kMaxCoef][kMaxCoef + 1];     // rows padded: conflict-free row reads
   __shared__ float sMoved[kTcSamples];
   __shared__ float sScore[8][4][2];
   __shared__ float sIab[2];
