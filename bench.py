@@ -38,6 +38,10 @@ METRIC = "plan solves/sec (samples x inner iters x outer iters)"
 UNIT = "sample-iters/s"
 FP32_LANES_PER_SM = 128
 SM_COUNT_NOMINAL = 152
+# DRAM bytes (read + write) of one fused solve of this workload, by kernel shape
+# (warps per sample, samples per CTA), from the ncu capture summarised in
+# profiles/fused_kernel_dense_traffic_B1000.md; must be re-taken when the kernel changes.
+FUSED_TRAFFIC_BYTES = {(2, 1): 89600}
 
 
 def algorithmic_flops_per_sample_iter(m, n, N, n_eq=3):
@@ -370,7 +374,8 @@ def gpu_arm(args):
             "plain_fp64": plain,
             "speedup_vs_plain_fp64": (value / plain["value"]) if plain else None,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": FUSED_TRAFFIC_BYTES.get(tuple(shape)),
                          "kernel": f"fused_kernel (n=11, {shape[0]} warp(s)/sample, "
                                    f"{shape[1]} sample(s)/CTA; one lower-level solve, B=1000, K=100)",
                          "kernel_ms": kern_ms,
