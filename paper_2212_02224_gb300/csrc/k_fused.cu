@@ -67,6 +67,35 @@ __device__ __forceinline__ void kin(const float* __restrict__ row,
   }
 }
 
+// Sum over the warp of the 2 n partial sums of the transposed contraction:
+// on return lane (axis * 16 + k) holds the total of coefficient k of `axis`
+// (recursive halving: at offset o a lane keeps the half of the slots selected
+// by bit o of its index and adds its partner's copy of that half).
+template <int NC, int NP>
+__device__ __forceinline__ float warp_reduce_slots(const float2 (&wx)[NP], const float2 (&wy)[NP],
+                                                   int lane) {
+  float v[16];
+  const bool hi = (lane & 16) != 0;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    if (i < NC) {
+      const float xv = (i & 1) ? wx[i / 2].y : wx[i / 2].x;
+      const float yv = (i & 1) ? wy[i / 2].y : wy[i / 2].x;
+      v[i] = (hi ? yv : xv) + __shfl_xor_sync(kFull, hi ? xv : yv, 16);
+    } else {
+      v[i] = 0.f;
+    }
+  }
+#pragma unroll
+  for (int o = 8; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i)
+      v[i] = (up ? v[i + o] : v[i]) + __shfl_xor_sync(kFull, up ? v[i] : v[i + o], o);
+  }
+  return v[0];
+}
+
 // Barrier of the warps that share one sample.  With more than one warp per
 // sample a CTA holds exactly one sample group, so a fixed barrier id is used
 // (a run-time id would make the compiler reserve all 16 barriers per CTA).
@@ -82,7 +111,8 @@ template <int SLOTS, int WPS>
 struct RegCap {
   // registers per thread: one timestep slot per 32 lanes needs about 70, the
   // rest is per-sample state; capped so that enough warps stay resident
-  static constexpr int value = SLOTS * WPS >= 8 ? 255 : (SLOTS >= 4 ? 224 : (SLOTS == 2 ? 144 : 96));
+  static constexpr int value =
+      SLOTS * WPS >= 8 ? 255 : (SLOTS >= 4 ? 224 : (SLOTS == 2 ? 144 : (WPS == 4 ? 72 : 96)));
 };
 
 template <int NC, int SLOTS, int WPS>
@@ -110,7 +140,10 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   float4* sObs = reinterpret_cast<float4*>(smem + m * ST);   // [N][4]
   float* sBuf = reinterpret_cast<float*>(sObs + 4 * N);      // [warps][64]
   constexpr int RS = 32 * WPS + 4;                           // row stride of the reduction table
-  constexpr int RED = (WPS > 1 ? 2 : 1) * 2 * NC * RS;       // floats per sample group
+  // floats per sample group: one warp transposes through a [2n][RS] table; with
+  // several warps each warp reduces with shuffles and the warps add their
+  // [32] results through a double-buffered [2][WPS][32] table
+  constexpr int RED = WPS > 1 ? 2 * WPS * 32 : 2 * NC * RS;
   float* sRedAll = sBuf + 64 * warps;                        // [groups][RED]
   float* sScore = sRedAll + groups * RED;                    // [groups][WPS][2]
   float* sM = sScore + groups * WPS * 2;                     // [2][NC][NC] rows of M
@@ -417,14 +450,22 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     // ---- D: reduce over the sample's lanes through a shared-memory transpose,
     // multipliers, xi-step in increment form
     float wl;
-    {
-      float* rt = sRed + (WPS > 1 ? (it & 1) * 2 * NC * RS : 0);
+    if constexpr (WPS > 1) {
+      const float part = warp_reduce_slots<NC, NP>(wx, wy, lane);
+      float* rt = sRed + (it & 1) * WPS * 32;
+      rt[wig * 32 + lane] = part;
+      group_barrier(LPS);
+      wl = 0.f;
+#pragma unroll
+      for (int w = 0; w < WPS; ++w) wl += rt[w * 32 + lane];
+    } else {
+      float* rt = sRed;
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
         rt[k * RS + gl] = (k & 1) ? wx[k / 2].y : wx[k / 2].x;
         rt[(NC + k) * RS + gl] = (k & 1) ? wy[k / 2].y : wy[k / 2].x;
       }
-      if constexpr (WPS > 1) group_barrier(LPS); else __syncwarp();
+      __syncwarp();
       wl = 0.f;
       if (valid) {
         const float4* rrow = reinterpret_cast<const float4*>(rt + (axis * NC + kk) * RS);
@@ -490,7 +531,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
 template <int NC, int SLOTS, int WPS>
 size_t smem_bytes(const Params& prm, int spc) {
   const int warps = spc * WPS;
-  const int red = (WPS > 1 ? 2 : 1) * 2 * NC * (32 * WPS + 4);
+  const int red = WPS > 1 ? 2 * WPS * 32 : 2 * NC * (32 * WPS + 4);
   size_t f = size_t(prm.m) * basis32_stride(NC) + 16 * prm.max_obs + 64 * warps + spc * red +
              spc * WPS * 2 + 2 * NC * NC + size_t(6) * SLOTS * 32 * warps + size_t(warps) * prm.max_obs;
   return f * sizeof(float);
