@@ -112,6 +112,55 @@ def step1(p, scene, prm, basis):
     return np.concatenate([cx, cy], axis=1)
 
 
+def step1_layer(p, b0, prm, basis):
+    """The Step-1 QP as a layer of the learned sampler (Sec. IV, choice of the
+    differentiable optimizer: the convex cost of Alg. 1 line 7 and the equality
+    constraints, inequalities ignored), with a separate initial state per row:
+    p (B, d_p), b0 (B, 6) = (x, y, vx, vy, ax, ay) -> xi (B, 2n)."""
+    p = np.atleast_2d(np.asarray(p, dtype=np.float64))
+    b0 = np.atleast_2d(np.asarray(b0, dtype=np.float64))
+    m = basis[0].shape[0]
+    yd, vd = setpoint_vectors(p, m, prm.n_seg)
+    (Qx, Lx), (Qy, Ly) = step1_cost_matrices(basis, prm)
+    A = initial_rows(basis)
+    qx = -2.0 * prm.kp_lon * (vd @ Lx)
+    qy = -2.0 * prm.kp_lat * (yd @ Ly)
+    cx = np.stack([kkt_solve(Qx, A, -qx[j:j + 1], b0[j, [0, 2, 4]])[0] for j in range(len(p))])
+    cy = np.stack([kkt_solve(Qy, A, -qy[j:j + 1], b0[j, [1, 3, 5]])[0] for j in range(len(p))])
+    return np.concatenate([cx, cy], axis=1)
+
+
+def step1_layer_vjp(g, prm, basis):
+    """Vector-Jacobian product of step1_layer: g = dL/dxi (B, 2n) ->
+    (dL/dp (B, d_p), dL/db0 (B, 6)).  Implicit differentiation of the KKT
+    system K [z; mu] = [-q; b] (K symmetric): [u; w] = K^-1 [g_z; 0] gives
+    dL/d(-q) = u and dL/db = w; -q = 2 k L^T s(p) with s the set-point vector,
+    so dL/ds = 2 k L u and each entry of p collects dL/ds over its segment."""
+    g = np.atleast_2d(np.asarray(g, dtype=np.float64))
+    n = basis[0].shape[1]
+    m = basis[0].shape[0]
+    (Qx, Lx), (Qy, Ly) = step1_cost_matrices(basis, prm)
+    A = initial_rows(basis)
+    ne = A.shape[0]
+    seg_of_t = np.repeat(np.arange(prm.n_seg), segment_lengths(m, prm.n_seg))
+    B = len(g)
+    grad_p = np.zeros((B, 2 * prm.n_seg))
+    grad_b = np.zeros((B, 6))
+    for axis, (Q, L, k, off) in enumerate([(Qx, Lx, prm.kp_lon, prm.n_seg), (Qy, Ly, prm.kp_lat, 0)]):
+        K = np.zeros((n + ne, n + ne))
+        K[:n, :n] = Q
+        K[:n, n:] = A.T
+        K[n:, :n] = A
+        rhs = np.concatenate([g[:, axis * n:(axis + 1) * n].T, np.zeros((ne, B))], axis=0)
+        uw = np.linalg.solve(K, rhs)            # K is symmetric: K^-T = K^-1
+        u, w = uw[:n].T, uw[n:].T               # (B, n), (B, 3)
+        ds = 2.0 * k * (u @ L.T)                # (B, m)
+        for j in range(prm.n_seg):
+            grad_p[:, off + j] = ds[:, seg_of_t == j].sum(axis=1)
+        grad_b[:, [axis, axis + 2, axis + 4]] = w
+    return grad_p, grad_b
+
+
 # ----------------------------------------------------------------------------
 # Alg. 2: batch projection
 # ----------------------------------------------------------------------------
