@@ -334,6 +334,29 @@ int plan_sample(plan_ctx* ctx, const plan_scene* scene, const double* mu,
                 const double* sigma, int fresh, int l, uint64_t seed,
                 uint64_t episode_step, int B, double* p, void* stream);
 
+/* ------------------------------------------------ differentiable Step-1 layer */
+
+/* The Step-1 QP of Alg. 1 line 7 as a differentiable layer: the optimization
+ * layer of the learned sampler (Sec. IV, "choice of differentiable
+ * optimizer"), which keeps the convex cost of Eq. (lower_cost) and the
+ * equality constraints and ignores the inequalities.  Each row has its own
+ * initial state, as the training trajectories of a sampler do.
+ *   p   device, B x d_p   behavioural inputs (Eq. behaviour_param)
+ *   b0  device, B x 6     initial state (x, y, vx, vy, ax, ay) per row
+ *   xi  device, B x 2 n   output: [c_x | c_y], float64
+ * The solution is affine in (p, b0) through the float64 KKT inverse formed at
+ * plan_init.  Asynchronous on `stream`.  Errors: EINVAL (NULL buffer, B < 0),
+ * ECAPACITY (B > max_samples). */
+int plan_qp_forward(plan_ctx* ctx, const double* p, const double* b0, int B, double* xi,
+                    void* stream);
+
+/* Vector-Jacobian product of plan_qp_forward: given g = dL/dxi (device,
+ * B x 2 n) writes dL/dp (device, B x d_p) and, when grad_b0 is not NULL,
+ * dL/db0 (device, B x 6).  The layer is affine, so the product does not
+ * depend on the forward inputs.  Errors as plan_qp_forward. */
+int plan_qp_backward(plan_ctx* ctx, const double* g, int B, double* grad_p, double* grad_b0,
+                     void* stream);
+
 /* ------------------------------------------------ allocation-free lower level */
 
 /* The float64 lower-level solve of plan_solve (same kernels, same results) for

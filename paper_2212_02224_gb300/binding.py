@@ -81,7 +81,8 @@ EXPORTS = ("plan_init", "plan_destroy", "plan_status_str", "plan_last_error", "p
            "plan_step_resident", "plan_get_result", "plan_step", "plan_select_elites",
            "plan_update_distribution", "plan_sample", "plan_set_tuning", "plan_autotune",
            "plan_solve_fp64_noalloc", "plan_advance", "plan_server_create", "plan_server_destroy",
-           "plan_submit", "plan_poll", "plan_end_episode", "plan_server_info")
+           "plan_submit", "plan_poll", "plan_end_episode", "plan_server_info",
+           "plan_qp_forward", "plan_qp_backward")
 
 _lib = None
 
@@ -130,6 +131,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "plan_poll": (I, [V, U64, P(PlanResult), P(D), I]),
         "plan_end_episode": (I, [V, U64]),
         "plan_server_info": (I, [V, P(PlanServerStats)]),
+        "plan_qp_forward": (I, [V, V, V, I, V, V]),
+        "plan_qp_backward": (I, [V, V, I, V, V, V]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -288,6 +291,14 @@ def plan_sample(ctx, scene, mu, sigma, fresh: int, l: int, seed: int, step: int,
         *([float(sigma[a][b]) for a in range(d) for b in range(d)] if sigma is not None else [0.0]))
     check(load().plan_sample(ctx, arr, mu_c, sg_c, int(fresh), int(l), int(seed), int(step), int(B),
                              p_ptr, stream), ctx)
+
+
+def plan_qp_forward(ctx, p_ptr: int, b0_ptr: int, B: int, xi_ptr: int, stream: int = 0):
+    check(load().plan_qp_forward(ctx, p_ptr, b0_ptr, int(B), xi_ptr, stream), ctx)
+
+
+def plan_qp_backward(ctx, g_ptr: int, B: int, grad_p_ptr: int, grad_b0_ptr, stream: int = 0):
+    check(load().plan_qp_backward(ctx, g_ptr, int(B), grad_p_ptr, grad_b0_ptr, stream), ctx)
 
 
 def plan_set_tuning(ctx, warps_per_sample: int, samples_per_cta: int):

@@ -104,6 +104,12 @@ cudaError_t launch_tc(int prec, const DevScene* scenes, const Layout* layout, co
                       const Params& prm, double* xi, double* r, double* cu, int* err,
                       cudaStream_t s);
 
+// Differentiable Step-1 layer (k_qp.cu).
+cudaError_t launch_qp_forward(const Consts& c, const double* p, const double* b0, int B,
+                              double* xi, cudaStream_t s);
+cudaError_t launch_qp_backward(const Consts& c, const double* g, int B, double* grad_p,
+                               double* grad_b0, cudaStream_t s);
+
 struct Plain64Work {   // HBM intermediates of the FP64 path
   double* xibarp;  // [B][32] M xi_bar + C b
   double* xi;      // [B][32]

@@ -759,6 +759,30 @@ int plan_update_distribution(plan_ctx* ctx, const double* p_elite, const double*
   return PLAN_OK;
 }
 
+int plan_qp_forward(plan_ctx* ctx, const double* p, const double* b0, int B, double* xi,
+                    void* stream) {
+  if (!ctx) return PLAN_EINVAL;
+  if (B < 0) return fail(ctx, PLAN_EINVAL, "B must be >= 0");
+  if (B > ctx->cfg.max_samples) return fail(ctx, PLAN_ECAPACITY, "B exceeds max_samples");
+  if (B == 0) return PLAN_OK;
+  if (!p || !b0 || !xi) return fail(ctx, PLAN_EINVAL, "NULL buffer");
+  CU(ctx, cudaSetDevice(ctx->device));
+  CU(ctx, launch_qp_forward(ctx->c, p, b0, B, xi, static_cast<cudaStream_t>(stream)));
+  return PLAN_OK;
+}
+
+int plan_qp_backward(plan_ctx* ctx, const double* g, int B, double* grad_p, double* grad_b0,
+                     void* stream) {
+  if (!ctx) return PLAN_EINVAL;
+  if (B < 0) return fail(ctx, PLAN_EINVAL, "B must be >= 0");
+  if (B > ctx->cfg.max_samples) return fail(ctx, PLAN_ECAPACITY, "B exceeds max_samples");
+  if (B == 0) return PLAN_OK;
+  if (!g || !grad_p) return fail(ctx, PLAN_EINVAL, "NULL buffer");
+  CU(ctx, cudaSetDevice(ctx->device));
+  CU(ctx, launch_qp_backward(ctx->c, g, B, grad_p, grad_b0, static_cast<cudaStream_t>(stream)));
+  return PLAN_OK;
+}
+
 int plan_sample(plan_ctx* ctx, const plan_scene* scene, const double* mu, const double* sigma,
                 int fresh, int l, uint64_t seed, uint64_t episode_step, int B, double* p,
                 void* stream) {

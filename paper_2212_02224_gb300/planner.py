@@ -131,12 +131,49 @@ class Planner:
         B.plan_update_distribution(self.ctx, _ptr(p_elite), _ptr(cost), q, _ptr(mu), _ptr(sigma),
                                    _stream(stream))
 
+    # -------------------------------------------------------------- Step-1 layer
+    def qp_forward(self, p: torch.Tensor, b0: torch.Tensor, stream=None):
+        """xi (B, 2n) of the Step-1 QP for each row of p (B, d_p) and b0 (B, 6)."""
+        Bn = p.shape[0]
+        _need(p, (Bn, self.d_p), "p")
+        _need(b0, (Bn, 6), "b0")
+        xi = torch.empty((Bn, 2 * self.n), dtype=torch.float64, device=p.device)
+        B.plan_qp_forward(self.ctx, _ptr(p), _ptr(b0), Bn, _ptr(xi), _stream(stream))
+        return xi
+
+    def qp_backward(self, g: torch.Tensor, want_b0: bool = True, stream=None):
+        """(dL/dp, dL/db0) for g = dL/dxi (B, 2n); dL/db0 is None unless wanted."""
+        Bn = g.shape[0]
+        _need(g, (Bn, 2 * self.n), "g")
+        gp = torch.empty((Bn, self.d_p), dtype=torch.float64, device=g.device)
+        gb = torch.empty((Bn, 6), dtype=torch.float64, device=g.device) if want_b0 else None
+        B.plan_qp_backward(self.ctx, _ptr(g), Bn, _ptr(gp), _ptr(gb), _stream(stream))
+        return gp, gb
+
+    def qp_layer(self, p: torch.Tensor, b0: torch.Tensor):
+        """The Step-1 layer as a torch.autograd function of (p, b0)."""
+        return _QPLayer.apply(p, b0, self)
+
     def sample(self, scene, Bn: int, l: int, seed: int, step: int = 0, mu=None, sigma=None,
                stream=None, device=None):
         p = torch.empty((Bn, self.d_p), dtype=torch.float64, device=device or "cuda")
         B.plan_sample(self.ctx, scene, mu, sigma, int(mu is None), l, seed, step, Bn, _ptr(p),
                       _stream(stream))
         return p
+
+
+class _QPLayer(torch.autograd.Function):
+    """Forward and backward through the library's Step-1 layer kernels."""
+
+    @staticmethod
+    def forward(ctx, p, b0, planner):
+        ctx.planner = planner
+        return planner.qp_forward(p.contiguous(), b0.contiguous())
+
+    @staticmethod
+    def backward(ctx, g):
+        gp, gb = ctx.planner.qp_backward(g.contiguous(), want_b0=ctx.needs_input_grad[1])
+        return gp, gb, None
 
 
 class Server:
