@@ -55,6 +55,26 @@ def lane_bounds(scene, prm):
     return prm.lane_margin, scene.n_lanes * scene.lane_width - prm.lane_margin
 
 
+def road_at(scene, prm, x):
+    """Road curvature kappa(x) and lane limits y_lb(x), y_ub(x) at arc length x
+    (any shape), Table I's centripetal and lane-boundary rows on a road given
+    in the Frenet frame.  With a knot table (s, kappa, lb, ub): linear
+    interpolation in x + road_origin, constant beyond the end knots, limits =
+    edges moved inwards by the lane margin.  Without one: kappa_road and the straight
+    lanes of lane_bounds."""
+    x = np.asarray(x, dtype=np.float64) + float(getattr(scene, "road_origin", 0.0))
+    road = np.asarray(getattr(scene, "road", np.zeros((0, 4))), dtype=np.float64).reshape(-1, 4)
+    if road.shape[0] == 0:
+        ylb, yub = lane_bounds(scene, prm)
+        return (np.full(x.shape, float(scene.kappa_road)), np.full(x.shape, ylb),
+                np.full(x.shape, yub))
+    sk = road[:, 0]
+    kappa = np.interp(x, sk, road[:, 1])
+    ylb = np.interp(x, sk, road[:, 2]) + prm.lane_margin
+    yub = np.interp(x, sk, road[:, 3]) - prm.lane_margin
+    return kappa, ylb, yub
+
+
 def obstacle_trajectories(scene, m: int, dt: float):
     """x_o,i(t), y_o,i(t), (N, m): constant-velocity neighbours."""
     t = np.arange(m) * dt
@@ -193,13 +213,15 @@ def kinematics(xi, basis):
     return cx @ W.T, cy @ W.T, cx @ Wd.T, cy @ Wd.T, cx @ Wdd.T, cy @ Wdd.T
 
 
-def alpha_d_step(xi, scene, prm, basis, da_prev):
+def alpha_d_step(xi, scene, prm, basis, da_prev, x_prev=None):
     """Eq. (split_alpha_o) followed by the clips (clip_d_o), (clip_d_v), (clip_d_a).
 
     The unconstrained minimiser of ||F xi - h(alpha, d)||^2 makes every block
     residual zero: for obstacle i, (x - x_o, y - y_o) = (a d cos(al), b d sin(al))
     gives al = atan2((y - y_o)/b, (x - x_o)/a), d = its scaled length; for the
     velocity and acceleration blocks the polar angle and magnitude.
+    The road curvature of v_max-bar is kappa(^k xi) as printed in Eq. (clip_d_v):
+    taken at the positions x_prev of the previous iterate (default: of xi).
     Returns h (B, rows of F), the clipped d_a (B, m) and the pieces as a dict.
     """
     W = basis[0]
@@ -224,7 +246,7 @@ def alpha_d_step(xi, scene, prm, basis, da_prev):
     S = np.abs(np.sin(al_a - al_v))
     vmin_bar = np.maximum(prm.v_min, np.sqrt(da_prev * S / prm.kappa_max))
     cos2 = np.cos(al_v) ** 2
-    kr = abs(scene.kappa_road)
+    kr = np.abs(road_at(scene, prm, x if x_prev is None else x_prev)[0])
     with np.errstate(divide="ignore"):
         vmax_bar = np.where(kr * cos2 > 0.0,
                             np.minimum(prm.v_max, np.sqrt(prm.c_max / np.maximum(kr * cos2, 1e-300))),
@@ -246,14 +268,23 @@ def alpha_d_step(xi, scene, prm, basis, da_prev):
 
 
 def lane_vector(scene, prm, m):
-    """e of Eq. (lane_reform): G xi <= e with G = [W; -W] on the y block."""
+    """e of Eq. (lane_reform): G xi <= e with G = [W; -W] on the y block
+    (straight lanes; lane_vector_at for a road whose limits depend on x)."""
     ylb, yub = lane_bounds(scene, prm)
     return np.concatenate([np.full(m, yub), np.full(m, -ylb)])
 
 
+def lane_vector_at(scene, prm, x):
+    """e(xi) of Eq. (lane_reform) at the positions x (B, m) of an iterate:
+    (B, 2m) = [y_ub(x), -y_lb(x)]."""
+    _, ylb, yub = road_at(scene, prm, x)
+    return np.concatenate([yub, -ylb], axis=1)
+
+
 def slack_step(xi, G, e):
-    """s = max(0, e - G xi), the minimiser of ||G xi - e + s||^2 over s >= 0."""
-    return np.maximum(0.0, e[None, :] - xi @ G.T)
+    """s = max(0, e - G xi), the minimiser of ||G xi - e + s||^2 over s >= 0;
+    e is (2m,) or per sample (B, 2m)."""
+    return np.maximum(0.0, np.atleast_2d(e) - xi @ G.T)
 
 
 def xi_step(xi_bar, lam, h, s, ops, e, b_eq, rho):
@@ -261,7 +292,7 @@ def xi_step(xi_bar, lam, h, s, ops, e, b_eq, rho):
     F, G, A = ops
     nn = F.shape[1]
     H = np.eye(nn) + rho * (F.T @ F) + rho * (G.T @ G)
-    rhs = xi_bar + lam + rho * (h @ F) + rho * ((e[None, :] - s) @ G)
+    rhs = xi_bar + lam + rho * (h @ F) + rho * ((np.atleast_2d(e) - s) @ G)
     return kkt_solve(H, A, rhs, b_eq)
 
 
@@ -272,26 +303,28 @@ def project(xi_bar, scene, prm, basis, iters: int | None = None, trace: bool = F
     ||F xi - h|| + ||G xi - e + s|| (the residual the multipliers drive to zero).
     """
     K = prm.inner_iters if iters is None else iters
-    m = basis[0].shape[0]
     ops = projection_operators(basis, scene.n_obs)
     F, G, A = ops
-    e = lane_vector(scene, prm, m)
     x0, y0, vx0, vy0, ax0, ay0 = np.asarray(scene.ego, dtype=np.float64)
     b_eq = [x0, vx0, ax0, y0, vy0, ay0]
 
     xi = np.array(xi_bar, dtype=np.float64, copy=True)
     lam = np.zeros_like(xi)
-    _, _, _, _, xdd, ydd = kinematics(xi, basis)
+    x, _, _, _, xdd, ydd = kinematics(xi, basis)
     da = np.minimum(np.hypot(xdd, ydd), prm.a_max)
-    h, da, _ = alpha_d_step(xi, scene, prm, basis, da)
+    e = lane_vector_at(scene, prm, x)                                   # e(^0 xi)
+    h, da, _ = alpha_d_step(xi, scene, prm, basis, da, x)
     s = slack_step(xi, G, e)
     hist = []
     for _ in range(K):
-        xi = xi_step(xi_bar, lam, h, s, ops, e, b_eq, prm.rho)           # split_xy
-        h, da, _ = alpha_d_step(xi, scene, prm, basis, da)              # split_alpha_o + clips
+        x_prev = x
+        xi = xi_step(xi_bar, lam, h, s, ops, e, b_eq, prm.rho)           # split_xy with e(^k xi)
+        x = kinematics(xi, basis)[0]
+        h, da, _ = alpha_d_step(xi, scene, prm, basis, da, x_prev)      # split_alpha_o + clips
+        e = lane_vector_at(scene, prm, x)                               # e(^{k+1} xi)
         s = slack_step(xi, G, e)                                        # update_slack
         rf = xi @ F.T - h
-        rg = xi @ G.T - e[None, :] + s
+        rg = xi @ G.T - e + s
         lam = lam - 0.5 * prm.rho * (rf @ F) - 0.5 * prm.rho * (rg @ G)  # update_lagrange
         if trace:
             hist.append(float(np.mean(np.linalg.norm(rf, axis=1) + np.linalg.norm(rg, axis=1))))
@@ -317,11 +350,11 @@ def score(xi, scene, prm, basis):
     speed = np.hypot(xd, yd)
     with np.errstate(divide="ignore", invalid="ignore"):
         kappa = np.where(speed > 0.0, (ydd * xd - xdd * yd) / speed ** 3, 0.0)
-    ylb, yub = lane_bounds(scene, prm)
+    kroad, ylb, yub = road_at(scene, prm, x)
     per_t = (np.maximum(0.0, speed - prm.v_max)
              + np.maximum(0.0, np.hypot(xdd, ydd) - prm.a_max)
              + np.maximum(0.0, np.abs(kappa) - prm.kappa_max)
-             + np.maximum(0.0, xd ** 2 * abs(scene.kappa_road) - prm.c_max)
+             + np.maximum(0.0, xd ** 2 * np.abs(kroad) - prm.c_max)
              + np.maximum(0.0, y - yub) + np.maximum(0.0, ylb - y))
     r = coll + per_t.sum(axis=1)
     cu = ((speed - prm.v_max) ** 2).sum(axis=1)

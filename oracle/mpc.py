@@ -28,6 +28,7 @@ def advance(scene, xi, prm, steps: int = 5, basis=None):
     ob[:, 0] = ob[:, 0] + ob[:, 2] * t - x
     ob[:, 1] = ob[:, 1] + ob[:, 3] * t
     nxt.obstacles = ob
+    nxt.road_origin = float(getattr(scene, "road_origin", 0.0)) + x   # frame moves with the ego
     return nxt
 
 

@@ -84,10 +84,20 @@ class Scene:
     lane_width: float
     kappa_road: float
     obstacles: np.ndarray
+    # Road profile along the centre line (Frenet frame: x is arc length):
+    # (R, 4) knots (s, kappa, lb, ub), interpolated linearly in x and held
+    # constant beyond the ends; lb, ub are the road edges.  Empty: a road of
+    # constant curvature kappa_road with edges 0 and n_lanes * lane_width.
+    road: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((0, 4)))
+    road_origin: float = 0.0     # arc length of x = 0 along the road profile
 
     @property
     def n_obs(self) -> int:
         return int(self.obstacles.shape[0])
+
+    @property
+    def n_road(self) -> int:
+        return int(np.asarray(self.road).reshape(-1, 4).shape[0])
 
     def lane_centres(self) -> np.ndarray:
         return (np.arange(self.n_lanes) + 0.5) * self.lane_width
@@ -144,6 +154,24 @@ def make_scene(seed: int, n_lanes: int, n_obs: int, lane_width: float = 3.5,
         obs[:, 5] = axes[1]
     return Scene(ego=ego, n_lanes=n_lanes, lane_width=lane_width,
                  kappa_road=kappa_road, obstacles=obs)
+
+
+def curved_road(n_lanes: int, lane_width: float = 3.5, kappa: float = 0.01,
+                bend=(40.0, 140.0), narrow_at: float | None = 90.0) -> np.ndarray:
+    """Knots (s, kappa, lb, ub) of a road that enters a bend of curvature
+    `kappa` over the arc-length interval `bend` (ramps of 20 m), and, from
+    `narrow_at` on, loses its top lane (ramp of 10 m)."""
+    w = n_lanes * lane_width
+    s0, s1 = bend
+    knots = [(0.0, 0.0), (s0, 0.0), (s0 + 20.0, kappa), (s1 - 20.0, kappa), (s1, 0.0)]
+    ss = sorted({k[0] for k in knots} | ({narrow_at, narrow_at + 10.0} if narrow_at else set()))
+    ks, kv = zip(*knots)
+    rows = []
+    for x in ss:
+        ub = w if narrow_at is None else float(np.interp(x, [narrow_at, narrow_at + 10.0],
+                                                         [w, w - lane_width]))
+        rows.append((x, float(np.interp(x, ks, kv)), 0.0, ub))
+    return np.array(rows)
 
 
 def make_samples(seed: int, scene: Scene, B: int, n_seg: int,
