@@ -115,9 +115,22 @@ typedef struct { double x, y, vx, vy, ax, ay; } plan_ego;
  * Table I's collision constraint. */
 typedef struct { double x0, y0, vx, vy, a, b; } plan_obstacle;
 
+/* A knot of the road profile along the reference centre line (Frenet frame,
+ * Sec. III-C: x is arc length, y the lateral offset): road curvature kappa of
+ * Eq. (cent_bounds) and the road edges lb < ub of Table I's lane-boundary row
+ * at arc length s. */
+typedef struct { double s, kappa, lb, ub; } plan_road_knot;
+
 /* One driving scene; `obs` is host memory with n_obs entries (may be NULL
- * when n_obs == 0).  kappa_road is the road curvature of Eq. (cent_bounds);
- * 0 for a straight road. */
+ * when n_obs == 0).
+ * Road: with n_road == 0 the road is straight-laned with constant curvature
+ * kappa_road (0 for a straight road) and lane limits [lane_margin,
+ * n_lanes lane_width - lane_margin].  With n_road in 1..8 knots (host, s
+ * strictly increasing), kappa(x) and the edges are interpolated linearly in
+ * x + road_origin and held constant beyond the end knots; the lane limits are
+ * the edges moved inwards by lane_margin.  As the paper prescribes, the
+ * projection evaluates kappa and the limits at the positions of the current
+ * iterate (Alg. 2, analysis of step split_xy). */
 typedef struct {
     plan_ego ego;
     int n_lanes;
@@ -125,6 +138,9 @@ typedef struct {
     double kappa_road;
     int n_obs;
     const plan_obstacle* obs;
+    int n_road;
+    const plan_road_knot* road;
+    double road_origin;   /* arc length of x = 0 along the road profile */
 } plan_scene;
 
 /* Sampling distribution of p carried between MPC cycles (Alg. 1 lines 2, 14).
@@ -230,7 +246,9 @@ int plan_step(plan_ctx* ctx, const plan_scene* scene, plan_cem_state* st, int B,
  * `steps` elements of the plan, then replans): the new ego state is the
  * trajectory xi (2 n_coef coefficients, host) at t = steps dt, obstacles move
  * on at constant velocity, and the frame is shifted so that the ego is again at
- * x = 0.  out->obs points to out_obs (host, in->n_obs entries, caller-owned).
+ * x = 0 (road_origin grows by the distance travelled; the road knots are
+ * shared with `in`).  out->obs points to out_obs (host, in->n_obs entries,
+ * caller-owned).
  * Host-only arithmetic in float64; no device work. */
 int plan_advance(const plan_config* cfg, const plan_scene* in, const double* xi, int steps,
                  plan_scene* out, plan_obstacle* out_obs);
@@ -370,7 +388,7 @@ int plan_qp_backward(plan_ctx* ctx, const double* g, int B, double* grad_p, doub
  * No context is needed and nothing is allocated: no cudaMalloc / cudaFree and
  * no allocating library routine.  The basis, the KKT inverses, a copy of the
  * scene and the per-iteration intermediates live in one fixed __device__ array
- * of about 4.4 MB in the library, which every GPU that loads the library holds
+ * of about 4.7 MB in the library, which every GPU that loads the library holds
  * until the process exits.  Limits: B <= 256 samples, 8 <= m <= 128 timesteps,
  * n_obs <= 32 obstacles, n_coef <= 16, n_seg <= 4; larger requests return
  * PLAN_ECAPACITY.  Of `cfg` only m, n_coef, n_seg, inner_iters, dt, rho, the

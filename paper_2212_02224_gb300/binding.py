@@ -46,10 +46,15 @@ class PlanObstacle(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in ("x0", "y0", "vx", "vy", "a", "b")]
 
 
+class PlanRoadKnot(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("s", "kappa", "lb", "ub")]
+
+
 class PlanScene(ctypes.Structure):
     _fields_ = [("ego", PlanEgo), ("n_lanes", ctypes.c_int), ("lane_width", ctypes.c_double),
                 ("kappa_road", ctypes.c_double), ("n_obs", ctypes.c_int),
-                ("obs", ctypes.POINTER(PlanObstacle))]
+                ("obs", ctypes.POINTER(PlanObstacle)), ("n_road", ctypes.c_int),
+                ("road", ctypes.POINTER(PlanRoadKnot)), ("road_origin", ctypes.c_double)]
 
 
 class PlanCemState(ctypes.Structure):
@@ -194,6 +199,15 @@ def make_scenes(scenes):
             arr[i].obs = ctypes.cast(oa, ctypes.POINTER(PlanObstacle))
         else:
             arr[i].obs = None
+        road = [list(k) for k in getattr(sc, "road", [])]
+        arr[i].n_road = len(road)
+        if road:
+            ra = (PlanRoadKnot * len(road))(*[PlanRoadKnot(*[float(v) for v in k]) for k in road])
+            keep.append(ra)
+            arr[i].road = ctypes.cast(ra, ctypes.POINTER(PlanRoadKnot))
+        else:
+            arr[i].road = None
+        arr[i].road_origin = float(getattr(sc, "road_origin", 0.0))
     keep.append(arr)
     return arr, keep
 
@@ -321,11 +335,13 @@ def plan_solve_fp64_noalloc(cfg: PlanConfig, scene, p_ptr: int, B: int, xi_ptr, 
 
 
 class SceneView:
-    """Plain scene record (ego, n_lanes, lane_width, kappa_road, obstacles)."""
+    """Plain scene record (ego, n_lanes, lane_width, kappa_road, obstacles,
+    road knots, road_origin)."""
 
-    def __init__(self, ego, n_lanes, lane_width, kappa_road, obstacles):
+    def __init__(self, ego, n_lanes, lane_width, kappa_road, obstacles, road=(), road_origin=0.0):
         self.ego, self.n_lanes, self.lane_width = list(ego), n_lanes, lane_width
         self.kappa_road, self.obstacles = kappa_road, [list(o) for o in obstacles]
+        self.road, self.road_origin = [list(k) for k in road], road_origin
 
     @property
     def n_obs(self):
@@ -345,7 +361,7 @@ def plan_advance(cfg: PlanConfig, scene, xi, steps: int):
     obs = [[out_obs[i].x0, out_obs[i].y0, out_obs[i].vx, out_obs[i].vy, out_obs[i].a, out_obs[i].b]
            for i in range(n_obs)]
     return SceneView([e.x, e.y, e.vx, e.vy, e.ax, e.ay], out.n_lanes, out.lane_width,
-                     out.kappa_road, obs)
+                     out.kappa_road, obs, getattr(scene, "road", []), out.road_origin)
 
 
 def plan_server_create(cfg: PlanConfig, max_executors: int, device_budget: int, max_episodes: int):

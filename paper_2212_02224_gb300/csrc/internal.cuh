@@ -13,17 +13,75 @@ constexpr int kMaxDp = 8;        // entries of p
 constexpr int kMaxObs = 64;      // obstacles per scene
 constexpr int kMaxM = 256;       // timesteps
 constexpr int kMaxEliteC = 2048; // ConstraintEliteSet size
+constexpr int kMaxRoad = 8;      // knots of a road profile
 
 // Geometry of one scene as the kernels see it.
 struct DevScene {
   double ego[6];        // b0: x, y, vx, vy, ax, ay
-  double y_lb, y_ub;    // lane-boundary rows of Table I
-  double kappa_road;    // road curvature (centripetal bound)
+  double y_lb, y_ub;    // lane-boundary rows of Table I (no road profile)
+  double kappa_road;    // road curvature (centripetal bound, no road profile)
   double lane_width;
   int n_lanes, n_obs;
   int obs_off;          // first obstacle in the obstacle array (6 doubles each)
-  int pad;
+  int n_road;           // knots of the road profile (0: constant road)
+  // road profile in the scene's frame (knot s already shifted by the origin),
+  // edges already moved inwards by the lane margin: {s, kappa, y_lb, y_ub}
+  double road[kMaxRoad][4];
 };
+
+// The road profile of a scene in the scene's frame, edges moved inwards by the
+// lane margin (host side; the knots are validated by the caller).
+inline void fill_road(DevScene& d, const plan_scene& s, double lane_margin) {
+  d.n_road = s.n_road;
+  for (int i = 0; i < s.n_road && i < kMaxRoad; ++i) {
+    d.road[i][0] = s.road[i].s - s.road_origin;
+    d.road[i][1] = s.road[i].kappa;
+    d.road[i][2] = s.road[i].lb + lane_margin;
+    d.road[i][3] = s.road[i].ub - lane_margin;
+  }
+}
+
+// Road knots of a scene: NULL message when valid, else the reason.
+inline const char* road_invalid(const plan_scene& s, double lane_margin) {
+  if (s.n_road < 0 || s.n_road > kMaxRoad) return "n_road must be in [0, 8]";
+  if (s.n_road > 0 && !s.road) return "road is NULL";
+  if (!(s.road_origin == s.road_origin) || s.road_origin - s.road_origin != 0.0)
+    return "road_origin is not finite";
+  for (int i = 0; i < s.n_road; ++i) {
+    const plan_road_knot& k = s.road[i];
+    const double v[4] = {k.s, k.kappa, k.lb, k.ub};
+    for (double x : v)
+      if (x - x != 0.0) return "road knot not finite";
+    if (i > 0 && !(k.s > s.road[i - 1].s)) return "road knots: s must increase";
+    if (!(k.ub - k.lb - 2 * lane_margin > 0)) return "road knot narrower than twice lane_margin";
+  }
+  return nullptr;
+}
+
+// Road curvature and lane limits at x (linear between knots, constant beyond).
+template <class T>
+__host__ __device__ inline void road_eval(const DevScene& sc, T x, T* kappa, T* ylb, T* yub) {
+  const int n = sc.n_road;
+  if (n == 0) {
+    *kappa = T(sc.kappa_road); *ylb = T(sc.y_lb); *yub = T(sc.y_ub);
+    return;
+  }
+  if (!(x > T(sc.road[0][0]))) {
+    *kappa = T(sc.road[0][1]); *ylb = T(sc.road[0][2]); *yub = T(sc.road[0][3]);
+    return;
+  }
+  int i = 0;
+  while (i + 1 < n && T(sc.road[i + 1][0]) < x) ++i;
+  if (i + 1 >= n) {
+    *kappa = T(sc.road[n - 1][1]); *ylb = T(sc.road[n - 1][2]); *yub = T(sc.road[n - 1][3]);
+    return;
+  }
+  const T s0 = T(sc.road[i][0]), s1 = T(sc.road[i + 1][0]);
+  const T w = (x - s0) / (s1 - s0);
+  *kappa = T(sc.road[i][1]) + w * (T(sc.road[i + 1][1]) - T(sc.road[i][1]));
+  *ylb = T(sc.road[i][2]) + w * (T(sc.road[i + 1][2]) - T(sc.road[i][2]));
+  *yub = T(sc.road[i][3]) + w * (T(sc.road[i + 1][3]) - T(sc.road[i][3]));
+}
 
 // Per-scene state of the outer loop (Alg. 1), device resident.
 struct DevCem {
@@ -118,6 +176,7 @@ struct Plain64Work {   // HBM intermediates of the FP64 path
   double* state;   // [B][6][m]
   double* eps;     // [B][7][m]
   double* da;      // [B][m]
+  double* xprev;   // [B][m] positions x of the previous iterate (road curvature)
 };
 
 cudaError_t launch_plain64(const DevScene* scenes, const Layout* layout, const int* sample_scene,

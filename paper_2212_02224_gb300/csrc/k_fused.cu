@@ -112,7 +112,7 @@ struct RegCap {
   // registers per thread: one timestep slot per 32 lanes needs about 70, the
   // rest is per-sample state; capped so that enough warps stay resident
   static constexpr int value =
-      SLOTS * WPS >= 8 ? 255 : (SLOTS >= 4 ? 224 : (SLOTS == 2 ? 144 : (WPS == 4 ? 72 : 96)));
+      SLOTS * WPS >= 8 ? 255 : (SLOTS >= 4 ? 224 : (SLOTS == 2 ? 144 : (WPS == 4 ? 76 : 96)));
 };
 
 template <int NC, int SLOTS, int WPS>
@@ -269,6 +269,10 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   float da[SLOTS];
 #pragma unroll
   for (int s = 0; s < SLOTS; ++s) da[s] = 0.f;
+  // road profile: curvature at the previous iterate (Eq. clip_d_v), lane limits
+  // at the current one; without a profile both are the scene's constants
+  const bool road = sc.n_road > 0;
+  float xprev[SLOTS];
 
   float lam = 0.f, dl = 0.f;     // lambda and delta of this lane's slot
   float r_acc = 0.f, cu_acc = 0.f;
@@ -311,9 +315,14 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
         const float sp = fast_sqrt(fmaf(vx[s], vx[s], vy[s] * vy[s]));
         const float am = fast_sqrt(fmaf(ax[s], ax[s], ay[s] * ay[s]));
         const float kap = sp > 0.f ? __fdividef(ay[s] * vx[s] - ax[s] * vy[s], sp * sp * sp) : 0.f;
+        float kro = kr, ylo = y_lb, yup = y_ub;
+        if (road) {
+          road_eval<float>(sc, px[s], &kro, &ylo, &yup);
+          kro = fabsf(kro);
+        }
         const float rt = coll[s] + fmaxf(0.f, sp - v_max) + fmaxf(0.f, am - a_max) +
-                         fmaxf(0.f, fabsf(kap) - kmax) + fmaxf(0.f, vx[s] * vx[s] * kr - c_max) +
-                         fmaxf(0.f, py[s] - y_ub) + fmaxf(0.f, y_lb - py[s]);
+                         fmaxf(0.f, fabsf(kap) - kmax) + fmaxf(0.f, vx[s] * vx[s] * kro - c_max) +
+                         fmaxf(0.f, py[s] - yup) + fmaxf(0.f, ylo - py[s]);
         const float dv = sp - v_max;
         r_acc = fmaf(act[s], rt, r_acc);
         cu_acc = fmaf(act[s] * dv, dv, cu_acc);
@@ -415,8 +424,16 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       const float dap = (it == 0) ? fminf(am, a_max) : da[s];
       const float vmin_b = fmaxf(v_min, fast_sqrt(dap * S * inv_kmax));
       float vmax_b = v_max;
-      if (kr > 0.f) {
-        const float tc = kr * cv * cv;
+      float krs = kr, ylbs = y_lb, yubs = y_ub;
+      if (road) {
+        float unused;
+        road_eval<float>(sc, it == 0 ? px[s] : xprev[s], &krs, &unused, &unused);
+        krs = fabsf(krs);
+        road_eval<float>(sc, px[s], &unused, &ylbs, &yubs);
+        xprev[s] = px[s];
+      }
+      if (krs > 0.f) {
+        const float tc = krs * cv * cv;
         if (tc > 0.f) vmax_b = fminf(v_max, fast_sqrt(__fdividef(c_max, tc)));
       }
       const float dv = fminf(fmaxf(sp, vmin_b), vmax_b);
@@ -427,7 +444,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       const float A = act[s];
       const float evx = A * fmaf(dv, cv, -vx[s]), evy = A * fmaf(dv, sv, -vy[s]);
       const float eax = A * fmaf(dan, ca, -ax[s]), eay = A * fmaf(dan, sa, -ay[s]);
-      const float ely = fminf(fmaxf(py[s], y_lb), y_ub) - py[s];
+      const float ely = fminf(fmaxf(py[s], ylbs), yubs) - py[s];
       const float exs = A * ex[s];
       const float eoy = A * (ey[s] + ely);
       const float* row = sW + tcl[s] * ST;

@@ -104,14 +104,21 @@ __global__ void project_kernel(int total, const DevScene* scenes, const int* sam
   const double dap = first ? fmin(am, prm.a_max) : da[t];
   const double vmin_b = fmax(prm.v_min, sqrt(dap * S / prm.kappa_max));
   double vmax_b = prm.v_max;
-  const double kr = fabs(sc.kappa_road);
+  // road curvature at the previous iterate (Eq. clip_d_v), lane limits at this one
+  double* xp = w.xprev + size_t(j) * m;
+  const double xk = first ? x : xp[t];
+  xp[t] = x;
+  double kroad, ylb, yub, unused0, unused1;
+  road_eval(sc, xk, &kroad, &unused0, &unused1);
+  road_eval(sc, x, &unused0, &ylb, &yub);
+  const double kr = fabs(kroad);
   if (kr * cv * cv > 0.0) vmax_b = fmin(prm.v_max, sqrt(prm.c_max / (kr * cv * cv)));
   const double dv = fmin(fmax(sp, vmin_b), vmax_b);
   const double kd = dv * dv * prm.kappa_max;
   const double amax_b = (S * prm.a_max <= kd) ? prm.a_max : kd / S;
   const double dan = fmin(fmax(am, 0.0), amax_b);
   da[t] = dan;
-  const double s1 = fmax(0.0, sc.y_ub - y), s2 = fmax(0.0, y - sc.y_lb);
+  const double s1 = fmax(0.0, yub - y), s2 = fmax(0.0, y - ylb);
   double* e = w.eps + size_t(j) * 7 * m;
   e[t] = ex;
   e[m + t] = ey;
@@ -120,7 +127,7 @@ __global__ void project_kernel(int total, const DevScene* scenes, const int* sam
   e[4 * m + t] = dan * ca - ax;
   e[5 * m + t] = dan * sa - ay;
   // G^T (e - s - G xi) per t: (y_ub - s1 - y) - (-y_lb - s2 + y)
-  e[6 * m + t] = (sc.y_ub - s1 - y) - (-sc.y_lb - s2 + y);
+  e[6 * m + t] = (yub - s1 - y) - (-ylb - s2 + y);
 }
 
 // w = F^T (h - F xi) + G^T (e - s - G xi): thread = (sample, slot).
@@ -178,11 +185,13 @@ __global__ void score_kernel(const DevScene* scenes, const int* sample_scene, co
   const int m = prm.m, n = prm.n;
   const DevScene& sc = scenes[scene_of(sample_scene, j)];
   const double* st = w.state + size_t(j) * 6 * m;
-  const double kr = fabs(sc.kappa_road);
   double r = 0.0, cu = 0.0;
   for (int t = lane; t < m; t += 32) {
     const double x = st[t], y = st[m + t], vx = st[2 * m + t], vy = st[3 * m + t];
     const double ax = st[4 * m + t], ay = st[5 * m + t];
+    double kroad, ylb, yub;
+    road_eval(sc, x, &kroad, &ylb, &yub);
+    const double kr = fabs(kroad);
     const double tt = t * prm.dt;
     double coll = 0.0;
     for (int i = 0; i < sc.n_obs; ++i) {
@@ -195,7 +204,7 @@ __global__ void score_kernel(const DevScene* scenes, const int* sample_scene, co
     const double kap = sp > 0.0 ? (ay * vx - ax * vy) / (sp * sp * sp) : 0.0;
     r += coll + fmax(0.0, sp - prm.v_max) + fmax(0.0, am - prm.a_max) +
          fmax(0.0, fabs(kap) - prm.kappa_max) + fmax(0.0, vx * vx * kr - prm.c_max) +
-         fmax(0.0, y - sc.y_ub) + fmax(0.0, sc.y_lb - y);
+         fmax(0.0, y - yub) + fmax(0.0, ylb - y);
     cu += (sp - prm.v_max) * (sp - prm.v_max);
   }
   for (int o = 16; o >= 1; o >>= 1) {

@@ -337,6 +337,10 @@ tc_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ layout
   const float* Mrow = &sM[caxis][kk][0];
 
   float da[4] = {0.f, 0.f, 0.f, 0.f};
+  // road profile: curvature at the previous iterate (Eq. clip_d_v), lane limits
+  // at the current one; without a profile both are the scene's constants
+  const bool road = sc.n_road > 0;
+  float xprev[4] = {0.f, 0.f, 0.f, 0.f};
   float lam = 0.f, dl = 0.f;
   float r_acc[4] = {0.f, 0.f, 0.f, 0.f}, cu_acc[4] = {0.f, 0.f, 0.f, 0.f};
   float* thr = sThr + warp * 4 * N;
@@ -404,9 +408,14 @@ tc_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ layout
         const float am = fast_sqrt(fmaf(ax[sl], ax[sl], ay[sl] * ay[sl]));
         const float kap =
             sp > 0.f ? __fdividef(ay[sl] * vx[sl] - ax[sl] * vy[sl], sp * sp * sp) : 0.f;
+        float kro = kr, ylo = y_lb, yup = y_ub;
+        if (road) {
+          road_eval<float>(sc, px[sl], &kro, &ylo, &yup);
+          kro = fabsf(kro);
+        }
         const float rt = coll + fmaxf(0.f, sp - v_max) + fmaxf(0.f, am - a_max) +
-                         fmaxf(0.f, fabsf(kap) - kmax) + fmaxf(0.f, vx[sl] * vx[sl] * kr - c_max) +
-                         fmaxf(0.f, py[sl] - y_ub) + fmaxf(0.f, y_lb - py[sl]);
+                         fmaxf(0.f, fabsf(kap) - kmax) + fmaxf(0.f, vx[sl] * vx[sl] * kro - c_max) +
+                         fmaxf(0.f, py[sl] - yup) + fmaxf(0.f, ylo - py[sl]);
         const float dv = sp - v_max;
         r_acc[sl] = A[sl] * rt;
         cu_acc[sl] = A[sl] * dv * dv;
@@ -473,8 +482,16 @@ tc_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ layout
       const float dap = (it == 0) ? fminf(am, a_max) : da[sl];
       const float vmin_b = fmaxf(v_min, fast_sqrt(dap * S * inv_kmax));
       float vmax_b = v_max;
-      if (kr > 0.f) {
-        const float tc = kr * cv * cv;
+      float krs = kr, ylbs = y_lb, yubs = y_ub;
+      if (road) {
+        float unused;
+        road_eval<float>(sc, it == 0 ? px[sl] : xprev[sl], &krs, &unused, &unused);
+        krs = fabsf(krs);
+        road_eval<float>(sc, px[sl], &unused, &ylbs, &yubs);
+        xprev[sl] = px[sl];
+      }
+      if (krs > 0.f) {
+        const float tc = krs * cv * cv;
         if (tc > 0.f) vmax_b = fminf(v_max, fast_sqrt(__fdividef(c_max, tc)));
       }
       const float dv = fminf(fmaxf(sp, vmin_b), vmax_b);
@@ -484,7 +501,7 @@ tc_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ layout
       da[sl] = dan;
       const float a_ = A[sl];
       const float rows[6] = {a_ * ex,
-                             a_ * (ey + fminf(fmaxf(py[sl], y_lb), y_ub) - py[sl]),
+                             a_ * (ey + fminf(fmaxf(py[sl], ylbs), yubs) - py[sl]),
                              a_ * fmaf(dv, cv, -vx[sl]), a_ * fmaf(dv, sv, -vy[sl]),
                              a_ * fmaf(dan, ca, -ax[sl]), a_ * fmaf(dan, sa, -ay[sl])};
       if (t < mK) {

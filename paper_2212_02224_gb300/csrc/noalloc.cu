@@ -40,9 +40,9 @@ constexpr size_t kEps = al(sizeof(double) * kNaMaxB * 7 * kNaMaxM);
 constexpr size_t kDa = al(sizeof(double) * kNaMaxB * kNaMaxM);
 constexpr size_t kScratchBytes = kScene + kObs + kLayout + kSampleScene + kBasis64 + kBasis32 +
                                  kS1_64 + kS1_32 + kPj64 + kPj32 + 4 * kVec + kState + kEps +
-                                 kDa;
+                                 2 * kDa;
 
-// The scratch array (about 4.4 MB); every GPU that loads the library holds it
+// The scratch array (about 4.7 MB); every GPU that loads the library holds it
 // until the process exits.  All calls share it.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -99,6 +99,7 @@ extern "C" int plan_solve_fp64_noalloc(const plan_config* cfg, const plan_scene*
   for (int i = 0; i < scene->n_obs; ++i)
     if (!(scene->obs[i].a > 0) || !(scene->obs[i].b > 0))
       return na_fail(PLAN_EINVAL, "obstacle axes must be > 0");
+  if (const char* why = road_invalid(*scene, cfg->lane_margin)) return na_fail(PLAN_EINVAL, why);
   if (B == 0) return PLAN_OK;
   if (!p || !resid || !cu) return na_fail(PLAN_EINVAL, "p, resid and cu must be non-NULL");
 
@@ -148,6 +149,7 @@ extern "C" int plan_solve_fp64_noalloc(const plan_config* cfg, const plan_scene*
   w.state = reinterpret_cast<double*>(take(kState));
   w.eps = reinterpret_cast<double*>(take(kEps));
   w.da = reinterpret_cast<double*>(take(kDa));
+  w.xprev = reinterpret_cast<double*>(take(kDa));
 
   Params prm{};
   prm.m = cfg->m; prm.n = cfg->n_coef; prm.n_seg = cfg->n_seg; prm.K = cfg->inner_iters;
@@ -168,6 +170,7 @@ extern "C" int plan_solve_fp64_noalloc(const plan_config* cfg, const plan_scene*
   sp.sc.n_lanes = scene->n_lanes;
   sp.sc.n_obs = scene->n_obs;
   sp.sc.obs_off = 0;
+  fill_road(sp.sc, *scene, cfg->lane_margin);
   for (int i = 0; i < scene->n_obs; ++i) {
     const plan_obstacle& o = scene->obs[i];
     const double v[6] = {o.x0, o.y0, o.vx, o.vy, o.a, o.b};

@@ -191,6 +191,8 @@ int check_scene(plan_ctx* ctx, const plan_scene* s, int idx) {
         !std::isfinite(o.vx) || !std::isfinite(o.vy))
       return fail(ctx, PLAN_EINVAL, "scene %d: obstacle %d invalid (axes must be > 0)", idx, i);
   }
+  if (const char* why = road_invalid(*s, ctx->cfg.lane_margin))
+    return fail(ctx, PLAN_EINVAL, "scene %d: %s", idx, why);
   return PLAN_OK;
 }
 
@@ -205,6 +207,7 @@ DevScene to_dev(const plan_ctx* ctx, const plan_scene& s, int obs_off) {
   d.n_lanes = s.n_lanes;
   d.n_obs = s.n_obs;
   d.obs_off = obs_off;
+  fill_road(d, s, ctx->cfg.lane_margin);
   return d;
 }
 
@@ -536,6 +539,7 @@ int plan_init(const plan_config* cfg, plan_ctx** out) {
     A(dalloc(ctx, &ctx->pw.state, B * 6 * m));
     A(dalloc(ctx, &ctx->pw.eps, B * 7 * m));
     A(dalloc(ctx, &ctx->pw.da, B * m));
+    A(dalloc(ctx, &ctx->pw.xprev, B * m));
   }
   if (st != PLAN_OK) return bail(st);
   cem_setup();
@@ -956,6 +960,7 @@ int plan_advance(const plan_config* cfg, const plan_scene* in, const double* xi,
     out_obs[i] = ob;
   }
   o.obs = in->n_obs > 0 ? out_obs : nullptr;
+  o.road_origin = in->road_origin + st[0];   // same knots, frame moved with the ego
   *out = o;
   return PLAN_OK;
 }

@@ -43,6 +43,7 @@ struct Request {
   uint64_t ticket = 0;
   plan_scene scene{};
   std::vector<plan_obstacle> obs;
+  std::vector<plan_road_knot> road;
   int B = 0, m = 0;
   uint64_t episode = 0, seed = 0;
   int fresh = 0;
@@ -188,6 +189,7 @@ bool launch_wave(plan_server* s, Executor* e) {
     Request& r = e->wave[i];
     scenes[i] = r.scene;
     scenes[i].obs = r.obs.empty() ? nullptr : r.obs.data();
+    scenes[i].road = r.road.empty() ? nullptr : r.road.data();
     B[i] = r.B;
     plan_cem_state cs{};
     cs.seed = r.seed;
@@ -329,9 +331,11 @@ int plan_submit(plan_server* s, const plan_request* req, uint64_t* ticket) {
     return fail_srv(s, PLAN_ECAPACITY, "n_obs exceeds max_obs");
   if (sc.n_obs > 0 && !sc.obs) return fail_srv(s, PLAN_EINVAL, "obs is NULL");
   if (sc.n_lanes < 1 || !(sc.lane_width > 0)) return fail_srv(s, PLAN_EINVAL, "invalid lanes");
+  if (const char* why = road_invalid(sc, s->base.lane_margin)) return fail_srv(s, PLAN_EINVAL, why);
   Request r;
   r.scene = sc;
   r.obs.assign(sc.obs, sc.obs + sc.n_obs);
+  r.road.assign(sc.road, sc.road + sc.n_road);
   r.B = req->B;
   r.m = m;
   r.episode = req->episode;
