@@ -1,606 +1,13 @@
-// Fused FP32 lower-level solve: Step 1 (Alg. 1 line 7 through the folded KKT
-// inverse of Eq. over_3), all K iterations of Alg. 2 and the scoring of
-// Alg. 1 line 9 / Sec. V-A, one warp per sample, all state on chip.
-//
-// State is kept relative to the Step-1 solution: delta = xi - xi_bar.  Per
-// iteration and sample the warp
-//   A. evaluates x, y and their derivatives at the lane's timesteps
-//      t = s*32 + lane as (reference at xi_bar) + W delta (Eq. param; basis
-//      rows staged in shared memory),
-//   B. projects onto every obstacle ellipse (Eqs. split_alpha_o, clip_d_o),
-//   C. projects velocity and acceleration (Eqs. clip_d_v, clip_d_a), the lane
-//      rows (Eq. update_slack) and accumulates the transposed contraction
-//        w = F^T (h - F xi) + G^T (e - s - G xi),
-//   D. reduce-scatters w over the warp, updates the multipliers
-//      lambda += rho/2 w (Eq. update_lagrange) and takes the xi-step of
-//      Eq. split_xy in increment form
-//        delta' = delta + M (lambda + rho w - delta).
-// The increment form is exact: with H = I + rho P, P = F^T F + G^T G and the
-// KKT inverse [[M, C], [C^T, D]] of [[H, A^T], [A, 0]], M H = I - C A, so
-// M (xi_bar + lambda + rho F^T h + rho G^T (e - s)) + C b0
-//   = xi + M (xi_bar - xi + lambda + rho w) + C (b0 - A xi),
-// and every iterate satisfies A xi = b0.  Working on delta (metres) instead
-// of xi (hundreds of metres) keeps float32 rounding from accumulating.
-//
-// The closed form of Eq. split_alpha_o is used without trigonometry: for an
-// obstacle with scaled offset (sx, sy) = ((x - x_o)/a, (y - y_o)/b) and
-// d^2 = sx^2 + sy^2, cos(alpha) = sx/d, sin(alpha) = sy/d, so the clipped
-// point h = o + (a max(1,d) cos, b max(1,d) sin) differs from the trajectory
-// point by (x - x_o, y - y_o) (1/d - 1) when d < 1 and by zero otherwise.
-#include "internal.cuh"
+// Fused FP32 lower-level solve: host side of the scenes without a road profile
+// (the kernel template is in fused_kernel.cuh; road-profile instantiations in
+// k_fused_road.cu).
+#include "fused_kernel.cuh"
 
 namespace plan {
-namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
-
-// sqrt(x) for x >= 0 through the hardware reciprocal square root.
-__device__ __forceinline__ float fast_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
-
-// Packed float32 pairs (two independent fma.rn per instruction on sm_100+).
-__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-
-// W[t] . a, Wd[t] . a, Wdd[t] . a for both axes, with coefficient pairs
-// (k, k+1) in packed registers: `row` holds the three zero-padded basis rows
-// of timestep t, xv / yv the padded coefficient pairs.
-template <int NC>
-__device__ __forceinline__ void kin(const float* __restrict__ row,
-                                    const float2 (&xv)[basis32_ncp(NC) / 2],
-                                    const float2 (&yv)[basis32_ncp(NC) / 2], float (&o)[6]) {
-  constexpr int NCP = basis32_ncp(NC);
-#pragma unroll
-  for (int mat = 0; mat < 3; ++mat) {
-    float2 ax = f2(0.f, 0.f), ay = f2(0.f, 0.f);
-#pragma unroll
-    for (int k4 = 0; k4 < NCP; k4 += 4) {
-      const float4 w = *reinterpret_cast<const float4*>(row + mat * NCP + k4);
-      const float2 w01 = f2(w.x, w.y), w23 = f2(w.z, w.w);
-      ax = fma2(w01, xv[k4 / 2], ax);
-      ay = fma2(w01, yv[k4 / 2], ay);
-      ax = fma2(w23, xv[k4 / 2 + 1], ax);
-      ay = fma2(w23, yv[k4 / 2 + 1], ay);
-    }
-    o[2 * mat] = ax.x + ax.y;
-    o[2 * mat + 1] = ay.x + ay.y;
-  }
-}
-
-// Sum over the warp of the 2 n partial sums of the transposed contraction:
-// on return lane (axis * 16 + k) holds the total of coefficient k of `axis`
-// (recursive halving: at offset o a lane keeps the half of the slots selected
-// by bit o of its index and adds its partner's copy of that half).
-template <int NC, int NP>
-__device__ __forceinline__ float warp_reduce_slots(const float2 (&wx)[NP], const float2 (&wy)[NP],
-                                                   int lane) {
-  float v[16];
-  const bool hi = (lane & 16) != 0;
-#pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    if (i < NC) {
-      const float xv = (i & 1) ? wx[i / 2].y : wx[i / 2].x;
-      const float yv = (i & 1) ? wy[i / 2].y : wy[i / 2].x;
-      v[i] = (hi ? yv : xv) + __shfl_xor_sync(kFull, hi ? xv : yv, 16);
-    } else {
-      v[i] = 0.f;
-    }
-  }
-#pragma unroll
-  for (int o = 8; o >= 1; o >>= 1) {
-    const bool up = (lane & o) != 0;
-#pragma unroll
-    for (int i = 0; i < o; ++i)
-      v[i] = (up ? v[i + o] : v[i]) + __shfl_xor_sync(kFull, up ? v[i] : v[i + o], o);
-  }
-  return v[0];
-}
-
-// Barrier of the warps that share one sample.  With more than one warp per
-// sample a CTA holds exactly one sample group, so a fixed barrier id is used
-// (a run-time id would make the compiler reserve all 16 barriers per CTA).
-__device__ __forceinline__ void group_barrier(int nthreads) {
-  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
-}
-
-// One sample per group of WPS warps (32 WPS lanes); a CTA holds blockDim.x /
-// (32 WPS) groups (one group when WPS > 1).  Timestep t = s * 32 WPS +
-// (warp-in-group) * 32 + lane for slot s; lanes with t >= m compute on the
-// last timestep's data and contribute nothing.
-template <int SLOTS, int WPS>
-struct RegCap {
-  // registers per thread: one timestep slot per 32 lanes needs about 70, the
-  // rest is per-sample state; capped so that enough warps stay resident
-  static constexpr int value =
-      SLOTS * WPS >= 8 ? 255 : (SLOTS >= 4 ? 224 : (SLOTS == 2 ? 144 : (WPS == 4 ? 76 : 96)));
-};
-
-template <int NC, int SLOTS, int WPS>
-__global__ void __launch_bounds__(256) __maxnreg__((RegCap<SLOTS, WPS>::value))
-fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ layout,
-             const double* __restrict__ obs, const Tile* __restrict__ tiles,
-             const double* __restrict__ pin, Consts c, Params prm,
-             double* __restrict__ xi_out, double* __restrict__ r_out,
-             double* __restrict__ cu_out) {
-  constexpr int NCP = basis32_ncp(NC);
-  constexpr int NP = NCP / 2;              // coefficient pairs
-  constexpr int ST = basis32_stride(NC);
-  constexpr int LPS = 32 * WPS;
-  constexpr bool kPairSlots = SLOTS % 2 == 0;
-  extern __shared__ __align__(16) float smem[];
-  const int m = prm.m;
-  const int ns = prm.n_seg;
-  const Tile tile = tiles[blockIdx.x];
-  const DevScene& sc = scenes[tile.scene];
-  const int N = sc.n_obs;
-  const int warps = blockDim.x >> 5;
-  const int groups = warps / WPS;
-
-  float* sW = smem;                                          // [m][ST]
-  float4* sObs = reinterpret_cast<float4*>(smem + m * ST);   // [N][4]
-  float* sBuf = reinterpret_cast<float*>(sObs + 4 * N);      // [warps][64]
-  constexpr int RS = 32 * WPS + 4;                           // row stride of the reduction table
-  // floats per sample group: one warp transposes through a [2n][RS] table; with
-  // several warps each warp reduces with shuffles and the warps add their
-  // [32] results through a double-buffered [2][WPS][32] table
-  constexpr int RED = WPS > 1 ? 2 * WPS * 32 : 2 * NC * RS;
-  float* sRedAll = sBuf + 64 * warps;                        // [groups][RED]
-  float* sScore = sRedAll + groups * RED;                    // [groups][WPS][2]
-  float* sM = sScore + groups * WPS * 2;                     // [2][NC][NC] rows of M
-  float* sRef = sM + 2 * NC * NC;                            // [warps][6][SLOTS][32]
-  float* sThr = sRef + warps * 6 * SLOTS * 32;               // [warps][N] obstacle re-test levels
-
-  {
-    const float4* src = reinterpret_cast<const float4*>(c.basis32);
-    float4* dst = reinterpret_cast<float4*>(sW);
-    for (int i = threadIdx.x; i < m * ST / 4; i += blockDim.x) dst[i] = src[i];
-  }
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    // scaled trajectory: (x - x_o(t)) / a = x / a + (-x0/a) + (-vx dt / a) t,
-    // constants duplicated for packed pairs of timesteps
-    const double* o = obs + size_t(sc.obs_off + i) * 6;
-    const double ia = 1.0 / o[4], ib = 1.0 / o[5];
-    const float nx0 = float(-o[0] * ia), nvx = float(-o[2] * ia * prm.dt);
-    const float ny0 = float(-o[1] * ib), nvy = float(-o[3] * ib * prm.dt);
-    sObs[4 * i + 0] = make_float4(nx0, nx0, nvx, nvx);
-    sObs[4 * i + 1] = make_float4(ny0, ny0, nvy, nvy);
-    sObs[4 * i + 2] = make_float4(float(ia), float(ia), float(ib), float(ib));
-    sObs[4 * i + 3] = make_float4(float(o[4]), float(o[5]), 0.f, 0.f);
-  }
-  for (int e = threadIdx.x; e < 2 * NC * NC; e += blockDim.x) {
-    const int ax_ = e / (NC * NC), k_ = (e / NC) % NC, i_ = e % NC;
-    sM[e] = c.pj32[size_t((N * 2 + ax_) * NC + k_) * (2 * NC + 3) + i_];
-  }
-  __syncthreads();
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int grp = warp / WPS, wig = warp % WPS;
-  if (grp >= tile.count) return;
-  const int gl = wig * 32 + lane;                           // lane within the sample group
-  const int j = layout[tile.scene].off + tile.first + grp;  // global sample index
-  float* xbuf = sBuf + warp * 64;      // slot layout: xi_bar, then delta (per warp copy)
-  float* vbuf = xbuf + 32;             // slot layout: lambda + rho w - delta
-  float* sRed = sRedAll + grp * RED;
-  float* ref = sRef + warp * 6 * SLOTS * 32 + lane;   // ref[(q * SLOTS + s) * 32]
-  // Obstacle i can hold a point of this warp's timesteps only once the
-  // trajectory has moved by (scaled) thr[i] - moved - 1 since it was last
-  // tested: positions are convex combinations of the coefficients (Bernstein
-  // rows are nonnegative and sum to one), so no point moves further than the
-  // largest coefficient change.  Skipped obstacles contribute exactly zero.
-  float* thr = sThr + warp * N;
-  for (int i = lane; i < N; i += 32) thr[i] = -3.0e38f;
-  float ia_max = 0.f, ib_max = 0.f;
-  for (int i = lane; i < N; i += 32) {
-    ia_max = fmaxf(ia_max, sObs[4 * i + 2].x);
-    ib_max = fmaxf(ib_max, sObs[4 * i + 2].z);
-  }
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) {
-    ia_max = fmaxf(ia_max, __shfl_xor_sync(kFull, ia_max, o));
-    ib_max = fmaxf(ib_max, __shfl_xor_sync(kFull, ib_max, o));
-  }
-  float moved = 0.f;   // bound on the scaled movement of any point since iteration 0
-
-  // ---- per-lane coefficient slot: Step 1 and the row of M
-  const int axis = lane >> 4, kk = lane & 15;
-  const bool valid = kk < NC;
-  const float* Mrow = sM + (axis * NC + (valid ? kk : 0)) * NC;
-  float xb_l = 0.f;     // xi_bar of this lane's slot
-  if (valid) {
-    // xi_bar = Gs p_axis + Hs b_axis (x uses the v_d entries, y the y_d entries),
-    // applied in float64: at high polynomial degree the Step-1 map has entries
-    // of order 1e3 whose products cancel to the coefficients' size
-    const double* s1 = c.s1_64 + size_t(axis * NC + kk) * (ns + 3);
-    const double* pj = pin + size_t(j) * (2 * ns);
-    double xb = 0.0;
-    for (int q = 0; q < ns; ++q) xb = fma(s1[q], pj[(axis == 0 ? ns : 0) + q], xb);
-    xb = fma(s1[ns], sc.ego[axis], xb);
-    xb = fma(s1[ns + 1], sc.ego[axis + 2], xb);
-    xb = fma(s1[ns + 2], sc.ego[axis + 4], xb);
-    xb_l = float(xb);
-  }
-  xbuf[lane] = xb_l;     // padding slots hold 0: they meet zero basis columns
-  __syncwarp();
-
-  int tcl[SLOTS];     // clamped timestep (valid row address)
-  float act[SLOTS];   // 1 for t < m, else 0
-  float tt[SLOTS];    // timestep index as float (obstacle tables hold per-step rates)
-#pragma unroll
-  for (int s = 0; s < SLOTS; ++s) {
-    const int t = s * LPS + gl;
-    tcl[s] = min(t, m - 1);
-    act[s] = t < m ? 1.f : 0.f;
-    tt[s] = float(t);
-  }
-
-  auto load_iterate = [&](float2 (&xv)[NP], float2 (&yv)[NP]) {
-#pragma unroll
-    for (int i4 = 0; i4 < NCP; i4 += 4) {
-      const float4 a = *reinterpret_cast<const float4*>(xbuf + i4);
-      const float4 b = *reinterpret_cast<const float4*>(xbuf + 16 + i4);
-      xv[i4 / 2] = f2(a.x, a.y); xv[i4 / 2 + 1] = f2(a.z, a.w);
-      yv[i4 / 2] = f2(b.x, b.y); yv[i4 / 2 + 1] = f2(b.z, b.w);
-    }
-  };
-
-  // ---- reference kinematics at xi_bar
-  {
-    float2 xv[NP], yv[NP];
-    load_iterate(xv, yv);
-#pragma unroll
-    for (int s = 0; s < SLOTS; ++s) {
-      float o[6];
-      kin<NC>(sW + tcl[s] * ST, xv, yv, o);
-#pragma unroll
-      for (int q = 0; q < 6; ++q) ref[(q * SLOTS + s) * 32] = o[q];
-    }
-  }
-  __syncwarp();
-  xbuf[lane] = 0.f;    // delta^0 = 0
-
-  const float rho = float(prm.rho);
-  const float hrho = 0.5f * rho;
-  const float v_min = float(prm.v_min), v_max = float(prm.v_max), a_max = float(prm.a_max);
-  const float kmax = float(prm.kappa_max), inv_kmax = float(1.0 / prm.kappa_max);
-  const float c_max = float(prm.c_max);
-  const float kr = float(fabs(sc.kappa_road));
-  const float y_lb = float(sc.y_lb), y_ub = float(sc.y_ub);
-
-  float da[SLOTS];
-#pragma unroll
-  for (int s = 0; s < SLOTS; ++s) da[s] = 0.f;
-  // road profile: curvature at the previous iterate (Eq. clip_d_v), lane limits
-  // at the current one; without a profile both are the scene's constants
-  const bool road = sc.n_road > 0;
-  float xprev[SLOTS];
-
-  float lam = 0.f, dl = 0.f;     // lambda and delta of this lane's slot
-  float r_acc = 0.f, cu_acc = 0.f;
-
-  for (int it = 0;; ++it) {
-    __syncwarp();
-    float2 xv[NP], yv[NP];
-    load_iterate(xv, yv);
-
-    // ---- A: kinematics at the lane's timesteps
-    float px[SLOTS], py[SLOTS], vx[SLOTS], vy[SLOTS], ax[SLOTS], ay[SLOTS];
-#pragma unroll
-    for (int s = 0; s < SLOTS; ++s) {
-      float o[6], r6[6];
-      kin<NC>(sW + tcl[s] * ST, xv, yv, o);
-#pragma unroll
-      for (int q = 0; q < 6; ++q) r6[q] = ref[(q * SLOTS + s) * 32];
-      px[s] = r6[0] + o[0]; py[s] = r6[1] + o[1];
-      vx[s] = r6[2] + o[2]; vy[s] = r6[3] + o[3];
-      ax[s] = r6[4] + o[4]; ay[s] = r6[5] + o[5];
-    }
-
-    if (it == prm.K) {
-      // ---- scoring of xi^K (Alg. 1 line 9 and the Sec. V-A cost)
-      float coll[SLOTS];
-#pragma unroll
-      for (int s = 0; s < SLOTS; ++s) coll[s] = 0.f;
-#pragma unroll 1
-      for (int i = 0; i < N; ++i) {
-        const float4 q0 = sObs[4 * i], q1 = sObs[4 * i + 1], q2 = sObs[4 * i + 2];
-#pragma unroll
-        for (int s = 0; s < SLOTS; ++s) {
-          const float sx = fmaf(px[s], q2.x, fmaf(q0.z, tt[s], q0.x));
-          const float sy = fmaf(py[s], q2.z, fmaf(q1.z, tt[s], q1.x));
-          coll[s] += fmaxf(0.f, 1.f - fmaf(sx, sx, sy * sy));
-        }
-      }
-#pragma unroll
-      for (int s = 0; s < SLOTS; ++s) {
-        const float sp = fast_sqrt(fmaf(vx[s], vx[s], vy[s] * vy[s]));
-        const float am = fast_sqrt(fmaf(ax[s], ax[s], ay[s] * ay[s]));
-        const float kap = sp > 0.f ? __fdividef(ay[s] * vx[s] - ax[s] * vy[s], sp * sp * sp) : 0.f;
-        float kro = kr, ylo = y_lb, yup = y_ub;
-        if (road) {
-          road_eval<float>(sc, px[s], &kro, &ylo, &yup);
-          kro = fabsf(kro);
-        }
-        const float rt = coll[s] + fmaxf(0.f, sp - v_max) + fmaxf(0.f, am - a_max) +
-                         fmaxf(0.f, fabsf(kap) - kmax) + fmaxf(0.f, vx[s] * vx[s] * kro - c_max) +
-                         fmaxf(0.f, py[s] - yup) + fmaxf(0.f, ylo - py[s]);
-        const float dv = sp - v_max;
-        r_acc = fmaf(act[s], rt, r_acc);
-        cu_acc = fmaf(act[s] * dv, dv, cu_acc);
-      }
-      break;
-    }
-
-    // ---- B: obstacle projection, accumulated residual sum_i (h_o,i - p).
-    // A branch-free pass marks, per slot, the obstacles whose ellipse holds the
-    // point (d < 1); only those get the correction (x - x_o, y - y_o)(1/d - 1).
-    float ex[SLOTS], ey[SLOTS];
-#pragma unroll
-    for (int s = 0; s < SLOTS; ++s) { ex[s] = 0.f; ey[s] = 0.f; }
-    for (int i0 = 0; i0 < N; i0 += 32) {
-      const int nc = min(32, N - i0);
-      unsigned ins[SLOTS];
-#pragma unroll
-      for (int s = 0; s < SLOTS; ++s) ins[s] = 0u;
-      // obstacles that may be within reach (warp-uniform mask)
-      unsigned near = __ballot_sync(kFull, lane < nc && thr[i0 + lane] - moved <= 1.001f);
-      while (near) {
-        const int ii = __ffs(near) - 1;
-        near &= near - 1u;
-        const float4 q0 = sObs[4 * (i0 + ii)], q1 = sObs[4 * (i0 + ii) + 1];
-        const float4 q2 = sObs[4 * (i0 + ii) + 2];
-        float dmin = 3.0e38f;
-        if constexpr (kPairSlots) {
-#pragma unroll
-          for (int s = 0; s < SLOTS; s += 2) {
-            const float2 tp = f2(tt[s], tt[s + 1]);
-            const float2 sx = fma2(f2(px[s], px[s + 1]), f2(q2.x, q2.y),
-                                   fma2(f2(q0.z, q0.w), tp, f2(q0.x, q0.y)));
-            const float2 sy = fma2(f2(py[s], py[s + 1]), f2(q2.z, q2.w),
-                                   fma2(f2(q1.z, q1.w), tp, f2(q1.x, q1.y)));
-            const float2 d2 = fma2(sx, sx, mul2(sy, sy));
-            ins[s] |= (d2.x < 1.f ? 1u : 0u) << ii;
-            ins[s + 1] |= (d2.y < 1.f ? 1u : 0u) << ii;
-            dmin = fminf(dmin, fminf(act[s] > 0.f ? d2.x : 3.0e38f, act[s + 1] > 0.f ? d2.y : 3.0e38f));
-          }
-        } else {
-#pragma unroll
-          for (int s = 0; s < SLOTS; ++s) {
-            const float sx = fmaf(px[s], q2.x, fmaf(q0.z, tt[s], q0.x));
-            const float sy = fmaf(py[s], q2.z, fmaf(q1.z, tt[s], q1.x));
-            const float d2 = fmaf(sx, sx, sy * sy);
-            ins[s] |= (d2 < 1.f ? 1u : 0u) << ii;
-            dmin = fminf(dmin, act[s] > 0.f ? d2 : 3.0e38f);
-          }
-        }
-        // warp minimum of a nonnegative float: integer order of its bits
-        dmin = __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(dmin)));
-        if (lane == 0) thr[i0 + ii] = fast_sqrt(dmin) + moved;
-      }
-      unsigned any = 0u;
-#pragma unroll
-      for (int s = 0; s < SLOTS; ++s) {
-        ins[s] = act[s] > 0.f ? ins[s] : 0u;
-        any |= ins[s];
-      }
-      unsigned uni = __reduce_or_sync(kFull, any);
-      while (uni) {
-        const int ii = __ffs(uni) - 1;
-        uni &= uni - 1u;
-        const float4 q0 = sObs[4 * (i0 + ii)], q1 = sObs[4 * (i0 + ii) + 1];
-        const float4 q2 = sObs[4 * (i0 + ii) + 2], q3 = sObs[4 * (i0 + ii) + 3];
-#pragma unroll
-        for (int s = 0; s < SLOTS; ++s) {
-          if ((ins[s] >> ii) & 1u) {
-            const float sx = fmaf(px[s], q2.x, fmaf(q0.z, tt[s], q0.x));
-            const float sy = fmaf(py[s], q2.z, fmaf(q1.z, tt[s], q1.x));
-            const float d2 = fmaf(sx, sx, sy * sy);
-            if (d2 > 0.f) {
-              const float g = rsqrtf(d2) - 1.f;
-              ex[s] = fmaf(g * q3.x, sx, ex[s]);
-              ey[s] = fmaf(g * q3.y, sy, ey[s]);
-            } else {
-              ex[s] += q3.x;     // atan2(0, 0) = 0: h = (x_o + a, y_o)
-            }
-          }
-        }
-      }
-    }
-
-    // ---- C: velocity / acceleration / lane rows and the transposed contraction
-    float2 wx[NP], wy[NP];
-#pragma unroll
-    for (int k = 0; k < NP; ++k) { wx[k] = f2(0.f, 0.f); wy[k] = f2(0.f, 0.f); }
-#pragma unroll
-    for (int s = 0; s < SLOTS; ++s) {
-      const float v2 = fmaf(vx[s], vx[s], vy[s] * vy[s]);
-      const bool vp = v2 > 0.f;
-      const float rv = rsqrtf(v2);
-      const float cv = vp ? vx[s] * rv : 1.f, sv = vp ? vy[s] * rv : 0.f, sp = vp ? v2 * rv : 0.f;
-      const float a2 = fmaf(ax[s], ax[s], ay[s] * ay[s]);
-      const bool ap = a2 > 0.f;
-      const float ra = rsqrtf(a2);
-      const float ca = ap ? ax[s] * ra : 1.f, sa = ap ? ay[s] * ra : 0.f, am = ap ? a2 * ra : 0.f;
-      const float S = fabsf(sa * cv - ca * sv);               // |sin(alpha_a - alpha_v)|
-      const float dap = (it == 0) ? fminf(am, a_max) : da[s];
-      const float vmin_b = fmaxf(v_min, fast_sqrt(dap * S * inv_kmax));
-      float vmax_b = v_max;
-      float krs = kr, ylbs = y_lb, yubs = y_ub;
-      if (road) {
-        float unused;
-        road_eval<float>(sc, it == 0 ? px[s] : xprev[s], &krs, &unused, &unused);
-        krs = fabsf(krs);
-        road_eval<float>(sc, px[s], &unused, &ylbs, &yubs);
-        xprev[s] = px[s];
-      }
-      if (krs > 0.f) {
-        const float tc = krs * cv * cv;
-        if (tc > 0.f) vmax_b = fminf(v_max, fast_sqrt(__fdividef(c_max, tc)));
-      }
-      const float dv = fminf(fmaxf(sp, vmin_b), vmax_b);
-      const float kd = dv * dv * kmax;
-      const float amax_b = (S * a_max <= kd) ? a_max : __fdividef(kd, S);
-      const float dan = fminf(am, amax_b);
-      da[s] = dan;
-      const float A = act[s];
-      const float evx = A * fmaf(dv, cv, -vx[s]), evy = A * fmaf(dv, sv, -vy[s]);
-      const float eax = A * fmaf(dan, ca, -ax[s]), eay = A * fmaf(dan, sa, -ay[s]);
-      const float ely = fminf(fmaxf(py[s], ylbs), yubs) - py[s];
-      const float exs = A * ex[s];
-      const float eoy = A * (ey[s] + ely);
-      const float* row = sW + tcl[s] * ST;
-      const float2 ex_[3] = {f2(exs, exs), f2(evx, evx), f2(eax, eax)};
-      const float2 ey_[3] = {f2(eoy, eoy), f2(evy, evy), f2(eay, eay)};
-#pragma unroll
-      for (int mat = 0; mat < 3; ++mat) {
-#pragma unroll
-        for (int k4 = 0; k4 < NCP; k4 += 4) {
-          const float4 w = *reinterpret_cast<const float4*>(row + mat * NCP + k4);
-          const float2 w01 = f2(w.x, w.y), w23 = f2(w.z, w.w);
-          wx[k4 / 2] = fma2(w01, ex_[mat], wx[k4 / 2]);
-          wy[k4 / 2] = fma2(w01, ey_[mat], wy[k4 / 2]);
-          wx[k4 / 2 + 1] = fma2(w23, ex_[mat], wx[k4 / 2 + 1]);
-          wy[k4 / 2 + 1] = fma2(w23, ey_[mat], wy[k4 / 2 + 1]);
-        }
-      }
-    }
-
-    // ---- D: reduce over the sample's lanes through a shared-memory transpose,
-    // multipliers, xi-step in increment form
-    float wl;
-    if constexpr (WPS > 1) {
-      const float part = warp_reduce_slots<NC, NP>(wx, wy, lane);
-      float* rt = sRed + (it & 1) * WPS * 32;
-      rt[wig * 32 + lane] = part;
-      group_barrier(LPS);
-      wl = 0.f;
-#pragma unroll
-      for (int w = 0; w < WPS; ++w) wl += rt[w * 32 + lane];
-    } else {
-      float* rt = sRed;
-#pragma unroll
-      for (int k = 0; k < NC; ++k) {
-        rt[k * RS + gl] = (k & 1) ? wx[k / 2].y : wx[k / 2].x;
-        rt[(NC + k) * RS + gl] = (k & 1) ? wy[k / 2].y : wy[k / 2].x;
-      }
-      __syncwarp();
-      wl = 0.f;
-      if (valid) {
-        const float4* rrow = reinterpret_cast<const float4*>(rt + (axis * NC + kk) * RS);
-        float4 a = rrow[0];
-#pragma unroll
-        for (int c4 = 1; c4 < 8 * WPS; ++c4) {
-          const float4 b = rrow[c4];
-          a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
-        }
-        wl = (a.x + a.y) + (a.z + a.w);
-      }
-    }
-    if (valid) {
-      if (it > 0) lam = fmaf(hrho, wl, lam);
-      vbuf[lane] = fmaf(rho, wl, lam) - dl;
-    }
-    __syncwarp();
-    float acc_step = 0.f;
-    if (valid) {
-      const float* vb = vbuf + axis * 16;
-      float acc0 = 0.f, acc1 = 0.f;
-#pragma unroll
-      for (int i = 0; i < NC; i += 2) {
-        acc0 = fmaf(Mrow[i], vb[i], acc0);
-        if (i + 1 < NC) acc1 = fmaf(Mrow[i + 1], vb[i + 1], acc1);
-      }
-      acc_step = acc0 + acc1;
-      dl += acc_step;
-      xbuf[lane] = dl;
-    }
-    {
-      // scaled bound on how far any point moves in this step
-      const float mv = valid ? fabsf(acc_step) * (axis ? ib_max : ia_max) : 0.f;
-      moved += 1.41422f * __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(mv)));
-    }
-  }
-
-  // ---- outputs
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) {
-    r_acc += __shfl_xor_sync(kFull, r_acc, o);
-    cu_acc += __shfl_xor_sync(kFull, cu_acc, o);
-  }
-  if constexpr (WPS > 1) {
-    float* sc2 = sScore + grp * WPS * 2;
-    if (lane == 0) { sc2[2 * wig] = r_acc; sc2[2 * wig + 1] = cu_acc; }
-    group_barrier(LPS);
-    r_acc = 0.f;
-    cu_acc = 0.f;
-#pragma unroll
-    for (int w = 0; w < WPS; ++w) { r_acc += sc2[2 * w]; cu_acc += sc2[2 * w + 1]; }
-  }
-  if (wig == 0) {
-    if (lane == 0) {
-      r_out[j] = double(r_acc);
-      cu_out[j] = double(cu_acc);
-    }
-    if (xi_out != nullptr && valid)
-      xi_out[size_t(j) * 2 * NC + axis * NC + kk] = double(xb_l) + double(dl);
-  }
-}
-
-template <int NC, int SLOTS, int WPS>
-size_t smem_bytes(const Params& prm, int spc) {
-  const int warps = spc * WPS;
-  const int red = WPS > 1 ? 2 * WPS * 32 : 2 * NC * (32 * WPS + 4);
-  size_t f = size_t(prm.m) * basis32_stride(NC) + 16 * prm.max_obs + 64 * warps + spc * red +
-             spc * WPS * 2 + 2 * NC * NC + size_t(6) * SLOTS * 32 * warps + size_t(warps) * prm.max_obs;
-  return f * sizeof(float);
-}
-
-template <int NC, int SLOTS, int WPS>
-cudaError_t launch_t(const DevScene* scenes, const Layout* layout, const double* obs,
-                     const Tile* tiles, int n_tiles, int spc, const double* p, const Consts& c,
-                     const Params& prm, double* xi, double* r, double* cu, cudaStream_t s) {
-  fused_kernel<NC, SLOTS, WPS><<<n_tiles, spc * WPS * 32, smem_bytes<NC, SLOTS, WPS>(prm, spc), s>>>(
-      scenes, layout, obs, tiles, p, c, prm, xi, r, cu);
-  return cudaGetLastError();
-}
-
-template <int NC, int SLOTS, int WPS>
-void set_attr() {
-  cudaFuncSetAttribute(fused_kernel<NC, SLOTS, WPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       200 * 1024);
-  // every CTA stages the basis: ask for the largest shared-memory carveout so
-  // that occupancy is bounded by registers, not by the L1 / shared split
-  cudaFuncSetAttribute(fused_kernel<NC, SLOTS, WPS>,
-                       cudaFuncAttributePreferredSharedMemoryCarveout,
-                       int(cudaSharedmemCarveoutMaxShared));
-}
-
-template <int NC>
-void set_attr_nc() {
-  set_attr<NC, 4, 1>(); set_attr<NC, 8, 1>();
-  set_attr<NC, 2, 2>(); set_attr<NC, 4, 2>();
-  set_attr<NC, 1, 4>(); set_attr<NC, 2, 4>();
-}
-
-template <int NC>
-cudaError_t launch_nc(int wps, const DevScene* scenes, const Layout* layout, const double* obs,
-                      const Tile* tiles, int n_tiles, int spc, const double* p, const Consts& c,
-                      const Params& prm, double* xi, double* r, double* cu, cudaStream_t s) {
-  const int m = prm.m;
-#define PLAN_L(SL, W) \
-  launch_t<NC, SL, W>(scenes, layout, obs, tiles, n_tiles, spc, p, c, prm, xi, r, cu, s)
-  if (wps == 1) return m <= 128 ? PLAN_L(4, 1) : PLAN_L(8, 1);
-  if (wps == 2) return m <= 128 ? PLAN_L(2, 2) : PLAN_L(4, 2);
-  if (wps == 4) return m <= 128 ? PLAN_L(1, 4) : PLAN_L(2, 4);
-#undef PLAN_L
-  return cudaErrorInvalidValue;
-}
-
-}  // namespace
 
 void fused_setup() {
-  set_attr_nc<8>();
-  set_attr_nc<11>();
-  set_attr_nc<16>();
+  setup_road<false>();
+  fused_setup_road();
 }
 
 bool fused_supported(int n, int m) {
@@ -615,13 +22,13 @@ bool fused_shape_ok(int wps, int spc) {
 cudaError_t launch_fused_f32(const DevScene* scenes, const Layout* layout, const double* obs,
                              const Tile* tiles, int n_tiles, int wps, int spc, const double* p,
                              const Consts& c, const Params& prm, double* xi, double* r,
-                             double* cu, cudaStream_t s) {
+                             double* cu, bool road, cudaStream_t s) {
   if (n_tiles == 0) return cudaSuccess;
   if (!fused_shape_ok(wps, spc)) return cudaErrorInvalidValue;
-  if (prm.n == 8) return launch_nc<8>(wps, scenes, layout, obs, tiles, n_tiles, spc, p, c, prm, xi, r, cu, s);
-  if (prm.n == 11) return launch_nc<11>(wps, scenes, layout, obs, tiles, n_tiles, spc, p, c, prm, xi, r, cu, s);
-  if (prm.n == 16) return launch_nc<16>(wps, scenes, layout, obs, tiles, n_tiles, spc, p, c, prm, xi, r, cu, s);
-  return cudaErrorInvalidValue;
+  if (road)
+    return launch_fused_f32_road(scenes, layout, obs, tiles, n_tiles, wps, spc, p, c, prm, xi, r,
+                                 cu, s);
+  return launch_road<false>(scenes, layout, obs, tiles, n_tiles, wps, spc, p, c, prm, xi, r, cu, s);
 }
 
 }  // namespace plan

@@ -29,10 +29,12 @@ struct SceneSet {
   Layout* layout = nullptr;
   Tile* tiles = nullptr;
   int* sample_scene = nullptr;
+  bool road = false;       // some uploaded scene has a road profile
 };
 
 struct GraphEntry {
   std::vector<int> B;
+  bool road = false;       // kernel variant captured (road profile or not)
   SceneSet set;            // own layout / tiles / sample_scene (scenes+obs shared)
   cudaGraphExec_t exec = nullptr;
   int total_B = 0, max_B = 0;
@@ -276,7 +278,9 @@ int upload(plan_ctx* ctx, SceneSet& set, const plan_scene* scenes, int S, const 
   std::vector<DevScene> ds;
   std::vector<double> ob;
   if (scenes) {
+    set.road = false;
     for (int i = 0; i < S; ++i) {
+      set.road = set.road || scenes[i].n_road > 0;
       ds.push_back(to_dev(ctx, scenes[i], int(ob.size() / 6)));
       for (int k = 0; k < scenes[i].n_obs; ++k) {
         const plan_obstacle& o = scenes[i].obs[k];
@@ -320,7 +324,7 @@ cudaError_t run_solve(plan_ctx* ctx, const SceneSet& set, const SceneSet& lay, i
   if (ctx->cfg.prec == PLAN_PREC_FP32) {
     const Shape sh = pick_shape(ctx, total_B);
     return launch_fused_f32(set.scenes, lay.layout, set.obs, lay.tiles, n_tiles, sh.wps, sh.spc,
-                            p, ctx->c, ctx->prm, xi, r, cu, s);
+                            p, ctx->c, ctx->prm, xi, r, cu, set.road, s);
   }
   if (ctx->cfg.prec >= PLAN_PREC_TF32)
     return launch_tc(ctx->cfg.prec, set.scenes, lay.layout, set.obs, lay.tiles, n_tiles, p, ctx->c,
@@ -681,14 +685,16 @@ int plan_step_resident(plan_ctx* ctx, const int* B, int S, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   GraphEntry* g = nullptr;
   for (auto& e : ctx->graphs)
-    if (e.B == Bv) g = &e;
+    if (e.B == Bv && e.road == ctx->res.road) g = &e;
   if (!g) {
     GraphEntry e;
     e.B = Bv;
+    e.road = ctx->res.road;
     e.total_B = int(total);
     e.max_B = max_B;
     e.set.scenes = ctx->res.scenes;
     e.set.obs = ctx->res.obs;
+    e.set.road = ctx->res.road;
     TRY(dalloc(ctx, &e.set.layout, S));
     TRY(dalloc(ctx, &e.set.tiles, size_t(total) + S));
     TRY(dalloc(ctx, &e.set.sample_scene, size_t(total)));
