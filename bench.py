@@ -324,6 +324,8 @@ def gpu_arm(args):
     peak = sms * FP32_LANES_PER_SM * 2 * peak_clock * 1e6 / 1e12
     achieved = flops / (kern_ms * 1e-3) / 1e12
     pl.close()
+    from paper_2212_02224_gb300 import binding
+    probe = binding.plan_probe_alu()
 
     # ---- precision modes: one lower-level solve of the same B = 1000 samples per
     # mode, timed alone, and its error against the plain FP64 GPU path
@@ -381,7 +383,10 @@ def gpu_arm(args):
                                    f"{shape[1]} sample(s)/CTA; one lower-level solve, B=1000, K=100)",
                          "kernel_ms": kern_ms,
                          "peak_basis": f"FP32 FMA pipe: {sms} SMs x 128 lanes x 2 flop x "
-                                       f"{peak_clock:.0f} MHz"},
+                                       f"{peak_clock:.0f} MHz",
+                         "probe": {k: v for k, v in probe.items()},
+                         "probe_basis": "plan_probe_alu: independent FFMA / FFMA2 / DFMA / "
+                                        "MUFU rsqrt chains, 8 CTAs x 256 threads per SM"},
             "cpu_baseline": cpu,
             "clocks": clocks,
             "precision": precision,

@@ -375,6 +375,17 @@ int plan_qp_forward(plan_ctx* ctx, const double* p, const double* b0, int B, dou
 int plan_qp_backward(plan_ctx* ctx, const double* g, int B, double* grad_p, double* grad_b0,
                      void* stream);
 
+/* ------------------------------------------------ arithmetic ceilings */
+
+/* Measured throughput of the arithmetic the fused kernel is bound by, on the
+ * current device: out[0] float32 FMA TFLOP/s, out[1] packed float32x2 FMA
+ * TFLOP/s, out[2] float64 FMA TFLOP/s, out[3] MUFU reciprocal square roots
+ * (10^12 per s), out[4] the SM count.  Independent FMA chains over 8 CTAs of
+ * 256 threads per SM, best of three timed launches.  Synchronous on `stream`;
+ * allocates a small sink buffer.  The paper has no counterpart: this measures
+ * the roofline's denominators.  Errors: EINVAL (NULL out), ECUDA. */
+int plan_probe_alu(double* out, void* stream);
+
 /* ------------------------------------------------ allocation-free lower level */
 
 /* The float64 lower-level solve of plan_solve (same kernels, same results) for

@@ -87,7 +87,7 @@ EXPORTS = ("plan_init", "plan_destroy", "plan_status_str", "plan_last_error", "p
            "plan_update_distribution", "plan_sample", "plan_set_tuning", "plan_autotune",
            "plan_solve_fp64_noalloc", "plan_advance", "plan_server_create", "plan_server_destroy",
            "plan_submit", "plan_poll", "plan_end_episode", "plan_server_info",
-           "plan_qp_forward", "plan_qp_backward")
+           "plan_qp_forward", "plan_qp_backward", "plan_probe_alu")
 
 _lib = None
 
@@ -138,6 +138,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "plan_server_info": (I, [V, P(PlanServerStats)]),
         "plan_qp_forward": (I, [V, V, V, I, V, V]),
         "plan_qp_backward": (I, [V, V, I, V, V, V]),
+        "plan_probe_alu": (I, [P(D), V]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -313,6 +314,14 @@ def plan_qp_forward(ctx, p_ptr: int, b0_ptr: int, B: int, xi_ptr: int, stream: i
 
 def plan_qp_backward(ctx, g_ptr: int, B: int, grad_p_ptr: int, grad_b0_ptr, stream: int = 0):
     check(load().plan_qp_backward(ctx, g_ptr, int(B), grad_p_ptr, grad_b0_ptr, stream), ctx)
+
+
+def plan_probe_alu(stream: int = 0) -> dict:
+    """Measured arithmetic ceilings of the current device (see include/plan.h)."""
+    out = (ctypes.c_double * 5)()
+    check(load().plan_probe_alu(out, stream), None)
+    return dict(fp32_tflops=out[0], fp32x2_tflops=out[1], fp64_tflops=out[2],
+                rsqrt_tops=out[3], sms=int(out[4]))
 
 
 def plan_set_tuning(ctx, warps_per_sample: int, samples_per_cta: int):

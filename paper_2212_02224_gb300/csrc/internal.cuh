@@ -164,6 +164,9 @@ cudaError_t launch_tc(int prec, const DevScene* scenes, const Layout* layout, co
                       const Params& prm, double* xi, double* r, double* cu, int* err,
                       cudaStream_t s);
 
+// Arithmetic throughput probe (k_peaks.cu): out[0..4] as plan_probe_alu.
+int probe_alu(double* out, cudaStream_t s);
+
 // Differentiable Step-1 layer (k_qp.cu).
 cudaError_t launch_qp_forward(const Consts& c, const double* p, const double* b0, int B,
                               double* xi, cudaStream_t s);

@@ -769,6 +769,19 @@ int plan_update_distribution(plan_ctx* ctx, const double* p_elite, const double*
   return PLAN_OK;
 }
 
+int plan_probe_alu(double* out, void* stream) {
+  if (!out) {
+    set_unbound_error("out is NULL");
+    return PLAN_EINVAL;
+  }
+  if (probe_alu(out, static_cast<cudaStream_t>(stream)) != 0) {
+    set_unbound_error("probe launch failed");
+    cudaGetLastError();
+    return PLAN_ECUDA;
+  }
+  return PLAN_OK;
+}
+
 int plan_qp_forward(plan_ctx* ctx, const double* p, const double* b0, int B, double* xi,
                     void* stream) {
   if (!ctx) return PLAN_EINVAL;

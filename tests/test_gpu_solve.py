@@ -170,3 +170,14 @@ def test_autotune_returns_a_valid_shape(tmp_path, monkeypatch):
     with pytest.raises(binding.PlanError):
         pl.set_tuning(3, 1)
     pl.close()
+
+
+def test_arithmetic_probe():
+    """The roofline's denominators measured on the device: positive, the SM
+    count of the device, FP32 FMA no faster than SMs x 128 lanes x 2 flop at
+    the maximum SM clock (a little slack for clock reporting)."""
+    out = binding.plan_probe_alu()
+    props = torch.cuda.get_device_properties(0)
+    assert out["sms"] == props.multi_processor_count
+    assert out["fp32_tflops"] > 0 and out["fp64_tflops"] > 0 and out["rsqrt_tops"] > 0
+    assert out["fp32_tflops"] <= 1.1 * out["sms"] * 128 * 2 * 2.1e9 / 1e12
