@@ -299,10 +299,12 @@ def gpu_arm(args):
             e2e_ms.append(dt_ms)
     e2e_total = ranks.max(sum(e2e_ms) / 1e3)
     e2e_value = replica_value(units, len(e2e_ms), e2e_total, world)
-    dev_scene = 96 + 48 * sc.n_obs
-    dev_cem = 1464
-    h2d = dev_scene + dev_cem
-    d2h = 2 * dev_cem
+    # plan_step copies, per cycle: up the device scene record (352 B), its
+    # obstacles (48 B each) and the sampling state (1464 B); down the final
+    # state with the best pair (1464 B) and the timeout flag (4 B)
+    dev_scene, dev_cem = 352, 1464
+    h2d = dev_scene + 48 * sc.n_obs + dev_cem
+    d2h = dev_cem + 4
 
     # ---- roofline of the fused solve kernel (timed alone on this stream)
     p = torch.tensor(sg.make_samples(303, sc, B, prm.n_seg), dtype=torch.float64, device="cuda")

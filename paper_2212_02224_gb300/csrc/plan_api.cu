@@ -615,6 +615,28 @@ int plan_set_state(plan_ctx* ctx, int slot, const plan_cem_state* st, void* stre
   return stage_release(ctx, s);
 }
 
+void cem_to_state(const plan_ctx* ctx, const DevCem& c, plan_cem_state* st) {
+  const int d = 2 * ctx->cfg.n_seg;
+  std::memset(st, 0, sizeof *st);
+  for (int a = 0; a < d; ++a) {
+    st->mu[a] = c.mu[a];
+    for (int b = 0; b < d; ++b) st->sigma[a * 8 + b] = c.sigma[a * kMaxDp + b];
+  }
+  st->seed = c.seed;
+  st->episode_step = c.step;
+  st->fresh = c.fresh;
+}
+
+void cem_to_result(const plan_ctx* ctx, const DevCem& c, plan_result* out) {
+  std::memset(out, 0, sizeof *out);
+  for (int a = 0; a < 2 * ctx->cfg.n_seg; ++a) out->p[a] = c.best_p[a];
+  for (int a = 0; a < 2 * ctx->cfg.n_coef; ++a) out->xi[a] = c.best_xi[a];
+  out->cost = c.best_cost;
+  out->resid = c.best_r;
+  out->cu = c.best_cu;
+  out->index = c.best_index;
+}
+
 int plan_get_state(plan_ctx* ctx, int slot, plan_cem_state* st, void* stream) {
   if (!ctx) return PLAN_EINVAL;
   if (!st || slot < 0 || slot >= ctx->cfg.max_scenes) return fail(ctx, PLAN_EINVAL, "bad slot/state");
@@ -630,15 +652,7 @@ int plan_get_state(plan_ctx* ctx, int slot, plan_cem_state* st, void* stream) {
   int tc_timeout = 0;
   std::memcpy(&tc_timeout, ctx->stage + sizeof c, sizeof tc_timeout);
   if (tc_timeout) return fail(ctx, PLAN_ETIMEOUT, "a tensor-core wait of the solve timed out");
-  const int d = 2 * ctx->cfg.n_seg;
-  std::memset(st, 0, sizeof *st);
-  for (int a = 0; a < d; ++a) {
-    st->mu[a] = c.mu[a];
-    for (int b = 0; b < d; ++b) st->sigma[a * 8 + b] = c.sigma[a * kMaxDp + b];
-  }
-  st->seed = c.seed;
-  st->episode_step = c.step;
-  st->fresh = c.fresh;
+  cem_to_state(ctx, c, st);
   return PLAN_OK;
 }
 
@@ -657,13 +671,7 @@ int plan_get_result(plan_ctx* ctx, int slot, plan_result* out, void* stream) {
   int tc_timeout = 0;
   std::memcpy(&tc_timeout, ctx->stage + sizeof c, sizeof tc_timeout);
   if (tc_timeout) return fail(ctx, PLAN_ETIMEOUT, "a tensor-core wait of the solve timed out");
-  std::memset(out, 0, sizeof *out);
-  for (int a = 0; a < 2 * ctx->cfg.n_seg; ++a) out->p[a] = c.best_p[a];
-  for (int a = 0; a < 2 * ctx->cfg.n_coef; ++a) out->xi[a] = c.best_xi[a];
-  out->cost = c.best_cost;
-  out->resid = c.best_r;
-  out->cu = c.best_cu;
-  out->index = c.best_index;
+  cem_to_result(ctx, c, out);
   if (!std::isfinite(c.best_cost)) return fail(ctx, PLAN_ENONFINITE, "best cost is not finite");
   return PLAN_OK;
 }
@@ -740,11 +748,51 @@ int plan_step(plan_ctx* ctx, const plan_scene* scene, plan_cem_state* st, int B,
               void* stream) {
   if (!ctx) return PLAN_EINVAL;
   if (!scene || !st || !out) return fail(ctx, PLAN_EINVAL, "scene, state and out must be non-NULL");
-  TRY(plan_upload_scenes(ctx, scene, 1, stream));
-  TRY(plan_set_state(ctx, 0, st, stream));
+  TRY(check_scene(ctx, scene, 0));
+  if (B < 1 || B > ctx->cfg.max_samples) return fail(ctx, PLAN_ECAPACITY, "B out of range");
+  DevCem c0;
+  TRY(make_cem(ctx, st, scene->n_lanes, scene->lane_width, &c0));
+  CU(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // one pinned staging buffer: scene, obstacles and state go up, the final
+  // state (with the best pair) and the timeout flag come back, one sync
+  const size_t n_obs = size_t(scene->n_obs) * 6 * sizeof(double);
+  const size_t o_obs = align_up(sizeof(DevScene)), o_cem = o_obs + align_up(n_obs);
+  const size_t o_ret = o_cem + align_up(sizeof(DevCem));
+  TRY(stage_acquire(ctx, o_ret + sizeof(DevCem) + sizeof(int)));
+  const DevScene ds = to_dev(ctx, *scene, 0);
+  std::memcpy(ctx->stage, &ds, sizeof ds);
+  double* ob = reinterpret_cast<double*>(ctx->stage + o_obs);
+  for (int k = 0; k < scene->n_obs; ++k) {
+    const plan_obstacle& o = scene->obs[k];
+    const double v[6] = {o.x0, o.y0, o.vx, o.vy, o.a, o.b};
+    std::memcpy(ob + 6 * k, v, sizeof v);
+  }
+  std::memcpy(ctx->stage + o_cem, &c0, sizeof c0);
+  CU(ctx, cudaMemcpyAsync(ctx->res.scenes, ctx->stage, sizeof ds, cudaMemcpyHostToDevice, s));
+  if (n_obs) CU(ctx, cudaMemcpyAsync(ctx->res.obs, ob, n_obs, cudaMemcpyHostToDevice, s));
+  CU(ctx, cudaMemcpyAsync(ctx->cem, ctx->stage + o_cem, sizeof c0, cudaMemcpyHostToDevice, s));
+  TRY(stage_release(ctx, s));   // a graph capture below may reuse the staging buffer
+  ctx->res.road = scene->n_road > 0;
+  ctx->res_host.assign(1, ds);
+  ctx->n_uploaded = 1;
   TRY(plan_step_resident(ctx, &B, 1, stream));
-  TRY(plan_get_result(ctx, 0, out, stream));
-  return plan_get_state(ctx, 0, st, stream);
+  // waits only for the uploads above (the cycle is already queued behind them)
+  TRY(stage_acquire(ctx, o_ret + sizeof(DevCem) + sizeof(int)));
+  CU(ctx, cudaMemcpyAsync(ctx->stage + o_ret, ctx->cem, sizeof(DevCem), cudaMemcpyDeviceToHost, s));
+  CU(ctx, cudaMemcpyAsync(ctx->stage + o_ret + sizeof(DevCem), ctx->tc_err, sizeof(int),
+                          cudaMemcpyDeviceToHost, s));
+  CU(ctx, cudaStreamSynchronize(s));
+  ctx->stage_pending = false;
+  DevCem c;
+  std::memcpy(&c, ctx->stage + o_ret, sizeof c);
+  int tc_timeout = 0;
+  std::memcpy(&tc_timeout, ctx->stage + o_ret + sizeof c, sizeof tc_timeout);
+  if (tc_timeout) return fail(ctx, PLAN_ETIMEOUT, "a tensor-core wait of the solve timed out");
+  cem_to_result(ctx, c, out);
+  cem_to_state(ctx, c, st);
+  if (!std::isfinite(c.best_cost)) return fail(ctx, PLAN_ENONFINITE, "best cost is not finite");
+  return PLAN_OK;
 }
 
 int plan_select_elites(plan_ctx* ctx, const double* resid, const double* cu, int B, int n_c, int q,
