@@ -9,6 +9,8 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libplan.so")
 
@@ -192,20 +194,20 @@ def make_scenes(scenes):
         arr[i].n_lanes = int(sc.n_lanes)
         arr[i].lane_width = float(sc.lane_width)
         arr[i].kappa_road = float(sc.kappa_road)
-        ob = list(sc.obstacles)
-        arr[i].n_obs = len(ob)
-        if ob:
-            oa = (PlanObstacle * len(ob))(*[PlanObstacle(*[float(v) for v in row]) for row in ob])
-            keep.append(oa)
-            arr[i].obs = ctypes.cast(oa, ctypes.POINTER(PlanObstacle))
+        # obstacle rows and road knots are passed straight from float64 buffers
+        # laid out like plan_obstacle / plan_road_knot
+        ob = np.ascontiguousarray(np.asarray(sc.obstacles, dtype=np.float64).reshape(-1, 6))
+        arr[i].n_obs = ob.shape[0]
+        if ob.shape[0]:
+            keep.append(ob)
+            arr[i].obs = ob.ctypes.data_as(ctypes.POINTER(PlanObstacle))
         else:
             arr[i].obs = None
-        road = [list(k) for k in getattr(sc, "road", [])]
-        arr[i].n_road = len(road)
-        if road:
-            ra = (PlanRoadKnot * len(road))(*[PlanRoadKnot(*[float(v) for v in k]) for k in road])
-            keep.append(ra)
-            arr[i].road = ctypes.cast(ra, ctypes.POINTER(PlanRoadKnot))
+        road = np.ascontiguousarray(np.asarray(getattr(sc, "road", ()), dtype=np.float64).reshape(-1, 4))
+        arr[i].n_road = road.shape[0]
+        if road.shape[0]:
+            keep.append(road)
+            arr[i].road = road.ctypes.data_as(ctypes.POINTER(PlanRoadKnot))
         else:
             arr[i].road = None
         arr[i].road_origin = float(getattr(sc, "road_origin", 0.0))
