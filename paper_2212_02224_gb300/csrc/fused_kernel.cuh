@@ -207,7 +207,13 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   // ---- per-lane coefficient slot: Step 1 and the row of M
   const int axis = lane >> 4, kk = lane & 15;
   const bool valid = kk < NC;
-  const float* Mrow = sM + (axis * NC + (valid ? kk : 0)) * NC;
+  const float* Mrow_s = sM + (axis * NC + (valid ? kk : 0)) * NC;
+  // shapes with few timestep slots keep the reference kinematics and the row of
+  // M in registers; the others read them from shared memory
+  constexpr bool kRegState = WPS == 1 && SLOTS <= 4;
+  float Mrow_r[kRegState ? NC : 1];
+#pragma unroll
+  for (int i = 0; i < (kRegState ? NC : 1); ++i) Mrow_r[i] = Mrow_s[i];
   float xb_l = 0.f;     // xi_bar of this lane's slot
   if (valid) {
     // xi_bar = Gs p_axis + Hs b_axis (x uses the v_d entries, y the y_d entries),
@@ -246,6 +252,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     }
   };
 
+  float rref[kRegState ? SLOTS : 1][6];   // reference kinematics at xi_bar (register copy)
   // ---- reference kinematics at xi_bar
   {
     float2 xv[NP], yv[NP];
@@ -255,7 +262,10 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       float o[6];
       kin<NC>(sW + tcl[s] * ST, xv, yv, o);
 #pragma unroll
-      for (int q = 0; q < 6; ++q) ref[(q * SLOTS + s) * 32] = o[q];
+      for (int q = 0; q < 6; ++q) {
+        if constexpr (kRegState) rref[s][q] = o[q];
+        else ref[(q * SLOTS + s) * 32] = o[q];
+      }
     }
   }
   __syncwarp();
@@ -292,7 +302,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       float o[6], r6[6];
       kin<NC>(sW + tcl[s] * ST, xv, yv, o);
 #pragma unroll
-      for (int q = 0; q < 6; ++q) r6[q] = ref[(q * SLOTS + s) * 32];
+      for (int q = 0; q < 6; ++q) r6[q] = kRegState ? rref[s][q] : ref[(q * SLOTS + s) * 32];
       px[s] = r6[0] + o[0]; py[s] = r6[1] + o[1];
       vx[s] = r6[2] + o[2]; vy[s] = r6[3] + o[3];
       ax[s] = r6[4] + o[4]; ay[s] = r6[5] + o[5];
@@ -509,8 +519,8 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll
       for (int i = 0; i < NC; i += 2) {
-        acc0 = fmaf(Mrow[i], vb[i], acc0);
-        if (i + 1 < NC) acc1 = fmaf(Mrow[i + 1], vb[i + 1], acc1);
+        acc0 = fmaf(kRegState ? Mrow_r[i] : Mrow_s[i], vb[i], acc0);
+        if (i + 1 < NC) acc1 = fmaf(kRegState ? Mrow_r[i + 1] : Mrow_s[i + 1], vb[i + 1], acc1);
       }
       acc_step = acc0 + acc1;
       dl += acc_step;
