@@ -215,6 +215,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
 #pragma unroll
   for (int i = 0; i < (kRegState ? NC : 1); ++i) Mrow_r[i] = Mrow_s[i];
   float xb_l = 0.f;     // xi_bar of this lane's slot
+  pdl_wait();           // p comes from the sampling kernel
   if (valid) {
     // xi_bar = Gs p_axis + Hs b_axis (x uses the v_d entries, y the y_d entries),
     // applied in float64: at high polynomial degree the Step-1 map has entries
@@ -534,6 +535,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   }
 
   // ---- outputs
+  pdl_trigger();
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) {
     r_acc += __shfl_xor_sync(kFull, r_acc, o);
@@ -571,9 +573,9 @@ template <int NC, int SLOTS, int WPS, bool ROAD>
 cudaError_t launch_t(const DevScene* scenes, const Layout* layout, const double* obs,
                      const Tile* tiles, int n_tiles, int spc, const double* p, const Consts& c,
                      const Params& prm, double* xi, double* r, double* cu, cudaStream_t s) {
-  fused_kernel<NC, SLOTS, WPS, ROAD><<<n_tiles, spc * WPS * 32, smem_bytes<NC, SLOTS, WPS>(prm, spc), s>>>(
-      scenes, layout, obs, tiles, p, c, prm, xi, r, cu);
-  return cudaGetLastError();
+  return launch_pdl(fused_kernel<NC, SLOTS, WPS, ROAD>, dim3(n_tiles), dim3(spc * WPS * 32),
+                    smem_bytes<NC, SLOTS, WPS>(prm, spc), s, scenes, layout, obs, tiles, p, c, prm,
+                    xi, r, cu);
 }
 
 template <int NC, int SLOTS, int WPS, bool ROAD>

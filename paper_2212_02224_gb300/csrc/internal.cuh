@@ -141,6 +141,33 @@ __host__ __device__ constexpr int basis32_stride(int n) {
   return ((3 * basis32_ncp(n)) / 4) % 2 == 1 ? 3 * basis32_ncp(n) : 3 * basis32_ncp(n) + 4;
 }
 
+// Programmatic dependent launch within the MPC cycle (sample -> solve ->
+// select): a kernel launched with launch_pdl may start while its predecessor
+// in the stream finishes; it must call pdl_wait() before touching anything the
+// predecessor writes or reads, and calls pdl_trigger() once its successor may
+// be scheduled (only after its own wait, or at the end of its main work, so
+// that waiting grids never hold resources an unfinished earlier grid needs).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Launchers (return the cudaError_t of the launch).
 cudaError_t build_constants(const Consts& c, const Params& p, cudaStream_t s);
 

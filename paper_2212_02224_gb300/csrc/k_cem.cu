@@ -29,6 +29,8 @@ __device__ __forceinline__ double unit_open(unsigned w) { return (double(w) + 0.
 // Alg. 1 line 4 for every scene: grid (ceil(max_B / 128), S).
 __global__ void sample_kernel(const DevScene* scenes, const Layout* layout, const DevCem* cem,
                               int l, Params prm, double* p) {
+  pdl_wait();      // the distribution comes from the previous selection kernel
+  pdl_trigger();
   const int s = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const Layout lay = layout[s];
@@ -301,6 +303,8 @@ select_update_kernel(const Layout* layout, DevCem* cem, int l, Params prm, const
                      const double* xi, const double* r, const double* cu, int* elite_out) {
   extern __shared__ __align__(16) unsigned char shraw[];
   SelShared& sh = *reinterpret_cast<SelShared*>(shraw);
+  pdl_wait();      // r, c_u, p and xi come from the solve kernel
+  pdl_trigger();
   const int s = blockIdx.x;
   const Layout lay = layout[s];
   DevCem& st = cem[s];
@@ -551,6 +555,8 @@ select_update_small_kernel(const Layout* layout, DevCem* cem, int l, Params prm,
                            const double* xi, const double* r, const double* cu, int* elite_out) {
   extern __shared__ __align__(16) unsigned char shraw[];
   SmallSel& sh = *reinterpret_cast<SmallSel*>(shraw);
+  pdl_wait();      // r, c_u, p and xi come from the solve kernel
+  pdl_trigger();
   const int s = blockIdx.x;
   const Layout lay = layout[s];
   DevCem& st = cem[s];
@@ -621,8 +627,7 @@ cudaError_t launch_sample(const DevScene* scenes, const Layout* layout, const De
                           int max_B, int l, const Params& prm, double* p, cudaStream_t s) {
   if (S == 0 || max_B == 0) return cudaSuccess;
   dim3 grid((max_B + 127) / 128, S);
-  sample_kernel<<<grid, 128, 0, s>>>(scenes, layout, cem, l, prm, p);
-  return cudaGetLastError();
+  return launch_pdl(sample_kernel, grid, dim3(128), 0, s, scenes, layout, cem, l, prm, p);
 }
 
 static bool g_sel_attr = false;
@@ -648,13 +653,11 @@ cudaError_t launch_select_update(const Layout* layout, DevCem* cem, int S, int l
   if (S == 0) return cudaSuccess;
   sel_attr();
   if (max_B <= kSmallMaxB && (prm.n_c > 0 ? prm.n_c : 3 * prm.q) <= kSmallMaxC) {
-    select_update_small_kernel<<<S, kSmallThreads, sizeof(SmallSel), s>>>(layout, cem, l, prm, p,
-                                                                          xi, r, cu, elite_out);
-    return cudaGetLastError();
+    return launch_pdl(select_update_small_kernel, dim3(S), dim3(kSmallThreads), sizeof(SmallSel),
+                      s, layout, cem, l, prm, p, xi, r, cu, elite_out);
   }
-  select_update_kernel<<<S, kSelThreads, sizeof(SelShared), s>>>(layout, cem, l, prm, p, xi, r, cu,
-                                                                 elite_out);
-  return cudaGetLastError();
+  return launch_pdl(select_update_kernel, dim3(S), dim3(kSelThreads), sizeof(SelShared), s, layout,
+                    cem, l, prm, p, xi, r, cu, elite_out);
 }
 
 cudaError_t launch_select_only(const double* r, const double* cu, int B, int n_c, int q,
