@@ -193,6 +193,26 @@ def test_velocity_acceleration_projection_invariants():
     np.testing.assert_allclose(hax[inside], xdd[inside], atol=1e-10)
 
 
+def test_vmin_bar_binds_at_low_speed():
+    """Eq. (d_reform_2) solved for d_v: with the previous acceleration d_a and
+    the angle between acceleration and velocity, a slow trajectory is sped up
+    to exactly sqrt(d_a |sin(alpha_a - alpha_v)| / kappa_max)."""
+    prm = _prm(kappa_max=0.2, v_min=0.1)
+    basis = bernstein(prm.m, prm.n_coef, prm.dt)
+    sc = _scene(0, n_lanes=4)
+    sc.ego[:] = [0.0, 5.25, 2.0, 0.0, 0.0, 1.5]          # slow, accelerating sideways
+    p = np.array([[8.75, 2.0]])
+    xi = lower.step1(p, sc, prm, basis)
+    _, _, xd, yd, xdd, ydd = lower.kinematics(xi, basis)
+    da_prev = np.full_like(xd, 4.0)
+    _, _, parts = lower.alpha_d_step(xi, sc, prm, basis, da_prev)
+    S = np.abs(np.sin(np.arctan2(ydd, xdd) - np.arctan2(yd, xd)))
+    bound = np.sqrt(da_prev * S / prm.kappa_max)
+    active = (bound > np.hypot(xd, yd) + 1e-6) & (bound < prm.v_max) & (bound > prm.v_min)
+    assert active.any()
+    np.testing.assert_allclose(parts["d_v"][active], bound[active], rtol=1e-12)
+
+
 def test_slack_nonnegative_and_exact_when_feasible():
     prm = _prm()
     basis = bernstein(prm.m, prm.n_coef, prm.dt)
