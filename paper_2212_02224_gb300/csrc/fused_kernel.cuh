@@ -1,10 +1,10 @@
 // Fused FP32 lower-level solve (kernel template, included by k_fused.cu and
 // k_fused_road.cu): Step 1 (Alg. 1 line 7 through the folded KKT
 // inverse of Eq. over_3), all K iterations of Alg. 2 and the scoring of
-// Alg. 1 line 9 / Sec. V-A, one warp per sample, all state on chip.
+// Alg. 1 line 9 / Sec. V-A, 1, 2 or 4 warps per sample, all state on chip.
 //
 // State is kept relative to the Step-1 solution: delta = xi - xi_bar.  Per
-// iteration and sample the warp
+// iteration and sample the warp(s)
 //   A. evaluates x, y and their derivatives at the lane's timesteps
 //      t = s*32 + lane as (reference at xi_bar) + W delta (Eq. param; basis
 //      rows staged in shared memory),
