@@ -5,8 +5,8 @@
 //
 // State is kept relative to the Step-1 solution: delta = xi - xi_bar.  Per
 // iteration and sample the warp(s)
-//   A. evaluates x, y and their derivatives at the lane's timesteps
-//      t = s*32 + lane as (reference at xi_bar) + W delta (Eq. param; basis
+//   A. evaluates x, y and their derivatives at the lane's timesteps (slot
+//      mapping below) as (reference at xi_bar) + W delta (Eq. param; basis
 //      rows staged in shared memory),
 //   B. projects onto every obstacle ellipse (Eqs. split_alpha_o, clip_d_o),
 //   C. projects velocity and acceleration (Eqs. clip_d_v, clip_d_a), the lane
