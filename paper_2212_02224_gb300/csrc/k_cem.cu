@@ -5,6 +5,8 @@
 // Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) with
 // key = (seed_lo, seed_hi) and counter = (j, l | c << 16, step_lo, step_hi);
 // Box-Muller turns word pairs (2q, 2q+1) into normals.
+#include <atomic>
+
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -630,9 +632,16 @@ cudaError_t launch_sample(const DevScene* scenes, const Layout* layout, const De
   return launch_pdl(sample_kernel, grid, dim3(128), 0, s, scenes, layout, cem, l, prm, p);
 }
 
-static bool g_sel_attr = false;
+// Shared-memory attributes of the selection kernels, set once per device
+// (a function attribute applies to the current device only).
+static std::atomic<bool> g_sel_attr[64];
 static void sel_attr() {
-  if (g_sel_attr) return;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    dev = 0;
+  }
+  if (g_sel_attr[dev].load()) return;
   cudaFuncSetAttribute(select_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        int(sizeof(SelShared)));
   cudaFuncSetAttribute(select_only_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -643,7 +652,7 @@ static void sel_attr() {
                        int(sizeof(SmallSel)));
   cudaFuncSetAttribute(select_only_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        int(sizeof(SmallSel)));
-  g_sel_attr = true;
+  g_sel_attr[dev].store(true);
 }
 
 cudaError_t launch_select_update(const Layout* layout, DevCem* cem, int S, int l,

@@ -651,7 +651,11 @@ int plan_get_state(plan_ctx* ctx, int slot, plan_cem_state* st, void* stream) {
   std::memcpy(&c, ctx->stage, sizeof c);
   int tc_timeout = 0;
   std::memcpy(&tc_timeout, ctx->stage + sizeof c, sizeof tc_timeout);
-  if (tc_timeout) return fail(ctx, PLAN_ETIMEOUT, "a tensor-core wait of the solve timed out");
+  if (tc_timeout) {
+    // report once: clear the flag for the next calls
+    cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), s);
+    return fail(ctx, PLAN_ETIMEOUT, "a tensor-core wait of the solve timed out");
+  }
   cem_to_state(ctx, c, st);
   return PLAN_OK;
 }
@@ -670,7 +674,11 @@ int plan_get_result(plan_ctx* ctx, int slot, plan_result* out, void* stream) {
   std::memcpy(&c, ctx->stage, sizeof c);
   int tc_timeout = 0;
   std::memcpy(&tc_timeout, ctx->stage + sizeof c, sizeof tc_timeout);
-  if (tc_timeout) return fail(ctx, PLAN_ETIMEOUT, "a tensor-core wait of the solve timed out");
+  if (tc_timeout) {
+    // report once: clear the flag for the next calls
+    cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), s);
+    return fail(ctx, PLAN_ETIMEOUT, "a tensor-core wait of the solve timed out");
+  }
   cem_to_result(ctx, c, out);
   if (!std::isfinite(c.best_cost)) return fail(ctx, PLAN_ENONFINITE, "best cost is not finite");
   return PLAN_OK;
@@ -788,7 +796,11 @@ int plan_step(plan_ctx* ctx, const plan_scene* scene, plan_cem_state* st, int B,
   std::memcpy(&c, ctx->stage + o_ret, sizeof c);
   int tc_timeout = 0;
   std::memcpy(&tc_timeout, ctx->stage + o_ret + sizeof c, sizeof tc_timeout);
-  if (tc_timeout) return fail(ctx, PLAN_ETIMEOUT, "a tensor-core wait of the solve timed out");
+  if (tc_timeout) {
+    // report once: clear the flag for the next calls
+    cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), s);
+    return fail(ctx, PLAN_ETIMEOUT, "a tensor-core wait of the solve timed out");
+  }
   cem_to_result(ctx, c, out);
   cem_to_state(ctx, c, st);
   if (!std::isfinite(c.best_cost)) return fail(ctx, PLAN_ENONFINITE, "best cost is not finite");
