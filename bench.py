@@ -42,7 +42,7 @@ SM_COUNT_NOMINAL = 152
 # (warps per sample, samples per CTA), from the ncu capture summarised in
 # profiles/fused_kernel_dense_traffic_B1000.md (traffic section); must be re-taken when the
 # kernel changes.
-FUSED_TRAFFIC_BYTES = {(2, 1): 91392}
+FUSED_TRAFFIC_BYTES = {(2, 1): 90880}
 
 
 def algorithmic_flops_per_sample_iter(m, n, N, n_eq=3):

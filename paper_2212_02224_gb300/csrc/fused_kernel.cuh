@@ -115,7 +115,7 @@ struct RegCap {
   // registers per thread: one timestep slot per 32 lanes needs about 70, the
   // rest is per-sample state; capped so that enough warps stay resident
   static constexpr int value =
-      SLOTS * WPS >= 8 ? 255 : (SLOTS >= 4 ? 224 : (SLOTS == 2 ? 144 : (WPS == 4 ? (ROAD ? 80 : 72) : 96)));
+      SLOTS * WPS >= 8 ? 255 : (SLOTS >= 4 ? 224 : (SLOTS == 2 ? 144 : (WPS == 4 ? 80 : 96)));
 };
 
 template <int NC, int SLOTS, int WPS, bool ROAD>
@@ -456,24 +456,35 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       const float dan = fminf(am, amax_b);
       da[s] = dan;
       const float A = act[s];
-      const float evx = A * fmaf(dv, cv, -vx[s]), evy = A * fmaf(dv, sv, -vy[s]);
-      const float eax = A * fmaf(dan, ca, -ax[s]), eay = A * fmaf(dan, sa, -ay[s]);
+      // Unclipped, h_v = v and h_a = a exactly (d = |v|, |a| with the same
+      // direction): their rows are zero, not the rounding noise of d (cos, sin) - v
+      const bool vclip = dv != sp, aclip = dan != am;
+      const float evx = vclip ? A * fmaf(dv, cv, -vx[s]) : 0.f;
+      const float evy = vclip ? A * fmaf(dv, sv, -vy[s]) : 0.f;
+      const float eax = aclip ? A * fmaf(dan, ca, -ax[s]) : 0.f;
+      const float eay = aclip ? A * fmaf(dan, sa, -ay[s]) : 0.f;
       const float ely = fminf(fmaxf(py[s], ylbs), yubs) - py[s];
       const float exs = A * ex[s];
       const float eoy = A * (ey[s] + ely);
-      const float* row = sW + tcl[s] * ST;
-      const float2 ex_[3] = {f2(exs, exs), f2(evx, evx), f2(eax, eax)};
-      const float2 ey_[3] = {f2(eoy, eoy), f2(evy, evy), f2(eay, eay)};
+      // a slot whose rows are zero on every lane adds nothing to the
+      // transposed contraction (all its constraints hold): skip it
+      const bool nz = (exs != 0.f) | (eoy != 0.f) | (evx != 0.f) | (evy != 0.f) |
+                      (eax != 0.f) | (eay != 0.f);
+      if (__any_sync(kFull, nz)) {
+        const float* row = sW + tcl[s] * ST;
+        const float2 ex_[3] = {f2(exs, exs), f2(evx, evx), f2(eax, eax)};
+        const float2 ey_[3] = {f2(eoy, eoy), f2(evy, evy), f2(eay, eay)};
 #pragma unroll
-      for (int mat = 0; mat < 3; ++mat) {
+        for (int mat = 0; mat < 3; ++mat) {
 #pragma unroll
-        for (int k4 = 0; k4 < NCP; k4 += 4) {
-          const float4 w = *reinterpret_cast<const float4*>(row + mat * NCP + k4);
-          const float2 w01 = f2(w.x, w.y), w23 = f2(w.z, w.w);
-          wx[k4 / 2] = fma2(w01, ex_[mat], wx[k4 / 2]);
-          wy[k4 / 2] = fma2(w01, ey_[mat], wy[k4 / 2]);
-          wx[k4 / 2 + 1] = fma2(w23, ex_[mat], wx[k4 / 2 + 1]);
-          wy[k4 / 2 + 1] = fma2(w23, ey_[mat], wy[k4 / 2 + 1]);
+          for (int k4 = 0; k4 < NCP; k4 += 4) {
+            const float4 w = *reinterpret_cast<const float4*>(row + mat * NCP + k4);
+            const float2 w01 = f2(w.x, w.y), w23 = f2(w.z, w.w);
+            wx[k4 / 2] = fma2(w01, ex_[mat], wx[k4 / 2]);
+            wy[k4 / 2] = fma2(w01, ey_[mat], wy[k4 / 2]);
+            wx[k4 / 2 + 1] = fma2(w23, ex_[mat], wx[k4 / 2 + 1]);
+            wy[k4 / 2 + 1] = fma2(w23, ey_[mat], wy[k4 / 2 + 1]);
+          }
         }
       }
     }
