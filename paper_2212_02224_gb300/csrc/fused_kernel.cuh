@@ -424,6 +424,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     float2 wx[NP], wy[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) { wx[k] = f2(0.f, 0.f); wy[k] = f2(0.f, 0.f); }
+    bool wany = false;     // some slot of this warp has a nonzero row (warp-uniform)
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) {
       const float v2 = fmaf(vx[s], vx[s], vy[s] * vy[s]);
@@ -471,6 +472,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       const bool nz = (exs != 0.f) | (eoy != 0.f) | (evx != 0.f) | (evy != 0.f) |
                       (eax != 0.f) | (eay != 0.f);
       if (__any_sync(kFull, nz)) {
+        wany = true;
         const float* row = sW + tcl[s] * ST;
         const float2 ex_[3] = {f2(exs, exs), f2(evx, evx), f2(eax, eax)};
         const float2 ey_[3] = {f2(eoy, eoy), f2(evy, evy), f2(eay, eay)};
@@ -493,7 +495,8 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     // multipliers, xi-step in increment form
     float wl;
     if constexpr (WPS > 1) {
-      const float part = warp_reduce_slots<NC, NP>(wx, wy, lane);
+      // a warp whose slots were all skipped has all-zero partial sums
+      const float part = wany ? warp_reduce_slots<NC, NP>(wx, wy, lane) : 0.f;
       float* rt = sRed + (it & 1) * WPS * 32;
       rt[wig * 32 + lane] = part;
       group_barrier(LPS);
