@@ -13,7 +13,10 @@ e2e    : the same metric through plan_step with host buffers (scene and
          distribution uploaded, best pair and distribution read back).
 plain_fp64 : the same cycle on the plain float64 path (reference GPU path).
 roofline   : the fused solve kernel against the FP32 FMA pipe.
-cpu_baseline: the FP64 oracle on a bounded sample, one host thread.
+latency_ms : p50 / p99 over --latency-cycles cycles after 50 warm-up cycles,
+             on the device (graph) and through plan_step (host wall clock).
+cpu_baseline: the FP64 oracle on a bounded sample, one host thread;
+cpu_baseline_all_cores: the same with one process per host core.
 
 --impl reference times the FP64 CPU oracle on the same metric instead.
 """
@@ -63,7 +66,7 @@ from oracle.basis import bernstein
 from paper_2212_02224_gb300 import scenegen as sg
 prm, sc, B = sg.workload(1)
 basis = bernstein(prm.m, prm.n_coef, prm.dt)
-p = sg.make_samples(303, sc, {nsamp}, prm.n_seg)
+p = sg.make_samples({seed}, sc, {nsamp}, prm.n_seg)
 lower.solve(p[:2], sc, prm, basis, iters=2)          # warm caches / imports
 t0 = time.perf_counter(); reps = 0
 while True:
@@ -76,9 +79,12 @@ print(json.dumps(dict(units=reps * {nsamp} * prm.inner_iters, seconds=dt, reps=r
 """
 
 
+_ONE_THREAD = dict(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+
+
 def run_oracle(nsamp=40, budget=12.0):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = _ORACLE_SNIPPET.format(root=ROOT, nsamp=nsamp, budget=budget)
+    env = dict(os.environ, **_ONE_THREAD)
+    code = _ORACLE_SNIPPET.format(root=ROOT, nsamp=nsamp, budget=budget, seed=303)
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
                          timeout=600)
     if out.returncode != 0:
@@ -88,6 +94,34 @@ def run_oracle(nsamp=40, budget=12.0):
                 sample=f"{res['reps']} x lower-level solve of {nsamp} samples of the workload "
                        f"(K=100), numpy float64, one thread; one sample-iteration = one Alg. 2 "
                        f"iteration of one sample")
+
+
+def run_oracle_all_cores(nsamp=20, budget=12.0):
+    """The same oracle solve in one single-threaded process per host core, each
+    on its own samples, all started together: the samples split across the
+    cores with no shared state.  value = all processes' sample-iterations over
+    the longest process's time."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    env = dict(os.environ, **_ONE_THREAD)
+    procs = [subprocess.Popen([sys.executable, "-c", _ORACLE_SNIPPET.format(
+                 root=ROOT, nsamp=nsamp, budget=budget, seed=1000 + i)],
+                 stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+             for i in range(cores)]
+    res = []
+    for pr in procs:
+        out, err = pr.communicate(timeout=600)
+        if pr.returncode != 0:
+            raise RuntimeError(err)
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    units = sum(r["units"] for r in res)
+    secs = max(r["seconds"] for r in res)
+    return dict(value=units / secs, unit=UNIT, cores=cores, kind="oracle",
+                sample=f"{cores} processes x (>= {min(r['reps'] for r in res)} lower-level solves "
+                       f"of {nsamp} samples of the workload, K=100), numpy float64, one thread "
+                       f"each, samples split across processes")
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -286,16 +320,24 @@ def gpu_arm(args):
     value = replica_value(units, args.steps, total_s, world)
     clocks = clk.summary()
 
+    # ---- latency: per-cycle device time over many cycles after 50 warm-up cycles
+    lat_ms = []
+    if args.latency_cycles > 0:
+        for _ in range(50):
+            pl.step_resident([B])
+        lat_ms = _timed(lambda: pl.step_resident([B]), args.latency_cycles, flush, stream)
+
     # ---- e2e: through host buffers (plan_step), wall clock per cycle
     e2e_ms = []
     mu = sigma = None
-    for i in range(args.warmup + args.steps):
+    n_e2e = max(args.steps, args.latency_cycles)
+    for i in range(max(args.warmup, 50 if args.latency_cycles > 0 else 0) + n_e2e):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         res = pl.step(sc, B, mu=mu, sigma=sigma, seed=99, step=i)
         dt_ms = (time.perf_counter() - t0) * 1e3
-        if i >= args.warmup:
+        if i >= max(args.warmup, 50 if args.latency_cycles > 0 else 0):
             e2e_ms.append(dt_ms)
     e2e_total = ranks.max(sum(e2e_ms) / 1e3)
     e2e_value = replica_value(units, len(e2e_ms), e2e_total, world)
@@ -354,12 +396,13 @@ def gpu_arm(args):
         plain = dict(value=units / (ms64 * 1e-3), unit=UNIT, ms_per_step=ms64, steps=n64)
         pf.close()
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         cpu = run_oracle()
+        cpu_all = run_oracle_all_cores()
 
     if rank == 0:
-        srt = sorted(e2e_ms)
+        lat = lat_ms or step_ms
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
@@ -369,10 +412,15 @@ def gpu_arm(args):
                        "l2": "flushed before every timed step (256 MiB write)",
                        "graph": "whole cycle captured as one CUDA graph",
                        "fused_shape": {"warps_per_sample": shape[0], "samples_per_cta": shape[1]}},
-            "latency_ms": {"p50": statistics.median(step_ms),
-                           "p99": float(np.percentile(step_ms, 99)),
+            "latency_ms": {"p50": statistics.median(lat),
+                           "p99": float(np.percentile(lat, 99)),
+                           "cycles": len(lat),
                            "e2e_p50": statistics.median(e2e_ms),
-                           "e2e_p99": float(np.percentile(srt, 99))},
+                           "e2e_p99": float(np.percentile(e2e_ms, 99)),
+                           "e2e_cycles": len(e2e_ms),
+                           "warmup_cycles": 50 if lat_ms else args.warmup,
+                           "basis": "device time per graph-captured cycle (L2 flushed before "
+                                    "each); e2e = wall time per plan_step call"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * 3 * L,
@@ -390,6 +438,7 @@ def gpu_arm(args):
                          "probe_basis": "plan_probe_alu: independent FFMA / FFMA2 / DFMA / "
                                         "MUFU rsqrt chains, 8 CTAs x 256 threads per SM"},
             "cpu_baseline": cpu,
+            "cpu_baseline_all_cores": cpu_all,
             "clocks": clocks,
             "precision": precision,
         }
@@ -582,6 +631,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--latency-cycles", type=int, default=1000,
+                    help="cycles of the latency run after 50 warm-up cycles (0: none)")
     ap.add_argument("--workload", default="dense", choices=["dense", "batched", "scale", "serving"])
     ap.add_argument("--rate", type=float, default=200.0, help="serving: requests per second")
     ap.add_argument("--serve-seconds", type=float, default=8.0)

@@ -71,3 +71,13 @@ def test_reference_arm_is_silent_on_other_ranks(monkeypatch):
     with contextlib.redirect_stdout(buf):
         bench.reference_arm(type("A", (), {"steps": 2, "warmup": 1})())
     assert buf.getvalue() == "" and called == []
+
+
+def test_all_cores_oracle_leg_counts_every_process():
+    """The all-cores CPU leg runs one single-threaded oracle process per core
+    and reports their summed work over the slowest process's time."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.run_oracle_all_cores(nsamp=2, budget=0.2)
+    assert r["kind"] == "oracle" and r["cores"] >= 1 and r["value"] > 0
+    assert f"{r['cores']} processes" in r["sample"]
