@@ -110,16 +110,21 @@ __device__ __forceinline__ void group_barrier(int nthreads) {
 // (32 WPS) groups (one group when WPS > 1).  Timestep t = s * 32 WPS +
 // (warp-in-group) * 32 + lane for slot s; lanes with t >= m compute on the
 // last timestep's data and contribute nothing.
-template <int SLOTS, int WPS, bool ROAD>
+template <int NC, int SLOTS, int WPS, bool ROAD>
 struct RegCap {
   // registers per thread: one timestep slot per 32 lanes needs about 70, the
-  // rest is per-sample state; capped so that enough warps stay resident
+  // rest is per-sample state; capped so that enough warps stay resident.  At
+  // 4 warps per sample, 72 registers let 7 CTAs of 128 threads share an SM
+  // (7 x 128 x 72 <= 65536), so 1000 samples fit one wave on 152 SMs; n = 16
+  // needs 80 to avoid spills
   static constexpr int value =
-      SLOTS * WPS >= 8 ? 255 : (SLOTS >= 4 ? 224 : (SLOTS == 2 ? 144 : (WPS == 4 ? 80 : 96)));
+      SLOTS * WPS >= 8 ? 255
+                       : (SLOTS >= 4 ? 224
+                                     : (SLOTS == 2 ? 144 : (WPS == 4 ? (NC <= 11 ? 72 : 80) : 96)));
 };
 
 template <int NC, int SLOTS, int WPS, bool ROAD>
-__global__ void __launch_bounds__(256) __maxnreg__((RegCap<SLOTS, WPS, ROAD>::value))
+__global__ void __launch_bounds__(256) __maxnreg__((RegCap<NC, SLOTS, WPS, ROAD>::value))
 fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ layout,
              const double* __restrict__ obs, const Tile* __restrict__ tiles,
              const double* __restrict__ pin, Consts c, Params prm,
@@ -211,9 +216,10 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   // shapes with few timestep slots keep the reference kinematics and the row of
   // M in registers; the others read them from shared memory
   constexpr bool kRegState = WPS == 1 && SLOTS <= 4;
-  float Mrow_r[kRegState ? NC : 1];
+  constexpr bool kRegM = kRegState || (WPS == 2 && SLOTS <= 2);
+  float Mrow_r[kRegM ? NC : 1];
 #pragma unroll
-  for (int i = 0; i < (kRegState ? NC : 1); ++i) Mrow_r[i] = Mrow_s[i];
+  for (int i = 0; i < (kRegM ? NC : 1); ++i) Mrow_r[i] = Mrow_s[i];
   float xb_l = 0.f;     // xi_bar of this lane's slot
   pdl_wait();           // p comes from the sampling kernel
   if (valid) {
@@ -345,16 +351,15 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     }
 
     // ---- B: obstacle projection, accumulated residual sum_i (h_o,i - p).
-    // A branch-free pass marks, per slot, the obstacles whose ellipse holds the
-    // point (d < 1); only those get the correction (x - x_o, y - y_o)(1/d - 1).
+    // For every obstacle within reach, one pass computes the scaled offsets of
+    // all slots, re-arms the obstacle's skip level from the warp minimum of the
+    // scaled distance, and gives the points inside its ellipse (d < 1) the
+    // correction (x - x_o, y - y_o)(1/d - 1).
     float ex[SLOTS], ey[SLOTS];
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) { ex[s] = 0.f; ey[s] = 0.f; }
     for (int i0 = 0; i0 < N; i0 += 32) {
       const int nc = min(32, N - i0);
-      unsigned ins[SLOTS];
-#pragma unroll
-      for (int s = 0; s < SLOTS; ++s) ins[s] = 0u;
       // obstacles that may be within reach (warp-uniform mask)
       unsigned near = __ballot_sync(kFull, lane < nc && thr[i0 + lane] - moved <= 1.001f);
       while (near) {
@@ -362,7 +367,9 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
         near &= near - 1u;
         const float4 q0 = sObs[4 * (i0 + ii)], q1 = sObs[4 * (i0 + ii) + 1];
         const float4 q2 = sObs[4 * (i0 + ii) + 2];
+        float sxs[SLOTS], sys[SLOTS], d2s[SLOTS];
         float dmin = 3.0e38f;
+        bool in_any = false;
         if constexpr (kPairSlots) {
 #pragma unroll
           for (int s = 0; s < SLOTS; s += 2) {
@@ -372,48 +379,38 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
             const float2 sy = fma2(f2(py[s], py[s + 1]), f2(q2.z, q2.w),
                                    fma2(f2(q1.z, q1.w), tp, f2(q1.x, q1.y)));
             const float2 d2 = fma2(sx, sx, mul2(sy, sy));
-            ins[s] |= (d2.x < 1.f ? 1u : 0u) << ii;
-            ins[s + 1] |= (d2.y < 1.f ? 1u : 0u) << ii;
-            dmin = fminf(dmin, fminf(act[s] > 0.f ? d2.x : 3.0e38f, act[s + 1] > 0.f ? d2.y : 3.0e38f));
+            sxs[s] = sx.x; sxs[s + 1] = sx.y;
+            sys[s] = sy.x; sys[s + 1] = sy.y;
+            d2s[s] = d2.x; d2s[s + 1] = d2.y;
           }
         } else {
 #pragma unroll
           for (int s = 0; s < SLOTS; ++s) {
-            const float sx = fmaf(px[s], q2.x, fmaf(q0.z, tt[s], q0.x));
-            const float sy = fmaf(py[s], q2.z, fmaf(q1.z, tt[s], q1.x));
-            const float d2 = fmaf(sx, sx, sy * sy);
-            ins[s] |= (d2 < 1.f ? 1u : 0u) << ii;
-            dmin = fminf(dmin, act[s] > 0.f ? d2 : 3.0e38f);
+            sxs[s] = fmaf(px[s], q2.x, fmaf(q0.z, tt[s], q0.x));
+            sys[s] = fmaf(py[s], q2.z, fmaf(q1.z, tt[s], q1.x));
+            d2s[s] = fmaf(sxs[s], sxs[s], sys[s] * sys[s]);
           }
+        }
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) {
+          dmin = fminf(dmin, act[s] > 0.f ? d2s[s] : 3.0e38f);
+          in_any |= act[s] > 0.f && d2s[s] < 1.f;
         }
         // warp minimum of a nonnegative float: integer order of its bits
         dmin = __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(dmin)));
         if (lane == 0) thr[i0 + ii] = fast_sqrt(dmin) + moved;
-      }
-      unsigned any = 0u;
+        if (__any_sync(kFull, in_any)) {
+          const float4 q3 = sObs[4 * (i0 + ii) + 3];
 #pragma unroll
-      for (int s = 0; s < SLOTS; ++s) {
-        ins[s] = act[s] > 0.f ? ins[s] : 0u;
-        any |= ins[s];
-      }
-      unsigned uni = __reduce_or_sync(kFull, any);
-      while (uni) {
-        const int ii = __ffs(uni) - 1;
-        uni &= uni - 1u;
-        const float4 q0 = sObs[4 * (i0 + ii)], q1 = sObs[4 * (i0 + ii) + 1];
-        const float4 q2 = sObs[4 * (i0 + ii) + 2], q3 = sObs[4 * (i0 + ii) + 3];
-#pragma unroll
-        for (int s = 0; s < SLOTS; ++s) {
-          if ((ins[s] >> ii) & 1u) {
-            const float sx = fmaf(px[s], q2.x, fmaf(q0.z, tt[s], q0.x));
-            const float sy = fmaf(py[s], q2.z, fmaf(q1.z, tt[s], q1.x));
-            const float d2 = fmaf(sx, sx, sy * sy);
-            if (d2 > 0.f) {
-              const float g = rsqrtf(d2) - 1.f;
-              ex[s] = fmaf(g * q3.x, sx, ex[s]);
-              ey[s] = fmaf(g * q3.y, sy, ey[s]);
-            } else {
-              ex[s] += q3.x;     // atan2(0, 0) = 0: h = (x_o + a, y_o)
+          for (int s = 0; s < SLOTS; ++s) {
+            if (act[s] > 0.f && d2s[s] < 1.f) {
+              if (d2s[s] > 0.f) {
+                const float g = rsqrtf(d2s[s]) - 1.f;
+                ex[s] = fmaf(g * q3.x, sxs[s], ex[s]);
+                ey[s] = fmaf(g * q3.y, sys[s], ey[s]);
+              } else {
+                ex[s] += q3.x;     // atan2(0, 0) = 0: h = (x_o + a, y_o)
+              }
             }
           }
         }
@@ -530,12 +527,19 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     __syncwarp();
     float acc_step = 0.f;
     if (valid) {
-      const float* vb = vbuf + axis * 16;
+      // this axis's half of the vector, 16-byte aligned (entries NC..15 unused)
+      const float4* vb4 = reinterpret_cast<const float4*>(vbuf + axis * 16);
+      float vb[NCP];
+#pragma unroll
+      for (int i4 = 0; i4 < NCP / 4; ++i4) {
+        const float4 v = vb4[i4];
+        vb[4 * i4] = v.x; vb[4 * i4 + 1] = v.y; vb[4 * i4 + 2] = v.z; vb[4 * i4 + 3] = v.w;
+      }
       float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll
       for (int i = 0; i < NC; i += 2) {
-        acc0 = fmaf(kRegState ? Mrow_r[i] : Mrow_s[i], vb[i], acc0);
-        if (i + 1 < NC) acc1 = fmaf(kRegState ? Mrow_r[i + 1] : Mrow_s[i + 1], vb[i + 1], acc1);
+        acc0 = fmaf(kRegM ? Mrow_r[i] : Mrow_s[i], vb[i], acc0);
+        if (i + 1 < NC) acc1 = fmaf(kRegM ? Mrow_r[i + 1] : Mrow_s[i + 1], vb[i + 1], acc1);
       }
       acc_step = acc0 + acc1;
       dl += acc_step;
