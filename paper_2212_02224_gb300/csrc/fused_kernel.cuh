@@ -44,6 +44,7 @@ __device__ __forceinline__ float fast_sqrt(float x) { return x > 0.f ? x * rsqrt
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
 // W[t] . a, Wd[t] . a, Wdd[t] . a for both axes, with coefficient pairs
 // (k, k+1) in packed registers: `row` holds the three zero-padded basis rows
@@ -511,13 +512,15 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       wl = 0.f;
       if (valid) {
         const float4* rrow = reinterpret_cast<const float4*>(rt + (axis * NC + kk) * RS);
-        float4 a = rrow[0];
+        const float4 a = rrow[0];
+        float2 lo = f2(a.x, a.y), hi = f2(a.z, a.w);
 #pragma unroll
         for (int c4 = 1; c4 < 8 * WPS; ++c4) {
           const float4 b = rrow[c4];
-          a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+          lo = add2(lo, f2(b.x, b.y));
+          hi = add2(hi, f2(b.z, b.w));
         }
-        wl = (a.x + a.y) + (a.z + a.w);
+        wl = (lo.x + lo.y) + (hi.x + hi.y);
       }
     }
     if (valid) {
