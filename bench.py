@@ -42,10 +42,11 @@ UNIT = "sample-iters/s"
 FP32_LANES_PER_SM = 128
 SM_COUNT_NOMINAL = 152
 # DRAM bytes (read + write) of one fused solve of this workload, by kernel shape
-# (warps per sample, samples per CTA), from the ncu capture summarised in
+# (warps per sample, samples per CTA), from the ncu captures summarised in
 # profiles/fused_kernel_dense_traffic_B1000.md (traffic section); must be re-taken when the
 # kernel changes.
-FUSED_TRAFFIC_BYTES = {(2, 1): 90880}
+FUSED_TRAFFIC_BYTES = {(1, 1): 102656, (1, 2): 93696, (1, 4): 90112, (1, 8): 88320, (2, 1): 90624,
+                       (4, 1): 97024}
 
 
 def algorithmic_flops_per_sample_iter(m, n, N, n_eq=3):

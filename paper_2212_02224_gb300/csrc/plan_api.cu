@@ -47,6 +47,7 @@ struct plan_ctx {
   Params prm{};
   Consts c{};
   int device = 0;
+  int sms = 0;                      // multiprocessors of the device
   int tune_wps = 0, tune_spc = 0;   // fused-kernel shape; 0 = automatic
   cudaStream_t internal = nullptr;
   cudaStream_t capture = nullptr;
@@ -265,8 +266,11 @@ struct Shape {
 Shape pick_shape(const plan_ctx* ctx, int total_B) {
   if (ctx->cfg.prec >= PLAN_PREC_TF32) return Shape{1, tc_samples_per_cta()};
   if (ctx->tune_wps > 0 && ctx->tune_spc > 0) return Shape{ctx->tune_wps, ctx->tune_spc};
-  const bool long_horizon = ctx->cfg.m > 128;
-  if (total_B <= 1024 || long_horizon) return Shape{2, 1};
+  // measured on the GB300: long horizons run best with two warps per sample;
+  // otherwise one warp per sample, 8 per CTA while the launch fits one CTA per
+  // SM, else 4 per CTA (several CTAs per SM)
+  if (ctx->cfg.m > 128) return Shape{2, 1};
+  if (total_B <= 8 * ctx->sms) return Shape{1, 8};
   return Shape{1, 4};
 }
 
@@ -504,7 +508,11 @@ int plan_init(const plan_config* cfg, plan_ctx** out) {
     plan_destroy(ctx);
     return code;
   };
-  if (cudaGetDevice(&ctx->device) != cudaSuccess) { cudaGetLastError(); return bail(PLAN_ECUDA); }
+  if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(PLAN_ECUDA);
+  }
   if (cudaStreamCreateWithFlags(&ctx->internal, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->stage_done, cudaEventDisableTiming) != cudaSuccess) {
