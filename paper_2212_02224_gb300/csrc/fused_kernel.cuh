@@ -145,8 +145,8 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   const int warps = blockDim.x >> 5;
   const int groups = warps / WPS;
 
-  float* sW = smem;                                          // [m][ST]
-  float4* sObs = reinterpret_cast<float4*>(smem + m * ST);   // [N][4]
+  float* sW = smem;                                          // [m + 1][ST]
+  float4* sObs = reinterpret_cast<float4*>(smem + (m + 1) * ST);   // [N][4]
   float* sBuf = reinterpret_cast<float*>(sObs + 4 * N);      // [warps][64]
   constexpr int RS = 32 * WPS + 4;                           // row stride of the reduction table
   // floats per sample group: one warp transposes through a [2n][RS] table; with
@@ -160,9 +160,12 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   float* sThr = sRef + warps * 6 * SLOTS * 32;               // [warps][N] obstacle re-test levels
 
   {
+    // rows 0..m-1 of the basis, then one zero row that lanes past the horizon
+    // read: their kinematics are zero and their residual rows contribute nothing
     const float4* src = reinterpret_cast<const float4*>(c.basis32);
     float4* dst = reinterpret_cast<float4*>(sW);
-    for (int i = threadIdx.x; i < m * ST / 4; i += blockDim.x) dst[i] = src[i];
+    for (int i = threadIdx.x; i < (m + 1) * ST / 4; i += blockDim.x)
+      dst[i] = i < m * ST / 4 ? src[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   }
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     // scaled trajectory: (x - x_o(t)) / a = x / a + (-x0/a) + (-vx dt / a) t,
@@ -239,13 +242,13 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   xbuf[lane] = xb_l;     // padding slots hold 0: they meet zero basis columns
   __syncwarp();
 
-  int tcl[SLOTS];     // clamped timestep (valid row address)
+  int tcl[SLOTS];     // basis row: t, or the zero row m for t >= m
   float act[SLOTS];   // 1 for t < m, else 0
   float tt[SLOTS];    // timestep index as float (obstacle tables hold per-step rates)
 #pragma unroll
   for (int s = 0; s < SLOTS; ++s) {
     const int t = s * LPS + gl;
-    tcl[s] = min(t, m - 1);
+    tcl[s] = min(t, m);
     act[s] = t < m ? 1.f : 0.f;
     tt[s] = float(t);
   }
@@ -367,7 +370,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
         const int ii = __ffs(near) - 1;
         near &= near - 1u;
         const float4 q0 = sObs[4 * (i0 + ii)], q1 = sObs[4 * (i0 + ii) + 1];
-        const float4 q2 = sObs[4 * (i0 + ii) + 2];
+        const float4 q2 = sObs[4 * (i0 + ii) + 2], q3 = sObs[4 * (i0 + ii) + 3];
         float sxs[SLOTS], sys[SLOTS], d2s[SLOTS];
         float dmin = 3.0e38f;
         bool in_any = false;
@@ -401,7 +404,6 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
         dmin = __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(dmin)));
         if (lane == 0) thr[i0 + ii] = fast_sqrt(dmin) + moved;
         if (__any_sync(kFull, in_any)) {
-          const float4 q3 = sObs[4 * (i0 + ii) + 3];
 #pragma unroll
           for (int s = 0; s < SLOTS; ++s) {
             if (act[s] > 0.f && d2s[s] < 1.f) {
@@ -454,21 +456,20 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       const float amax_b = (S * a_max <= kd) ? a_max : __fdividef(kd, S);
       const float dan = fminf(am, amax_b);
       da[s] = dan;
-      const float A = act[s];
       // Unclipped, h_v = v and h_a = a exactly (d = |v|, |a| with the same
-      // direction): their rows are zero, not the rounding noise of d (cos, sin) - v
+      // direction): their rows are zero, not the rounding noise of d (cos, sin) - v.
+      // Lanes past the horizon meet the zero basis row in the contraction.
       const bool vclip = dv != sp, aclip = dan != am;
-      const float evx = vclip ? A * fmaf(dv, cv, -vx[s]) : 0.f;
-      const float evy = vclip ? A * fmaf(dv, sv, -vy[s]) : 0.f;
-      const float eax = aclip ? A * fmaf(dan, ca, -ax[s]) : 0.f;
-      const float eay = aclip ? A * fmaf(dan, sa, -ay[s]) : 0.f;
+      const float evx = vclip ? fmaf(dv, cv, -vx[s]) : 0.f;
+      const float evy = vclip ? fmaf(dv, sv, -vy[s]) : 0.f;
+      const float eax = aclip ? fmaf(dan, ca, -ax[s]) : 0.f;
+      const float eay = aclip ? fmaf(dan, sa, -ay[s]) : 0.f;
       const float ely = fminf(fmaxf(py[s], ylbs), yubs) - py[s];
-      const float exs = A * ex[s];
-      const float eoy = A * (ey[s] + ely);
+      const float exs = ex[s];
+      const float eoy = ey[s] + ely;
       // a slot whose rows are zero on every lane adds nothing to the
       // transposed contraction (all its constraints hold): skip it
-      const bool nz = (exs != 0.f) | (eoy != 0.f) | (evx != 0.f) | (evy != 0.f) |
-                      (eax != 0.f) | (eay != 0.f);
+      const bool nz = act[s] > 0.f && (vclip | aclip | (exs != 0.f) | (eoy != 0.f));
       if (__any_sync(kFull, nz)) {
         wany = true;
         const float* row = sW + tcl[s] * ST;
@@ -585,7 +586,7 @@ template <int NC, int SLOTS, int WPS>
 size_t smem_bytes(const Params& prm, int spc) {
   const int warps = spc * WPS;
   const int red = WPS > 1 ? 2 * WPS * 32 : 2 * NC * (32 * WPS + 4);
-  size_t f = size_t(prm.m) * basis32_stride(NC) + 16 * prm.max_obs + 64 * warps + spc * red +
+  size_t f = size_t(prm.m + 1) * basis32_stride(NC) + 16 * prm.max_obs + 64 * warps + spc * red +
              spc * WPS * 2 + 2 * NC * NC + size_t(6) * SLOTS * 32 * warps + size_t(warps) * prm.max_obs;
   return f * sizeof(float);
 }
