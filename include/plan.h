@@ -314,8 +314,8 @@ int plan_server_info(plan_server* srv, plan_server_stats* out);
 /* ------------------------------------------------------------------- tuning */
 
 /* Shape of the fused FP32 kernel: warps_per_sample (the warps that share one
- * sample's timesteps) and samples_per_cta; valid shapes are (1, 1..8), (2, 1)
- * and (4, 1).  (0, 0) restores the built-in choice.  Clears the captured graphs of plan_step_resident.  Not a stage of
+ * sample's timesteps) and samples_per_cta; valid shapes are (1, 1..8),
+ * (2, 1), (2, 2), (2, 4) and (4, 1).  (0, 0) restores the built-in choice.  Clears the captured graphs of plan_step_resident.  Not a stage of
  * the paper's method: it only changes how the work is laid out on the GPU. */
 int plan_set_tuning(plan_ctx* ctx, int warps_per_sample, int samples_per_cta);
 

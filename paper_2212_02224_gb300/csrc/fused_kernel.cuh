@@ -100,15 +100,21 @@ __device__ __forceinline__ float warp_reduce_slots(const float2 (&wx)[NP], const
   return v[0];
 }
 
-// Barrier of the warps that share one sample.  With more than one warp per
-// sample a CTA holds exactly one sample group, so a fixed barrier id is used
-// (a run-time id would make the compiler reserve all 16 barriers per CTA).
-__device__ __forceinline__ void group_barrier(int nthreads) {
-  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+// Barrier of the warps that share one sample: named barrier 1 + grp for
+// sample group grp < 4 of the CTA (constant ids: a run-time id would make the
+// compiler reserve all 16 barriers per CTA).
+__device__ __forceinline__ void group_barrier(int grp, int nthreads) {
+  switch (grp) {
+    case 0: asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory"); break;
+    case 1: asm volatile("bar.sync 2, %0;" ::"r"(nthreads) : "memory"); break;
+    case 2: asm volatile("bar.sync 3, %0;" ::"r"(nthreads) : "memory"); break;
+    default: asm volatile("bar.sync 4, %0;" ::"r"(nthreads) : "memory"); break;
+  }
 }
 
 // One sample per group of WPS warps (32 WPS lanes); a CTA holds blockDim.x /
-// (32 WPS) groups (one group when WPS > 1).  Timestep t = s * 32 WPS +
+// (32 WPS) groups (up to 4 with two warps per sample, one with four).  Larger
+// CTAs share one staged copy of the basis among more samples.  Timestep t = s * 32 WPS +
 // (warp-in-group) * 32 + lane for slot s; lanes with t >= m compute on the
 // last timestep's data and contribute nothing.
 template <int NC, int SLOTS, int WPS, bool ROAD>
@@ -498,7 +504,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       const float part = wany ? warp_reduce_slots<NC, NP>(wx, wy, lane) : 0.f;
       float* rt = sRed + (it & 1) * WPS * 32;
       rt[wig * 32 + lane] = part;
-      group_barrier(LPS);
+      group_barrier(grp, LPS);
       wl = 0.f;
 #pragma unroll
       for (int w = 0; w < WPS; ++w) wl += rt[w * 32 + lane];
@@ -566,7 +572,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   if constexpr (WPS > 1) {
     float* sc2 = sScore + grp * WPS * 2;
     if (lane == 0) { sc2[2 * wig] = r_acc; sc2[2 * wig + 1] = cu_acc; }
-    group_barrier(LPS);
+    group_barrier(grp, LPS);
     r_acc = 0.f;
     cu_acc = 0.f;
 #pragma unroll

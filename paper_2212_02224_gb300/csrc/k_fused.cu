@@ -16,7 +16,8 @@ bool fused_supported(int n, int m) {
 
 bool fused_shape_ok(int wps, int spc) {
   if (wps == 1) return spc >= 1 && spc <= 8;
-  return (wps == 2 || wps == 4) && spc == 1;
+  if (wps == 2) return spc == 1 || spc == 2 || spc == 4;
+  return wps == 4 && spc == 1;
 }
 
 cudaError_t launch_fused_f32(const DevScene* scenes, const Layout* layout, const double* obs,

@@ -911,7 +911,7 @@ int plan_set_tuning(plan_ctx* ctx, int warps_per_sample, int samples_per_cta) {
   if (!ctx) return PLAN_EINVAL;
   const bool automatic = warps_per_sample == 0 && samples_per_cta == 0;
   if (!automatic && !fused_shape_ok(warps_per_sample, samples_per_cta))
-    return fail(ctx, PLAN_EINVAL, "need (1, 1..8), (2, 1) or (4, 1)");
+    return fail(ctx, PLAN_EINVAL, "need (1, 1..8), (2, 1), (2, 2), (2, 4) or (4, 1)");
   CU(ctx, cudaSetDevice(ctx->device));
   CU(ctx, cudaStreamSynchronize(ctx->internal));
   for (auto& g : ctx->graphs)
@@ -959,7 +959,7 @@ int plan_autotune(plan_ctx* ctx, const plan_scene* scene, int B, int* wps_out, i
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CU(ctx, cudaEventCreate(&e0));
   CU(ctx, cudaEventCreate(&e1));
-  const int cand[][2] = {{1, 1}, {1, 2}, {1, 4}, {1, 8}, {2, 1}, {4, 1}};
+  const int cand[][2] = {{1, 1}, {1, 2}, {1, 4}, {1, 8}, {2, 1}, {2, 2}, {2, 4}, {4, 1}};
   const int save_w = ctx->tune_wps, save_s = ctx->tune_spc;
   int best_w = 0, best_s = 0;
   float best = 1e30f;

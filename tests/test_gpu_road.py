@@ -61,7 +61,7 @@ def test_fp64_path_on_a_sharp_bend(origin):
 
 
 @pytest.mark.parametrize("prec,shape", [("fp32", (1, 1)), ("fp32", (1, 4)), ("fp32", (2, 1)),
-                                        ("fp32", (4, 1)), ("tf32x3", None)])
+                                        ("fp32", (2, 2)), ("fp32", (4, 1)), ("tf32x3", None)])
 @pytest.mark.parametrize("bend", ["sharp, K=10", "gentle, K=60"])
 def test_float32_paths_on_curved_roads(prec, shape, bend):
     if bend.startswith("sharp"):

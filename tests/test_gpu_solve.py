@@ -122,7 +122,7 @@ def test_capacity_and_argument_errors():
     pl.close()
 
 
-SHAPES = [(1, 1), (1, 4), (1, 8), (2, 1), (4, 1)]
+SHAPES = [(1, 1), (1, 4), (1, 8), (2, 1), (2, 2), (2, 4), (4, 1)]
 
 
 @pytest.fixture(scope="module")
@@ -144,14 +144,14 @@ def test_fused_kernel_shapes(wps, spc, dense_case):
     pl.close()
 
 
-@pytest.mark.parametrize("wps", [1, 2, 4])
-def test_long_and_ragged_horizons_per_shape(wps):
+@pytest.mark.parametrize("wps,spc", [(1, 1), (2, 1), (2, 2), (4, 1)])
+def test_long_and_ragged_horizons_per_shape(wps, spc):
     for m, n in ((37, 8), (200, 16)):
         prm = sg.Params(m=m, n_coef=n, inner_iters=25)
         sc = scene_with(40 + m, 4, 7, obs_x=(8.0, 60.0))
         p = sg.make_samples(41, sc, 9, 1)
         pl = planner(prm, "fp32", max_obs=8, max_samples=9)
-        pl.set_tuning(wps, 1)
+        pl.set_tuning(wps, spc)
         xi, r, cu = pl.solve(sc, to_dev(p))
         torch.cuda.synchronize()
         compare("fp32", prm, xi.cpu().numpy(), r.cpu().numpy(), cu.cpu().numpy(), *_oracle(prm, sc, p))
@@ -164,7 +164,7 @@ def test_autotune_returns_a_valid_shape(tmp_path, monkeypatch):
     monkeypatch.setenv("PLAN_TUNE_CACHE", str(cache))
     pl = planner(prm, "fp32", max_obs=16, max_samples=256)
     w, s = pl.autotune(sc, 256)
-    assert (w, s) in {(1, 1), (1, 2), (1, 4), (1, 8), (2, 1), (4, 1)}
+    assert (w, s) in {(1, 1), (1, 2), (1, 4), (1, 8), (2, 1), (2, 2), (2, 4), (4, 1)}
     assert cache.read_text().split()[4:6] == [str(w), str(s)]
     assert pl.autotune(sc, 256) == (w, s)          # served from the cache file
     with pytest.raises(binding.PlanError):
