@@ -266,10 +266,10 @@ struct Shape {
 Shape pick_shape(const plan_ctx* ctx, int total_B) {
   if (ctx->cfg.prec >= PLAN_PREC_TF32) return Shape{1, tc_samples_per_cta()};
   if (ctx->tune_wps > 0 && ctx->tune_spc > 0) return Shape{ctx->tune_wps, ctx->tune_spc};
-  // measured on the GB300: long horizons run best with two warps per sample;
-  // otherwise one warp per sample, 8 per CTA while the launch fits one CTA per
-  // SM, else 4 per CTA (several CTAs per SM)
-  if (ctx->cfg.m > 128) return Shape{2, 1};
+  // measured on the GB300: long horizons run best with two warps per sample,
+  // two samples per CTA (one staged basis for both); otherwise one warp per
+  // sample, 8 per CTA while the launch fits one CTA per SM, else 4 per CTA
+  if (ctx->cfg.m > 128) return Shape{2, 2};
   if (total_B <= 8 * ctx->sms) return Shape{1, 8};
   return Shape{1, 4};
 }
