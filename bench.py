@@ -10,7 +10,8 @@ value  : sample-iterations / s = B * K * L / device time of one cycle, inputs
          resident in HBM, CUDA events on the launching stream, L2 flushed
          (256 MiB write) before every timed cycle.
 e2e    : the same metric through plan_step with host buffers (scene and
-         distribution uploaded, best pair and distribution read back).
+         distribution go up, best pair and distribution come back; each cycle
+         warm-starts from the previous one's distribution, as an MPC loop does).
 plain_fp64 : the same cycle on the plain float64 path (reference GPU path).
 roofline   : the fused solve kernel against the FP32 FMA pipe.
 latency_ms : p50 / p99 over --latency-cycles cycles after 50 warm-up cycles,
@@ -338,16 +339,20 @@ def gpu_arm(args):
         t0 = time.perf_counter()
         res = pl.step(sc, B, mu=mu, sigma=sigma, seed=99, step=i)
         dt_ms = (time.perf_counter() - t0) * 1e3
+        # the next cycle warm-starts from this one's distribution (Alg. 1 across
+        # MPC cycles), as the resident loop above does on the device
+        mu, sigma = res["mu"], res["sigma"]
         if i >= max(args.warmup, 50 if args.latency_cycles > 0 else 0):
             e2e_ms.append(dt_ms)
     e2e_total = ranks.max(sum(e2e_ms) / 1e3)
     e2e_value = replica_value(units, len(e2e_ms), e2e_total, world)
-    # plan_step copies, per cycle: up the device scene record (352 B), its
-    # obstacles (48 B each) and the sampling state (1464 B); down the final
-    # state with the best pair (1464 B) and the timeout flag (4 B)
+    # plan_step moves, per cycle, from pinned host memory to the device: the
+    # scene record (352 B), its obstacles (48 B each) and the sampling state
+    # (1464 B); back: the final state with the best pair (1464 B) and the
+    # timeout flag (8 B)
     dev_scene, dev_cem = 352, 1464
     h2d = dev_scene + 48 * sc.n_obs + dev_cem
-    d2h = dev_cem + 4
+    d2h = dev_cem + 8
 
     # ---- roofline of the fused solve kernel (timed alone on this stream)
     p = torch.tensor(sg.make_samples(303, sc, B, prm.n_seg), dtype=torch.float64, device="cuda")

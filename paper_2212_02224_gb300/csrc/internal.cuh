@@ -216,8 +216,18 @@ cudaError_t launch_plain64(const DevScene* scenes, const Layout* layout, const i
                            const Params& prm, const Plain64Work& w, double* xi_out, double* r,
                            double* cu, cudaStream_t s);
 
+// pdl = false: a full dependency on the preceding work of the stream
 cudaError_t launch_sample(const DevScene* scenes, const Layout* layout, const DevCem* cem, int S,
-                          int max_B, int l, const Params& prm, double* p, cudaStream_t s);
+                          int max_B, int l, const Params& prm, double* p, cudaStream_t s,
+                          bool pdl = true);
+// Staging of one cycle through a pinned, device-mapped host buffer `io`: the
+// scene record (offset 0), its obstacle rows (o_obs) and the sampling state
+// (o_cem) go to the device copies; the final state and the tensor-core timeout
+// flag come back to offset o_ret.  One CTA each.
+cudaError_t launch_io_in(const void* io, size_t o_obs, size_t o_cem, DevScene* scene, double* obs,
+                         DevCem* cem, cudaStream_t s);
+cudaError_t launch_io_out(const DevCem* cem, const int* tc_err, void* io, size_t o_ret,
+                          cudaStream_t s);
 
 cudaError_t launch_select_update(const Layout* layout, DevCem* cem, int S, int l,
                                  const Params& prm, const double* p, const double* xi,
@@ -225,6 +235,7 @@ cudaError_t launch_select_update(const Layout* layout, DevCem* cem, int S, int l
                                  int max_B, cudaStream_t s);
 
 static_assert(sizeof(DevCem) % sizeof(unsigned long long) == 0, "DevCem is copied in 8-byte words");
+static_assert(sizeof(DevScene) % sizeof(unsigned long long) == 0, "DevScene is copied in 8-byte words");
 
 cudaError_t launch_cem_copy(DevCem* dst, const DevCem* src, const int* idx, int S, bool scatter,
                             cudaStream_t s);

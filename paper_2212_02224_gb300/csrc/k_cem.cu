@@ -615,6 +615,34 @@ __global__ void cem_copy_kernel(DevCem* dst, const DevCem* src, const int* idx, 
   b[w] = a[w];
 }
 
+// One MPC cycle through host buffers: the host writes the scene record, its
+// obstacle rows and the sampling state into a pinned host buffer mapped into
+// the device's address space; these kernels move them in 8-byte words at the
+// head of the cycle's graph and move the final state (with the best pair) and
+// the timeout flag back at its tail.  Offsets are in words; the host sizes the
+// obstacle region for max_obs rows and checks n_obs <= max_obs before staging.
+__global__ void io_in_kernel(const unsigned long long* io, size_t w_obs, size_t w_cem,
+                             DevScene* scene, double* obs, DevCem* cem) {
+  constexpr int WS = sizeof(DevScene) / sizeof(unsigned long long);
+  constexpr int WC = sizeof(DevCem) / sizeof(unsigned long long);
+  const int n_obs_w = reinterpret_cast<const DevScene*>(io)->n_obs * 6;
+  unsigned long long* ds = reinterpret_cast<unsigned long long*>(scene);
+  unsigned long long* dob = reinterpret_cast<unsigned long long*>(obs);
+  unsigned long long* dc = reinterpret_cast<unsigned long long*>(cem);
+  for (int i = threadIdx.x; i < WS; i += blockDim.x) ds[i] = io[i];
+  for (int i = threadIdx.x; i < n_obs_w; i += blockDim.x) dob[i] = io[w_obs + i];
+  for (int i = threadIdx.x; i < WC; i += blockDim.x) dc[i] = io[w_cem + i];
+}
+
+__global__ void io_out_kernel(const DevCem* cem, const int* tc_err, unsigned long long* io,
+                              size_t w_ret) {
+  constexpr int WC = sizeof(DevCem) / sizeof(unsigned long long);
+  const unsigned long long* sc = reinterpret_cast<const unsigned long long*>(cem);
+  for (int i = threadIdx.x; i < WC; i += blockDim.x) io[w_ret + i] = sc[i];
+  if (threadIdx.x == 0) io[w_ret + WC] = static_cast<unsigned long long>(*tc_err != 0);
+  __threadfence_system();
+}
+
 }  // namespace
 
 cudaError_t launch_cem_copy(DevCem* dst, const DevCem* src, const int* idx, int S, bool scatter,
@@ -626,10 +654,28 @@ cudaError_t launch_cem_copy(DevCem* dst, const DevCem* src, const int* idx, int 
 }
 
 cudaError_t launch_sample(const DevScene* scenes, const Layout* layout, const DevCem* cem, int S,
-                          int max_B, int l, const Params& prm, double* p, cudaStream_t s) {
+                          int max_B, int l, const Params& prm, double* p, cudaStream_t s,
+                          bool pdl) {
   if (S == 0 || max_B == 0) return cudaSuccess;
   dim3 grid((max_B + 127) / 128, S);
+  if (!pdl) {
+    sample_kernel<<<grid, 128, 0, s>>>(scenes, layout, cem, l, prm, p);
+    return cudaGetLastError();
+  }
   return launch_pdl(sample_kernel, grid, dim3(128), 0, s, scenes, layout, cem, l, prm, p);
+}
+
+cudaError_t launch_io_in(const void* io, size_t o_obs, size_t o_cem, DevScene* scene, double* obs,
+                         DevCem* cem, cudaStream_t s) {
+  io_in_kernel<<<1, 256, 0, s>>>(static_cast<const unsigned long long*>(io), o_obs / 8, o_cem / 8,
+                                 scene, obs, cem);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_io_out(const DevCem* cem, const int* tc_err, void* io, size_t o_ret,
+                          cudaStream_t s) {
+  io_out_kernel<<<1, 256, 0, s>>>(cem, tc_err, static_cast<unsigned long long*>(io), o_ret / 8);
+  return cudaGetLastError();
 }
 
 // Shared-memory attributes of the selection kernels, set once per device

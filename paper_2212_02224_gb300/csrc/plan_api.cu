@@ -35,6 +35,7 @@ struct SceneSet {
 struct GraphEntry {
   std::vector<int> B;
   bool road = false;       // kernel variant captured (road profile or not)
+  bool io = false;         // with the host-mapped staging of plan_step at head and tail
   SceneSet set;            // own layout / tiles / sample_scene (scenes+obs shared)
   cudaGraphExec_t exec = nullptr;
   int total_B = 0, max_B = 0;
@@ -68,6 +69,12 @@ struct plan_ctx {
   Plain64Work pw{};
   DevCem* cem_tmp = nullptr;   // single-stage sampling
   Layout* layout_tmp = nullptr;
+
+  // plan_step's pinned, device-mapped staging: scene record at 0, obstacle rows
+  // at io_obs (max_obs rows), sampling state at io_cem, result at io_ret
+  unsigned char* io = nullptr;
+  void* io_dev = nullptr;
+  size_t io_obs = 0, io_cem = 0, io_ret = 0;
 
   // pinned staging
   unsigned char* stage = nullptr;
@@ -477,6 +484,7 @@ int plan_destroy(plan_ctx* ctx) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
   for (void* p : ctx->allocs) cudaFree(p);
   if (ctx->stage) cudaFreeHost(ctx->stage);
+  if (ctx->io) cudaFreeHost(ctx->io);
   if (ctx->stage_done) cudaEventDestroy(ctx->stage_done);
   if (ctx->internal) cudaStreamDestroy(ctx->internal);
   if (ctx->capture) cudaStreamDestroy(ctx->capture);
@@ -554,6 +562,23 @@ int plan_init(const plan_config* cfg, plan_ctx** out) {
     A(dalloc(ctx, &ctx->pw.xprev, B * m));
   }
   if (st != PLAN_OK) return bail(st);
+  {
+    ctx->io_obs = align_up(sizeof(DevScene));
+    ctx->io_cem = ctx->io_obs + align_up(size_t(c.max_obs) * 6 * sizeof(double));
+    ctx->io_ret = ctx->io_cem + align_up(sizeof(DevCem));
+    const size_t io_bytes = ctx->io_ret + align_up(sizeof(DevCem) + sizeof(unsigned long long));
+    void* h = nullptr;
+    if (cudaHostAlloc(&h, io_bytes, cudaHostAllocMapped) != cudaSuccess) {
+      cudaGetLastError();
+      return bail(PLAN_ENOMEM);
+    }
+    ctx->io = static_cast<unsigned char*>(h);
+    std::memset(ctx->io, 0, io_bytes);
+    if (cudaHostGetDevicePointer(&ctx->io_dev, h, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return bail(PLAN_ECUDA);
+    }
+  }
   cem_setup();
   fused_setup();
   if (c.prec >= PLAN_PREC_TF32) tc_setup();
@@ -692,8 +717,12 @@ int plan_get_result(plan_ctx* ctx, int slot, plan_result* out, void* stream) {
   return PLAN_OK;
 }
 
-int plan_step_resident(plan_ctx* ctx, const int* B, int S, void* stream) {
-  if (!ctx) return PLAN_EINVAL;
+namespace {
+
+// Alg. 1 on the resident scene slots 0..S-1 as one captured graph per sample
+// layout; io: the graph also moves plan_step's staging in at its head and out
+// at its tail (through the host-mapped buffer), so that cycle needs no copies.
+int run_cycle(plan_ctx* ctx, const int* B, int S, void* stream, bool io) {
   if (S < 1 || !B) return fail(ctx, PLAN_EINVAL, "need S >= 1 and B");
   if (S > ctx->n_uploaded) return fail(ctx, PLAN_ECAPACITY, "S exceeds the uploaded scene slots");
   std::vector<int> Bv(B, B + S);
@@ -709,11 +738,12 @@ int plan_step_resident(plan_ctx* ctx, const int* B, int S, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   GraphEntry* g = nullptr;
   for (auto& e : ctx->graphs)
-    if (e.B == Bv && e.road == ctx->res.road) g = &e;
+    if (e.B == Bv && e.road == ctx->res.road && e.io == io) g = &e;
   if (!g) {
     GraphEntry e;
     e.B = Bv;
     e.road = ctx->res.road;
+    e.io = io;
     e.total_B = int(total);
     e.max_B = max_B;
     e.set.scenes = ctx->res.scenes;
@@ -728,9 +758,14 @@ int plan_step_resident(plan_ctx* ctx, const int* B, int S, void* stream) {
     cudaGraph_t graph = nullptr;
     CU(ctx, cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal));
     cudaError_t ce = cudaSuccess;
+    if (io)
+      ce = launch_io_in(ctx->io_dev, ctx->io_obs, ctx->io_cem, e.set.scenes, e.set.obs, ctx->cem,
+                        ctx->capture);
     for (int l = 1; l <= ctx->cfg.outer_iters && ce == cudaSuccess; ++l) {
+      // after the staging kernel the first sampling waits for it in full (its
+      // writes are read by the solve's prologue before that kernel's own wait)
       ce = launch_sample(e.set.scenes, e.set.layout, ctx->cem, S, max_B, l, ctx->prm, ctx->p,
-                         ctx->capture);
+                         ctx->capture, !(io && l == 1));
       if (ce == cudaSuccess)
         ce = run_solve(ctx, e.set, e.set, nt, int(total), ctx->p, ctx->xi, ctx->r, ctx->cu,
                        ctx->capture);
@@ -738,6 +773,8 @@ int plan_step_resident(plan_ctx* ctx, const int* B, int S, void* stream) {
         ce = launch_select_update(e.set.layout, ctx->cem, S, l, ctx->prm, ctx->p, ctx->xi, ctx->r,
                                   ctx->cu, ctx->elite, max_B, ctx->capture);
     }
+    if (io && ce == cudaSuccess)
+      ce = launch_io_out(ctx->cem, ctx->tc_err, ctx->io_dev, ctx->io_ret, ctx->capture);
     cudaError_t ee = cudaStreamEndCapture(ctx->capture, &graph);
     if (ce != cudaSuccess || ee != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
@@ -760,6 +797,13 @@ int plan_step_resident(plan_ctx* ctx, const int* B, int S, void* stream) {
   return PLAN_OK;
 }
 
+}  // namespace
+
+int plan_step_resident(plan_ctx* ctx, const int* B, int S, void* stream) {
+  if (!ctx) return PLAN_EINVAL;
+  return run_cycle(ctx, B, S, stream, false);
+}
+
 int plan_step(plan_ctx* ctx, const plan_scene* scene, plan_cem_state* st, int B, plan_result* out,
               void* stream) {
   if (!ctx) return PLAN_EINVAL;
@@ -770,40 +814,28 @@ int plan_step(plan_ctx* ctx, const plan_scene* scene, plan_cem_state* st, int B,
   TRY(make_cem(ctx, st, scene->n_lanes, scene->lane_width, &c0));
   CU(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // one pinned staging buffer: scene, obstacles and state go up, the final
-  // state (with the best pair) and the timeout flag come back, one sync
-  const size_t n_obs = size_t(scene->n_obs) * 6 * sizeof(double);
-  const size_t o_obs = align_up(sizeof(DevScene)), o_cem = o_obs + align_up(n_obs);
-  const size_t o_ret = o_cem + align_up(sizeof(DevCem));
-  TRY(stage_acquire(ctx, o_ret + sizeof(DevCem) + sizeof(int)));
+  // scene, obstacles and state go into the host-mapped staging buffer; the
+  // cycle's graph moves them in, runs Alg. 1 and moves the final state (with
+  // the best pair) and the timeout flag back: one launch, one sync.  The
+  // previous call synchronised, so no graph is still reading the buffer.
   const DevScene ds = to_dev(ctx, *scene, 0);
-  std::memcpy(ctx->stage, &ds, sizeof ds);
-  double* ob = reinterpret_cast<double*>(ctx->stage + o_obs);
+  std::memcpy(ctx->io, &ds, sizeof ds);
+  double* ob = reinterpret_cast<double*>(ctx->io + ctx->io_obs);
   for (int k = 0; k < scene->n_obs; ++k) {
     const plan_obstacle& o = scene->obs[k];
     const double v[6] = {o.x0, o.y0, o.vx, o.vy, o.a, o.b};
     std::memcpy(ob + 6 * k, v, sizeof v);
   }
-  std::memcpy(ctx->stage + o_cem, &c0, sizeof c0);
-  CU(ctx, cudaMemcpyAsync(ctx->res.scenes, ctx->stage, sizeof ds, cudaMemcpyHostToDevice, s));
-  if (n_obs) CU(ctx, cudaMemcpyAsync(ctx->res.obs, ob, n_obs, cudaMemcpyHostToDevice, s));
-  CU(ctx, cudaMemcpyAsync(ctx->cem, ctx->stage + o_cem, sizeof c0, cudaMemcpyHostToDevice, s));
-  TRY(stage_release(ctx, s));   // a graph capture below may reuse the staging buffer
+  std::memcpy(ctx->io + ctx->io_cem, &c0, sizeof c0);
   ctx->res.road = scene->n_road > 0;
   ctx->res_host.assign(1, ds);
   ctx->n_uploaded = 1;
-  TRY(plan_step_resident(ctx, &B, 1, stream));
-  // waits only for the uploads above (the cycle is already queued behind them)
-  TRY(stage_acquire(ctx, o_ret + sizeof(DevCem) + sizeof(int)));
-  CU(ctx, cudaMemcpyAsync(ctx->stage + o_ret, ctx->cem, sizeof(DevCem), cudaMemcpyDeviceToHost, s));
-  CU(ctx, cudaMemcpyAsync(ctx->stage + o_ret + sizeof(DevCem), ctx->tc_err, sizeof(int),
-                          cudaMemcpyDeviceToHost, s));
+  TRY(run_cycle(ctx, &B, 1, stream, true));
   CU(ctx, cudaStreamSynchronize(s));
-  ctx->stage_pending = false;
   DevCem c;
-  std::memcpy(&c, ctx->stage + o_ret, sizeof c);
-  int tc_timeout = 0;
-  std::memcpy(&tc_timeout, ctx->stage + o_ret + sizeof c, sizeof tc_timeout);
+  std::memcpy(&c, ctx->io + ctx->io_ret, sizeof c);
+  unsigned long long tc_timeout = 0;
+  std::memcpy(&tc_timeout, ctx->io + ctx->io_ret + sizeof c, sizeof tc_timeout);
   if (tc_timeout) {
     // report once: clear the flag for the next calls
     cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), s);
