@@ -8,10 +8,13 @@ iterations, ConstraintEliteSet 150 and EliteSet 50 (the paper's sizes).
 
 value  : sample-iterations / s = B * K * L / device time of one cycle, inputs
          resident in HBM, CUDA events on the launching stream, L2 flushed
-         (256 MiB write) before every timed cycle.
+         (256 MiB write) before every timed cycle.  Every cycle is a planning
+         call of its own (its first outer iteration samples the behavioural
+         prior, Alg. 1 line 2), so no cycle inherits a distribution that has
+         already converged on one trajectory.
 e2e    : the same metric through plan_step with host buffers (scene and
-         distribution go up, best pair and distribution come back; each cycle
-         warm-starts from the previous one's distribution, as an MPC loop does).
+         distribution go up, best pair and distribution come back), the same
+         sequence of planning calls.
 plain_fp64 : the same cycle on the plain float64 path (reference GPU path).
 roofline   : the fused solve kernel against the FP32 FMA pipe.
 latency_ms : p50 / p99 over --latency-cycles cycles after 50 warm-up cycles,
@@ -303,8 +306,15 @@ def gpu_arm(args):
     pl = Planner(prm, prec="fp32", max_obs=16, max_samples=B)
     shape = pl.autotune(sc, B)          # fused-kernel shape for this workload (setup, untimed)
     pl.upload([sc])
-    pl.set_state(0, seed=1234 + rank)
-    for _ in range(args.warmup):
+
+    def fresh(i):
+        # every cycle is a planning call of its own: its first outer iteration
+        # samples the behavioural prior (Alg. 1 line 2); the state upload is
+        # queued before the timed region starts
+        pl.set_state(0, seed=1234 + rank, step=i)
+
+    for i in range(args.warmup):
+        fresh(i)
         pl.step_resident([B])
     barrier()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -313,6 +323,7 @@ def gpu_arm(args):
         barrier()
         for i in range(args.steps):
             flush.zero_()
+            fresh(args.warmup + i)
             starts[i].record(stream)
             pl.step_resident([B])
             ends[i].record(stream)
@@ -325,23 +336,20 @@ def gpu_arm(args):
     # ---- latency: per-cycle device time over many cycles after 50 warm-up cycles
     lat_ms = []
     if args.latency_cycles > 0:
-        for _ in range(50):
+        for i in range(50):
+            fresh(i)
             pl.step_resident([B])
-        lat_ms = _timed(lambda: pl.step_resident([B]), args.latency_cycles, flush, stream)
+        lat_ms = _timed(lambda: pl.step_resident([B]), args.latency_cycles, flush, stream, prep=fresh)
 
     # ---- e2e: through host buffers (plan_step), wall clock per cycle
     e2e_ms = []
-    mu = sigma = None
     n_e2e = max(args.steps, args.latency_cycles)
     for i in range(max(args.warmup, 50 if args.latency_cycles > 0 else 0) + n_e2e):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = pl.step(sc, B, mu=mu, sigma=sigma, seed=99, step=i)
+        pl.step(sc, B, seed=1234 + rank, step=i)      # a fresh planning call, as above
         dt_ms = (time.perf_counter() - t0) * 1e3
-        # the next cycle warm-starts from this one's distribution (Alg. 1 across
-        # MPC cycles), as the resident loop above does on the device
-        mu, sigma = res["mu"], res["sigma"]
         if i >= max(args.warmup, 50 if args.latency_cycles > 0 else 0):
             e2e_ms.append(dt_ms)
     e2e_total = ranks.max(sum(e2e_ms) / 1e3)
@@ -394,6 +402,7 @@ def gpu_arm(args):
         fe = [torch.cuda.Event(enable_timing=True) for _ in range(n64)]
         for i in range(n64):
             flush.zero_()
+            pf.set_state(0, seed=1234 + rank, step=i)
             fs[i].record(stream)
             pf.step_resident([B])
             fe[i].record(stream)
@@ -417,6 +426,8 @@ def gpu_arm(args):
             "config": {"workload": WORKLOAD, "parallelism": f"replicas{world}",
                        "l2": "flushed before every timed step (256 MiB write)",
                        "graph": "whole cycle captured as one CUDA graph",
+                       "cycle": "each timed cycle is a fresh planning call (first outer "
+                                "iteration samples the behavioural prior)",
                        "fused_shape": {"warps_per_sample": shape[0], "samples_per_cta": shape[1]}},
             "latency_ms": {"p50": statistics.median(lat),
                            "p99": float(np.percentile(lat, 99)),
@@ -480,12 +491,16 @@ def reference_arm(args):
 
 # ----------------------------------------------------------------------------- other workloads
 
-def _timed(fn, reps, flush, stream):
+def _timed(fn, reps, flush, stream, prep=None):
+    """Device time of `reps` calls of fn, L2 flushed before each; prep(i) runs
+    (and queues its work) before each timed region starts."""
     import torch
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(reps)]
-    for a, b in ev:
+    for i, (a, b) in enumerate(ev):
         flush.zero_()
+        if prep is not None:
+            prep(i)
         a.record(stream)
         fn()
         b.record(stream)
@@ -504,14 +519,18 @@ def batched_arm(args):
     pl = Planner(prm, prec="fp32", max_obs=20, max_samples=tot, max_scenes=len(scenes))
     pl.set_tuning(1, 2)
     pl.upload(scenes)
-    for i in range(len(scenes)):
-        pl.set_state(i, seed=100 + i)
+
+    def fresh(i):      # every cycle a planning call of its own, as in the dense arm
+        for k in range(len(scenes)):
+            pl.set_state(k, seed=100 + k, step=i)
+
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
+    for i in range(args.warmup):
+        fresh(i)
         pl.step_resident(Bs)
     with ClockSampler(0) as clk:
-        ms = _timed(lambda: pl.step_resident(Bs), args.steps, flush, stream)
+        ms = _timed(lambda: pl.step_resident(Bs), args.steps, flush, stream, prep=fresh)
     units = tot * prm.inner_iters * prm.outer_iters
     print(json.dumps({
         "metric": METRIC, "workload": "batched", "value": units * len(ms) / (sum(ms) / 1e3),
@@ -537,10 +556,14 @@ def scale_arm(args):
         pl = Planner(prm, prec="fp32", max_obs=32, max_samples=B)
         pl.autotune(sc, B)
         pl.upload([sc])
-        pl.set_state(0, seed=7)
-        for _ in range(args.warmup):
+
+        def fresh(i, pl=pl):
+            pl.set_state(0, seed=7, step=i)
+
+        for i in range(args.warmup):
+            fresh(i)
             pl.step_resident([B])
-        ms = _timed(lambda: pl.step_resident([B]), max(3, args.steps // 4), flush, stream)
+        ms = _timed(lambda: pl.step_resident([B]), max(3, args.steps // 4), flush, stream, prep=fresh)
         p = torch.tensor(sg.make_samples(3, sc, B, prm.n_seg), device="cuda")
         ks = _timed(lambda: pl.solve(sc, p, want_xi=False), 5, flush, stream)
         flops = algorithmic_flops_per_sample_iter(prm.m, prm.n_coef, sc.n_obs) * B * prm.inner_iters
