@@ -232,53 +232,46 @@ __device__ void select_elite_set(const double* r, const double* cu, int B, int n
   bitonic_sort(sh, P);
 }
 
+// Sum over the warp in a fixed butterfly order (lane 0's result is used).
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // Eqs. (mean_update, cov_update, s_formula) over the q elites p_e(e), costs c_e(e).
-// The elite rows are staged into shared memory (`stage`, `cap` doubles) with
-// one parallel load per chunk; every sum still runs over e in increasing order
-// in one thread, so the result does not depend on the chunking.
+// Every sum runs on one warp: lane i adds the terms e = i, i + 32, ... in
+// increasing order, then the lanes combine in a fixed butterfly.  The result
+// does not depend on the block size, and the float64 chains stay a few terms
+// long (float64 runs at 1/64 of the float32 rate here).  accum holds
+// 1 + kMaxDp doubles: the weight total, then the new mean.
 template <class PE, class CE>
 __device__ void update_moments(PE p_e, CE c_e, double cmin, int q, int d_p, double gamma,
                                double eta, double* mu, double* sigma, int ld, double* sw,
-                               double* accum, double* stage, int cap) {
-  const int tid = threadIdx.x;
+                               double* accum) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int e = tid; e < q; e += blockDim.x) sw[e] = exp(-(c_e(e) - cmin) / gamma);
   __syncthreads();
-  double* mu_new = accum;
-  double* ssum = accum + kMaxDp;
-  if (tid == 0) {
-    double S = 0.0;
-    for (int e = 0; e < q; ++e) S += sw[e];
-    *ssum = S;
+  // the weight total and the weighted sums of each coordinate
+  for (int j = warp; j <= d_p; j += nw) {
+    double part = 0.0;
+    for (int e = lane; e < q; e += 32) part += j == 0 ? sw[e] : sw[e] * p_e(e, j - 1);
+    part = warp_sum_f64(part);
+    if (lane == 0) accum[j] = part;
   }
-  const int ch = cap / d_p;                 // elites per staged chunk
-  const bool resident = q <= ch;            // one chunk holds them all
-  auto load = [&](int e0, int ne) {
-    for (int t = tid; t < ne * d_p; t += blockDim.x) stage[t] = p_e(e0 + t / d_p, t % d_p);
-  };
-  double acc_mu = 0.0;
-  for (int e0 = 0; e0 < q; e0 += ch) {
-    const int ne = min(ch, q - e0);
-    load(e0, ne);
-    __syncthreads();
-    if (tid < d_p)
-      for (int e = 0; e < ne; ++e) acc_mu += sw[e0 + e] * stage[e * d_p + tid];
-    __syncthreads();
+  __syncthreads();
+  double* mu_new = accum + 1;
+  const double inv_s = 1.0 / accum[0];       // one float64 division for the whole update
+  if (tid < d_p) mu_new[tid] = (1.0 - eta) * mu[tid] + eta * mu_new[tid] * inv_s;
+  __syncthreads();
+  for (int j = warp; j < d_p * d_p; j += nw) {
+    const int a = j / d_p, b = j % d_p;
+    const double ma = mu_new[a], mb = mu_new[b];
+    double part = 0.0;
+    for (int e = lane; e < q; e += 32) part += sw[e] * (p_e(e, a) - ma) * (p_e(e, b) - mb);
+    part = warp_sum_f64(part);
+    if (lane == 0) sigma[a * ld + b] = (1.0 - eta) * sigma[a * ld + b] + eta * part * inv_s;
   }
-  if (tid < d_p) mu_new[tid] = (1.0 - eta) * mu[tid] + eta * acc_mu / *ssum;
-  if (!resident) __syncthreads();
-  const int a = tid / d_p, b = tid % d_p;
-  double acc = 0.0;
-  for (int e0 = 0; e0 < q; e0 += ch) {
-    const int ne = min(ch, q - e0);
-    if (!resident) load(e0, ne);
-    __syncthreads();
-    if (tid < d_p * d_p)
-      for (int e = 0; e < ne; ++e)
-        acc += sw[e0 + e] * (stage[e * d_p + a] - mu_new[a]) * (stage[e * d_p + b] - mu_new[b]);
-    if (!resident) __syncthreads();
-  }
-  if (tid < d_p * d_p)
-    sigma[a * ld + b] = (1.0 - eta) * sigma[a * ld + b] + eta * acc / *ssum;
   __syncthreads();
   if (tid < d_p) mu[tid] = mu_new[tid];
   __syncthreads();
@@ -324,9 +317,8 @@ select_update_kernel(const Layout* layout, DevCem* cem, int l, Params prm, const
   auto id_of = [&](int e) { const int id = sh.idx[e]; return (id >= 0 && id < B) ? id : 0; };
   auto p_e = [&](int e, int a) { return ps[size_t(id_of(e)) * d_p + a]; };
   auto c_e = [&](int e) { return cs[id_of(e)] + rs[id_of(e)]; };
-  // the order keys are no longer needed: their space stages the elite rows
   update_moments(p_e, c_e, c_e(0), q, d_p, prm.gamma, prm.eta, st.mu, st.sigma, kMaxDp, sh.sw,
-                 sh.acc, reinterpret_cast<double*>(sh.key), int(sizeof(sh.key) / sizeof(double)));
+                 sh.acc);
   const int best = id_of(0);
   if (threadIdx.x == 0) {
     cholesky(st.sigma, prm.cov_eps, d_p, st.chol);
@@ -366,190 +358,197 @@ update_only_kernel(const double* p_elite, const double* cost, int q, int d_p, do
   __syncthreads();
   auto p_e = [&](int e, int a) { return p_elite[size_t(e) * d_p + a]; };
   auto c_e = [&](int e) { return cost[e]; };
-  update_moments(p_e, c_e, cmin, q, d_p, gamma, eta, mu, sigma, d_p, sh.sw, sh.acc,
-                 reinterpret_cast<double*>(sh.key), int(sizeof(sh.key) / sizeof(double)));
+  update_moments(p_e, c_e, cmin, q, d_p, gamma, eta, mu, sigma, d_p, sh.sw, sh.acc);
 }
 
 // ---------------------------------------------------------------------------
-// Selection for B <= kSmallMaxB, one 256-thread block per scene, the order
-// keys staged in shared memory once.  Same sets as above: ConstraintEliteSet
-// (n_c lowest r) and EliteSet (q lowest cu + r among them, sorted), ties to
-// the lower sample index.
+// Selection for B <= kSmallMaxB, one 256-thread block per scene: a bitonic
+// sort of the (order key of r, sample index) pairs in shared memory gives the
+// ConstraintEliteSet (its first n_c entries: n_c lowest r, ties to the lower
+// index), and a second sort of the candidates by (order key of cu + r, sample
+// index) gives the EliteSet in order.  The same sets as the large-B path.
 constexpr int kSmallMaxB = 2048;
 constexpr int kSmallMaxC = 1024;
 constexpr int kSmallThreads = 256;
 
 struct SmallSel {
-  unsigned long long key[kSmallMaxB];    // order keys of r
+  unsigned long long key[kSmallMaxB];    // order keys of r, sorted in place
+  int kidx[kSmallMaxB];                  // their sample indices
   unsigned long long ckey[kSmallMaxC];   // order keys of cu + r of the candidates
-  int cand[kSmallMaxC];                  // ConstraintEliteSet, increasing sample index
   int idx[kSmallMaxC];                   // EliteSet, sorted by (cost, index)
-  unsigned hist[256];
-  unsigned wl[32], we[32];
-  unsigned long long gkey[32];
-  int gidx[32];
-  unsigned long long prefix, tk;
-  int need, gc, gcount, ti;
   double sw[kSmallMaxC];
   double acc[kMaxDp * kMaxDp + kMaxDp + 1];
 };
 
-// The k smallest of key[0..count) by (key, position), written as positions to
-// out[0..k) in increasing order.  Radix select on 8-bit digits (shared-memory
-// counts, one atomic per distinct digit within a warp) that stops as soon as
-// the group sharing the selected prefix is either taken whole or has at most
-// 32 members (ranked directly); then an ordered compaction.
-__device__ void small_select(const unsigned long long* key, int count, int k, int* out,
-                             SmallSel& sh) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const unsigned lt = (1u << lane) - 1u;
-  if (k >= count) {
-    for (int i = tid; i < count; i += blockDim.x) out[i] = i;
-    __syncthreads();
-    return;
+__device__ __forceinline__ bool pair_gt(unsigned long long ka, int ia, unsigned long long kb,
+                                        int ib) {
+  return ka > kb || (ka == kb && ia > ib);
+}
+
+// One compare-exchange of the bitonic network at element e against its
+// partner (ko, xo): e is the lower position when `lower`, and the kk-block of
+// e sorts ascending when (e & kk) == 0.
+__device__ __forceinline__ void bitonic_keep(unsigned long long& k, int& x, unsigned long long ko,
+                                             int xo, bool lower, bool asc) {
+  const bool gt = pair_gt(k, x, ko, xo);
+  if (lower == asc ? gt : !gt) {
+    k = ko;
+    x = xo;
   }
-  unsigned long long P = 0ull;
-  int need = k, gc = count, shift = 56;
-  if (tid == 0) sh.gcount = 0;
-  for (shift = 56;; shift -= 8) {
-    for (int d = tid; d < 256; d += blockDim.x) sh.hist[d] = 0u;
-    __syncthreads();
-    for (int base = 0; base < count; base += blockDim.x) {
-      const int i = base + tid;
-      bool in = false;
-      unsigned dig = 256u + lane;              // distinct for lanes that count nothing
-      if (i < count) {
-        const unsigned long long kk = key[i];
-        in = shift == 56 || ((kk ^ P) >> (shift + 8)) == 0ull;
-        if (in) dig = unsigned((kk >> shift) & 255ull);
+}
+
+// Stage at distance J < E between the elements of one thread.
+template <int E, int J>
+__device__ __forceinline__ void bitonic_intra(unsigned long long (&k)[E], int (&x)[E], int kk) {
+#pragma unroll
+  for (int u = 0; u < E; ++u) {
+    if ((u & J) == 0) {
+      const bool asc = ((E * int(threadIdx.x) + u) & kk) == 0;
+      unsigned long long ka = k[u], kb = k[u ^ J];
+      int xa = x[u], xb = x[u ^ J];
+      if (pair_gt(ka, xa, kb, xb) == asc) {
+        k[u] = kb; x[u] = xb;
+        k[u ^ J] = ka; x[u ^ J] = xa;
       }
-      const unsigned grp = __match_any_sync(0xffffffffu, dig);
-      if (in && (__ffs(grp) - 1) == lane) atomicAdd(&sh.hist[dig], unsigned(__popc(grp)));
     }
-    __syncthreads();
-    if (warp == 0) {
-      unsigned loc = 0;
-      for (int d = 0; d < 8; ++d) loc += sh.hist[8 * lane + d];
-      unsigned incl = loc;
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-      }
-      const unsigned hit = __ballot_sync(0xffffffffu, incl >= unsigned(need));
-      const int first = hit ? __ffs(hit) - 1 : 31;
-      if (lane == first) {
-        unsigned c = incl - loc;
-        int d = 8 * lane;
-        for (; d < 8 * lane + 7; ++d) {
-          if (c + sh.hist[d] >= unsigned(need)) break;
-          c += sh.hist[d];
+  }
+}
+
+// Bitonic sort ascending by (key, idx) of P = 256 E pairs held E per thread,
+// element E tid + u in k[u], x[u] (blockDim.x = 256).  Partners in the same
+// thread are exchanged in registers, partners in the same warp by shuffles;
+// only the stages whose partners sit in another warp (distance >= 32 E, six
+// stages) go through the scratch arrays skey / sidx [P], laid out u-major so
+// that those accesses are conflict-free.
+template <int E>
+__device__ void block_bitonic(unsigned long long (&k)[E], int (&x)[E], unsigned long long* skey,
+                              int* sidx) {
+  constexpr int P = 256 * E;
+  const int tid = threadIdx.x;
+  for (int kk = 2; kk <= P; kk <<= 1) {
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      if (j < E) {
+        if (j == 1) bitonic_intra<E, 1>(k, x, kk);
+        if constexpr (E > 2) if (j == 2) bitonic_intra<E, (E > 2 ? 2 : 1)>(k, x, kk);
+        if constexpr (E > 4) if (j == 4) bitonic_intra<E, (E > 4 ? 4 : 1)>(k, x, kk);
+      } else if (j < 32 * E) {
+        const int d = j / E;        // partner thread within the warp
+        const bool lower = (tid & d) == 0;
+#pragma unroll
+        for (int u = 0; u < E; ++u) {
+          const unsigned long long ko = __shfl_xor_sync(0xffffffffu, k[u], d);
+          const int xo = __shfl_xor_sync(0xffffffffu, x[u], d);
+          bitonic_keep(k[u], x[u], ko, xo, lower, ((E * tid + u) & kk) == 0);
         }
-        sh.prefix = P | (static_cast<unsigned long long>(d) << shift);
-        sh.need = need - int(c);
-        sh.gc = int(sh.hist[d]);
-      }
-    }
-    __syncthreads();
-    P = sh.prefix;
-    need = sh.need;
-    gc = sh.gc;
-    if (gc == need || gc <= 32 || shift == 0) break;
-  }
-  // mode 2: the whole prefix group is taken; mode 1: threshold (tk, ti) of the
-  // group's need-th member; mode 0: key < P, then ties of P in position order.
-  int mode = gc == need ? 2 : (gc <= 32 ? 1 : 0);
-  unsigned long long tk = 0ull;
-  int ti = 0;
-  if (mode == 1) {
-    for (int base = 0; base < count; base += blockDim.x) {
-      const int i = base + tid;
-      const bool g = i < count && ((key[i] ^ P) >> shift) == 0ull;
-      const unsigned gm = __ballot_sync(0xffffffffu, g);
-      int at = 0;
-      if (lane == 0 && gm) at = atomicAdd(&sh.gcount, __popc(gm));
-      at = __shfl_sync(0xffffffffu, at, 0);
-      if (g) {
-        const int pos = at + __popc(gm & lt);
-        if (pos < 32) { sh.gkey[pos] = key[i]; sh.gidx[pos] = i; }
-      }
-    }
-    __syncthreads();
-    if (warp == 0) {
-      const int n = min(gc, 32);
-      if (lane < n) {
-        const unsigned long long kg = sh.gkey[lane];
-        const int ig = sh.gidx[lane];
-        int rank = 0;
-        for (int h = 0; h < n; ++h) {
-          const unsigned long long kh = sh.gkey[h];
-          rank += (kh < kg || (kh == kg && sh.gidx[h] < ig)) ? 1 : 0;
+      } else {
+        const int d = j / E;        // partner thread in another warp
+        __syncthreads();            // the previous exchange has been read
+#pragma unroll
+        for (int u = 0; u < E; ++u) {
+          skey[u * 256 + tid] = k[u];
+          sidx[u * 256 + tid] = x[u];
         }
-        if (rank == need - 1) { sh.tk = kg; sh.ti = ig; }
+        __syncthreads();
+        const bool lower = (tid & d) == 0;
+#pragma unroll
+        for (int u = 0; u < E; ++u)
+          bitonic_keep(k[u], x[u], skey[u * 256 + (tid ^ d)], sidx[u * 256 + (tid ^ d)], lower,
+                       ((E * tid + u) & kk) == 0);
       }
     }
-    __syncthreads();
-    tk = sh.tk;
-    ti = sh.ti;
   }
-  const int per = ((count + 32 * nw - 1) / (32 * nw)) * 32;
-  const int lo = warp * per, hi = min(count, lo + per);
-  auto flags = [&](int i, bool& less, bool& eq) {
-    less = eq = false;
-    if (i >= hi) return;
-    const unsigned long long kk = key[i];
-    if (mode == 2) less = (kk >> shift) <= (P >> shift);
-    else if (mode == 1) less = kk < tk || (kk == tk && i <= ti);
-    else { less = kk < P; eq = kk == P; }
-  };
-  unsigned cl = 0, ce = 0;
-  for (int base = lo; base < hi; base += 32) {
-    bool less, eq;
-    flags(base + lane, less, eq);
-    cl += __popc(__ballot_sync(0xffffffffu, less));
-    ce += __popc(__ballot_sync(0xffffffffu, eq));
+  __syncthreads();   // the scratch arrays are free again
+}
+
+// ConstraintEliteSet (the n_c lowest (r key, index)) staged in sh.ckey /
+// sh.idx [0..n_c), padded to P2 (a power of two, >= 256).
+template <int E>
+__device__ void small_constraint_set(const double* r, const double* cu, int B, int n_c, int P2,
+                                     SmallSel& sh) {
+  unsigned long long k[E];
+  int x[E];
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < E; ++u) {
+    const int e = E * tid + u;
+    k[u] = e < B ? ord_key(r[e]) : ~0ull;    // padding sorts last
+    x[u] = e;
   }
-  if (lane == 0) { sh.wl[warp] = cl; sh.we[warp] = ce; }
-  __syncthreads();
-  int lb = 0, eb = 0;
-  for (int w = 0; w < warp; ++w) { lb += int(sh.wl[w]); eb += int(sh.we[w]); }
-  int sel = lb + min(eb, need), ties = eb;
-  for (int base = lo; base < hi; base += 32) {
-    const int i = base + lane;
-    bool less, eq;
-    flags(i, less, eq);
-    const unsigned em = __ballot_sync(0xffffffffu, eq);
-    const bool take = less || (eq && ties + __popc(em & lt) < need);
-    const unsigned tm = __ballot_sync(0xffffffffu, take);
-    const int pos = sel + __popc(tm & lt);
-    if (take && pos < k) out[pos] = i;
-    ties += __popc(em);
-    sel += __popc(tm);
+  block_bitonic<E>(k, x, sh.key, sh.kidx);
+#pragma unroll
+  for (int u = 0; u < E; ++u) {
+    const int e = E * tid + u;
+    if (e < n_c) {
+      sh.ckey[e] = ord_key(cu[x[u]] + r[x[u]]);
+      sh.idx[e] = x[u];
+    }
+  }
+  for (int e = n_c + tid; e < P2; e += blockDim.x) {
+    sh.ckey[e] = ~0ull;
+    sh.idx[e] = B + e;
   }
   __syncthreads();
 }
 
-// ConstraintEliteSet into sh.cand[0..n_c), EliteSet sorted into sh.idx[0..q).
+// EliteSet: the candidates sorted by (cost key, index), the first q into sh.idx.
+template <int E>
+__device__ void small_elite_set(int q, SmallSel& sh) {
+  unsigned long long k[E];
+  int x[E];
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < E; ++u) {
+    k[u] = sh.ckey[E * tid + u];
+    x[u] = sh.idx[E * tid + u];
+  }
+  block_bitonic<E>(k, x, sh.key, sh.kidx);   // ends with a barrier: sh.idx is free
+#pragma unroll
+  for (int u = 0; u < E; ++u)
+    if (E * tid + u < q) sh.idx[E * tid + u] = x[u];
+  __syncthreads();
+}
+
+// ConstraintEliteSet, then the EliteSet sorted into sh.idx[0..q) (blockDim.x = 256).
 __device__ void small_elites(const double* r, const double* cu, int B, int n_c, int q,
                              SmallSel& sh) {
-  for (int i = threadIdx.x; i < B; i += blockDim.x) sh.key[i] = ord_key(r[i]);
-  __syncthreads();
-  small_select(sh.key, B, n_c, sh.cand, sh);
-  for (int c = threadIdx.x; c < n_c; c += blockDim.x) {
-    const int id = sh.cand[c];
-    sh.ckey[c] = ord_key(cu[id] + r[id]);
+  int P = 256;
+  while (P < B) P <<= 1;
+  int P2 = 256;
+  while (P2 < n_c) P2 <<= 1;
+  switch (P) {
+    case 256: small_constraint_set<1>(r, cu, B, n_c, P2, sh); break;
+    case 512: small_constraint_set<2>(r, cu, B, n_c, P2, sh); break;
+    case 1024: small_constraint_set<4>(r, cu, B, n_c, P2, sh); break;
+    default: small_constraint_set<8>(r, cu, B, n_c, P2, sh); break;
   }
-  __syncthreads();
-  // candidates are in increasing sample index: rank by (cost key, position)
-  for (int c = threadIdx.x; c < n_c; c += blockDim.x) {
-    const unsigned long long kc = sh.ckey[c];
-    int rank = 0;
-    for (int h = 0; h < n_c; ++h) {
-      const unsigned long long kh = sh.ckey[h];
-      rank += (kh < kc || (kh == kc && h < c)) ? 1 : 0;
+  if (n_c <= 256) {
+    // few candidates: each one's rank is the number of (cost key, index)
+    // pairs below it (no barriers); ranks are distinct since indices are
+    const int tid = threadIdx.x;
+    if (tid < n_c) {
+      const unsigned long long kc = sh.ckey[tid];
+      const int ic = sh.idx[tid];
+      int r0 = 0, r1 = 0, r2 = 0, r3 = 0;   // independent counts hide the load latency
+      int h = 0;
+      for (; h + 4 <= n_c; h += 4) {
+        r0 += pair_gt(kc, ic, sh.ckey[h], sh.idx[h]) ? 1 : 0;
+        r1 += pair_gt(kc, ic, sh.ckey[h + 1], sh.idx[h + 1]) ? 1 : 0;
+        r2 += pair_gt(kc, ic, sh.ckey[h + 2], sh.idx[h + 2]) ? 1 : 0;
+        r3 += pair_gt(kc, ic, sh.ckey[h + 3], sh.idx[h + 3]) ? 1 : 0;
+      }
+      for (; h < n_c; ++h) r0 += pair_gt(kc, ic, sh.ckey[h], sh.idx[h]) ? 1 : 0;
+      const int rank = (r0 + r1) + (r2 + r3);
+      if (rank < q) sh.kidx[rank] = ic;
     }
-    if (rank < q) sh.idx[rank] = sh.cand[c];
+    __syncthreads();
+    for (int e = tid; e < q; e += blockDim.x) sh.idx[e] = sh.kidx[e];
+    __syncthreads();
+    return;
   }
-  __syncthreads();
+  switch (P2) {
+    case 512: small_elite_set<2>(q, sh); break;
+    default: small_elite_set<4>(q, sh); break;
+  }
 }
 
 __global__ void __launch_bounds__(kSmallThreads)
@@ -574,9 +573,8 @@ select_update_small_kernel(const Layout* layout, DevCem* cem, int l, Params prm,
   auto id_of = [&](int e) { const int id = sh.idx[e]; return (id >= 0 && id < B) ? id : 0; };
   auto p_e = [&](int e, int a) { return ps[size_t(id_of(e)) * d_p + a]; };
   auto c_e = [&](int e) { return cs[id_of(e)] + rs[id_of(e)]; };
-  // the order keys are no longer needed: their space stages the elite rows
   update_moments(p_e, c_e, c_e(0), q, d_p, prm.gamma, prm.eta, st.mu, st.sigma, kMaxDp, sh.sw,
-                 sh.acc, reinterpret_cast<double*>(sh.key), int(sizeof(sh.key) / sizeof(double)));
+                 sh.acc);
   const int best = id_of(0);
   if (threadIdx.x == 0) {
     cholesky(st.sigma, prm.cov_eps, d_p, st.chol);

@@ -17,7 +17,9 @@ pytestmark = pytest.mark.gpu
                                           (1000, 150, 50, False), (5000, 2048, 700, True),
                                           (40000, 150, 50, True), (64, 64, 64, True),
                                           (2048, 1024, 300, False), (2048, 1000, 1000, True),
-                                          (2049, 1024, 300, False), (100, 40, 10, "group")])
+                                          (2049, 1024, 300, False), (100, 40, 10, "group"),
+                                          (1500, 400, 120, True), (300, 256, 100, False),
+                                          (257, 257, 3, True)])
 def test_select_elites_bit_exact(B, n_c, q, ties):
     s = sg.Stream(B * 31 + n_c)
     if ties == "group":
