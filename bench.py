@@ -317,29 +317,44 @@ def gpu_arm(args):
         fresh(i)
         pl.step_resident([B])
     barrier()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    with ClockSampler(local) as clk:
-        barrier()
-        for i in range(args.steps):
-            flush.zero_()
-            fresh(args.warmup + i)
-            starts[i].record(stream)
-            pl.step_resident([B])
-            ends[i].record(stream)
-        barrier()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+
+    def measure():
+        # the timed cycles, then the latency run; the clock sampler covers both
+        # so that its 200 ms samples fall inside device-timed work
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        with ClockSampler(local) as clk:
+            barrier()
+            for i in range(args.steps):
+                flush.zero_()
+                fresh(args.warmup + i)
+                starts[i].record(stream)
+                pl.step_resident([B])
+                ends[i].record(stream)
+            barrier()
+            # ---- latency: per-cycle device time over many cycles after 50 warm-up cycles
+            lat = []
+            if args.latency_cycles > 0:
+                for i in range(50):
+                    fresh(i)
+                    pl.step_resident([B])
+                lat = _timed(lambda: pl.step_resident([B]), args.latency_cycles, flush, stream,
+                             prep=fresh)
+        return [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)], lat, clk.summary()
+
+    step_ms, lat_ms, clocks = measure()
+    bad = bool(clocks) and bool(
+        set(clocks["reasons"]) & {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
+        or (not clocks["reasons"] and clocks["sm_mhz"] < 0.9 * clocks["sm_max_mhz"]))
+    remeasured = False
+    if ranks.max(1.0 if bad else 0.0) > 0.5:      # decided together: measure() has barriers
+        # a slowdown, or clocks held below their maximum with no reason: measure once more
+        step_ms, lat_ms, clocks = measure()
+        remeasured = True
+    if clocks is not None:
+        clocks["remeasured"] = remeasured
     total_s = ranks.max(sum(step_ms) / 1e3)
     value = replica_value(units, args.steps, total_s, world)
-    clocks = clk.summary()
-
-    # ---- latency: per-cycle device time over many cycles after 50 warm-up cycles
-    lat_ms = []
-    if args.latency_cycles > 0:
-        for i in range(50):
-            fresh(i)
-            pl.step_resident([B])
-        lat_ms = _timed(lambda: pl.step_resident([B]), args.latency_cycles, flush, stream, prep=fresh)
 
     # ---- e2e: through host buffers (plan_step), wall clock per cycle
     e2e_ms = []
