@@ -615,7 +615,7 @@ def serving_arm(args):
     from paper_2212_02224_gb300 import scenegen as sg
     from paper_2212_02224_gb300.planner import Server, advance
     prm, _, _ = sg.workload(1)
-    srv = Server(prm, max_obs=24, max_samples=16384, max_scenes=32, max_executors=8,
+    srv = Server(prm, max_obs=24, max_samples=16384, max_scenes=32, max_executors=args.executors,
                  device_budget=16 << 30, max_episodes=4096)
     rng = np.random.default_rng(11)
     s = sg.Stream(4242)
@@ -623,13 +623,14 @@ def serving_arm(args):
     eps = []
     for e in range(n_ep):
         sc = sg.make_scene(50000 + e, n_lanes=4, n_obs=int(s.integers(4, 24, 1)[0]))
-        eps.append(dict(id=e, scene=sc, B=int(s.integers(512, 2048, 1)[0]),
+        eps.append(dict(id=e, scene=sc, B=int(s.integers(args.serve_b[0], args.serve_b[1], 1)[0]),
                         m=int(rng.choice([80, 100, 125, 150])), cycle=0, busy=False, ticket=None))
     # warm the executors (one per horizon) before timing
     for m in (80, 100, 125, 150):
         srv.wait(srv.submit(eps[0]["scene"], 512, m=m, episode=10**9 + m, seed=1))
         srv.end_episode(10**9 + m)
     lat, done_units = [], 0
+    by_ticket = {}
     t0 = time.perf_counter()
     next_arrival = t0
     duration = args.serve_seconds
@@ -637,7 +638,7 @@ def serving_arm(args):
     next_ep_id = n_ep
     while True:
         now = time.perf_counter()
-        if now - t0 > duration and all(not e["busy"] for e in eps):
+        if now - t0 > duration and not by_ticket:
             break
         while now >= next_arrival and next_arrival - t0 <= duration:
             # every arrival that is due (the loop may fall behind the arrival clock)
@@ -646,27 +647,31 @@ def serving_arm(args):
                 e = idle[rng.integers(len(idle))]
                 e["ticket"] = srv.submit(e["scene"], e["B"], m=e["m"], episode=e["id"], seed=e["id"])
                 e["busy"] = True
+                by_ticket[e["ticket"]] = e
                 submitted += 1
             else:
                 dropped += 1
             next_arrival += rng.exponential(1.0 / args.rate)
-        for e in eps:
-            if e["busy"]:
-                r = srv.poll(e["ticket"], 0)
-                if r is not None:
-                    e["busy"] = False
-                    completed += 1
-                    lat.append(r["latency_us"] / 1e3)
-                    done_units += e["B"] * prm.inner_iters * prm.outer_iters
-                    e["cycle"] += 1
-                    if e["cycle"] >= 50:              # episode over: a new vehicle takes the slot
-                        srv.end_episode(e["id"])
-                        e["id"], e["cycle"] = next_ep_id, 0
-                        next_ep_id += 1
-                        e["scene"] = sg.make_scene(60000 + e["id"], n_lanes=4,
-                                                   n_obs=int(s.integers(4, 24, 1)[0]))
-                    else:
-                        e["scene"] = advance(prm, e["scene"], r["xi"])
+        # block on the server's completions until the next arrival is due
+        wait_us = int(max(0.0, min(next_arrival - time.perf_counter(), 0.005)) * 1e6)
+        got = srv.poll_any(wait_us)
+        while got is not None:
+            ticket, r = got
+            e = by_ticket.pop(ticket)
+            e["busy"] = False
+            completed += 1
+            lat.append(r["latency_us"] / 1e3)
+            done_units += e["B"] * prm.inner_iters * prm.outer_iters
+            e["cycle"] += 1
+            if e["cycle"] >= 50:              # episode over: a new vehicle takes the slot
+                srv.end_episode(e["id"])
+                e["id"], e["cycle"] = next_ep_id, 0
+                next_ep_id += 1
+                e["scene"] = sg.make_scene(60000 + e["id"], n_lanes=4,
+                                           n_obs=int(s.integers(4, 24, 1)[0]))
+            else:
+                e["scene"] = advance(prm, e["scene"], r["xi"])
+            got = srv.poll_any(0)
     wall = time.perf_counter() - t0
     info = srv.info()
     srv.close()
@@ -695,6 +700,9 @@ def main():
     ap.add_argument("--workload", default="dense", choices=["dense", "batched", "scale", "serving"])
     ap.add_argument("--rate", type=float, default=200.0, help="serving: requests per second")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
+    ap.add_argument("--executors", type=int, default=16, help="serving: planner contexts")
+    ap.add_argument("--serve-b", type=int, nargs=2, default=[512, 2048],
+                    help="serving: range of samples per request")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

@@ -305,6 +305,14 @@ int plan_submit(plan_server* srv, const plan_request* req, uint64_t* ticket);
 int plan_poll(plan_server* srv, uint64_t ticket, plan_result* out, double* latency_us,
               int timeout_us);
 
+/* Wait up to timeout_us for any ticket to complete and take the one that
+ * completed first: *ticket names it, and *out / *latency_us / the return
+ * value are those plan_poll would give for it.  ETIMEOUT: none completed in
+ * time (*ticket is untouched).  EINVAL: srv or ticket is NULL.  Lets a client
+ * serve many episodes from one wait instead of polling each ticket. */
+int plan_poll_any(plan_server* srv, uint64_t* ticket, plan_result* out, double* latency_us,
+                  int timeout_us);
+
 /* Release an episode's warm-start row (no request of it may be pending). */
 int plan_end_episode(plan_server* srv, uint64_t episode);
 

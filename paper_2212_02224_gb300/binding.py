@@ -88,7 +88,7 @@ EXPORTS = ("plan_init", "plan_destroy", "plan_status_str", "plan_last_error", "p
            "plan_step_resident", "plan_get_result", "plan_step", "plan_select_elites",
            "plan_update_distribution", "plan_sample", "plan_set_tuning", "plan_autotune",
            "plan_solve_fp64_noalloc", "plan_advance", "plan_server_create", "plan_server_destroy",
-           "plan_submit", "plan_poll", "plan_end_episode", "plan_server_info",
+           "plan_submit", "plan_poll", "plan_poll_any", "plan_end_episode", "plan_server_info",
            "plan_qp_forward", "plan_qp_backward", "plan_probe_alu")
 
 _lib = None
@@ -136,6 +136,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "plan_server_destroy": (I, [V]),
         "plan_submit": (I, [V, P(PlanRequest), P(U64)]),
         "plan_poll": (I, [V, U64, P(PlanResult), P(D), I]),
+        "plan_poll_any": (I, [V, P(U64), P(PlanResult), P(D), I]),
         "plan_end_episode": (I, [V, U64]),
         "plan_server_info": (I, [V, P(PlanServerStats)]),
         "plan_qp_forward": (I, [V, V, V, I, V, V]),
@@ -405,6 +406,21 @@ def plan_poll(srv, ticket: int, timeout_us: int):
     if st not in (PLAN_OK, PLAN_ETIMEOUT):
         check(st, None)
     return st, out, lat.value
+
+
+def plan_poll_any(srv, timeout_us: int):
+    """(status, ticket, PlanResult, latency_us) of the first completed ticket;
+    status PLAN_ETIMEOUT (ticket None) means none completed in time."""
+    out = PlanResult()
+    lat = ctypes.c_double()
+    t = ctypes.c_uint64()
+    st = load().plan_poll_any(srv, ctypes.byref(t), ctypes.byref(out), ctypes.byref(lat),
+                              int(timeout_us))
+    if st == PLAN_ETIMEOUT:
+        return st, None, out, 0.0
+    if st != PLAN_OK:
+        check(st, None)
+    return st, t.value, out, lat.value
 
 
 def plan_end_episode(srv, episode: int):

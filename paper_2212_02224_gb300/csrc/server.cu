@@ -86,6 +86,7 @@ struct plan_server {
   std::condition_variable cv_done;   // ticket completions
   std::deque<Request> pending;
   std::unordered_map<uint64_t, Ticket> tickets;
+  std::deque<uint64_t> done_q;       // completed tickets in completion order
   uint64_t next_ticket = 1;
   std::vector<std::unique_ptr<Executor>> execs;
   std::thread worker;
@@ -159,6 +160,7 @@ void finalize(plan_server* s, Executor* e) {
     tk.t_done = t;
     tk.done = true;
     ++s->n_done;
+    s->done_q.push_back(e->wave[i].ticket);
   }
   e->wave.clear();
   e->busy = false;
@@ -212,6 +214,7 @@ bool launch_wave(plan_server* s, Executor* e) {
       tk.status = st;
       tk.done = true;
       tk.t_done = t;
+      s->done_q.push_back(r.ticket);
     }
     s->err = ctx_error(e->ctx);
     e->wave.clear();
@@ -383,6 +386,35 @@ int plan_poll(plan_server* s, uint64_t ticket, plan_result* out, double* latency
   }
   const Ticket tk = it->second;
   s->tickets.erase(it);
+  if (out) *out = tk.res;
+  if (latency_us) *latency_us = tk.t_done - tk.t_submit;
+  return tk.status;
+}
+
+int plan_poll_any(plan_server* s, uint64_t* ticket, plan_result* out, double* latency_us,
+                  int timeout_us) {
+  if (!s || !ticket) return PLAN_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  const auto deadline = std::chrono::steady_clock::now() +
+                        std::chrono::microseconds(timeout_us > 0 ? timeout_us : 0);
+  for (;;) {
+    // tickets already taken by plan_poll are stale entries: drop them
+    while (!s->done_q.empty() && s->tickets.find(s->done_q.front()) == s->tickets.end())
+      s->done_q.pop_front();
+    if (!s->done_q.empty()) break;
+    if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
+      while (!s->done_q.empty() && s->tickets.find(s->done_q.front()) == s->tickets.end())
+        s->done_q.pop_front();
+      if (s->done_q.empty()) return PLAN_ETIMEOUT;
+      break;
+    }
+  }
+  const uint64_t id = s->done_q.front();
+  s->done_q.pop_front();
+  auto it = s->tickets.find(id);
+  const Ticket tk = it->second;
+  s->tickets.erase(it);
+  *ticket = id;
   if (out) *out = tk.res;
   if (latency_us) *latency_us = tk.t_done - tk.t_submit;
   return tk.status;

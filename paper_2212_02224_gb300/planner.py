@@ -200,6 +200,15 @@ class Server:
         return dict(p=list(r.p[:self.d_p]), xi=list(r.xi[:2 * self.n]), cost=r.cost,
                     resid=r.resid, cu=r.cu, index=r.index, latency_us=lat)
 
+    def poll_any(self, timeout_us: int = 0):
+        """(ticket, result) of the first completed request, or None after
+        timeout_us without a completion."""
+        st, t, r, lat = B.plan_poll_any(self.srv, timeout_us)
+        if st == B.PLAN_ETIMEOUT:
+            return None
+        return t, dict(p=list(r.p[:self.d_p]), xi=list(r.xi[:2 * self.n]), cost=r.cost,
+                       resid=r.resid, cu=r.cu, index=r.index, latency_us=lat)
+
     def wait(self, ticket: int, timeout_s: float = 60.0):
         import time
         t_end = time.time() + timeout_s

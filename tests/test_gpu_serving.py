@@ -138,3 +138,32 @@ def test_server_errors():
         binding.plan_poll(srv.srv, 123456, 0)                # unknown ticket
     assert e.value.status == binding.PLAN_EINVAL
     srv.close()
+
+
+def test_poll_any_returns_every_ticket_once():
+    """plan_poll_any hands out completed tickets in completion order; tickets
+    already taken by plan_poll are skipped; results equal those of plan_poll."""
+    prm = _prm()
+    srv = Server(prm, max_obs=24, max_samples=4096, max_scenes=8, max_executors=2)
+    scenes = [_scene(20 + i) for i in range(9)]
+    tickets = [srv.submit(sc, 200 + 37 * i, episode=300 + i, seed=i) for i, sc in enumerate(scenes)]
+    direct = srv.wait(tickets[4])                  # one ticket taken by plan_poll
+    got = {}
+    while len(got) < len(tickets) - 1:
+        r = srv.poll_any(2_000_000)
+        assert r is not None, "no completion within 2 s"
+        t, res = r
+        assert t not in got and t != tickets[4]
+        got[t] = res
+    assert set(got) == set(tickets) - {tickets[4]}
+    assert srv.poll_any(0) is None                 # nothing left
+    srv.close()
+    assert all(np.isfinite(v["cost"]) for v in got.values()) and np.isfinite(direct["cost"])
+    # the same requests through plan_poll give the same results
+    srv = Server(prm, max_obs=24, max_samples=4096, max_scenes=8, max_executors=2)
+    again = [srv.submit(sc, 200 + 37 * i, episode=300 + i, seed=i) for i, sc in enumerate(scenes)]
+    for t0, t1 in zip(tickets, again):
+        r1 = srv.wait(t1)
+        r0 = direct if t0 == tickets[4] else got[t0]
+        assert r1["index"] == r0["index"] and r1["cost"] == r0["cost"]
+    srv.close()
