@@ -104,7 +104,9 @@ void CUDART_CB on_wave_done(void* arg) {
   e->srv->cv.notify_all();
 }
 
-int create_executor(plan_server* s, int m, Executor** out) {
+// A new executor for horizon m (called without the lock: plan_init allocates
+// and builds constants; the caller adds it to the server under the lock).
+int make_executor(plan_server* s, int m, std::unique_ptr<Executor>* out) {
   plan_config cfg = s->base;
   cfg.m = m;
   plan_ctx* ctx = nullptr;
@@ -135,9 +137,7 @@ int create_executor(plan_server* s, int m, Executor** out) {
     plan_destroy(ctx);
     return PLAN_ENOMEM;
   }
-  s->bytes_used += e->bytes;
-  *out = e.get();
-  s->execs.push_back(std::move(e));
+  *out = std::move(e);
   return PLAN_OK;
 }
 
@@ -168,9 +168,9 @@ void finalize(plan_server* s, Executor* e) {
   s->cv_done.notify_all();
 }
 
-// Fill and launch a wave on an idle executor from the pending queue (caller
-// holds the lock).  Returns false if nothing was launched.
-bool launch_wave(plan_server* s, Executor* e) {
+// Move pending requests of the executor's horizon into its wave and mark it
+// busy (caller holds the lock).  Returns the wave's size.
+int take_wave(plan_server* s, Executor* e) {
   const int cap_s = s->base.max_scenes, cap_b = s->base.max_samples;
   int samples = 0;
   for (auto it = s->pending.begin(); it != s->pending.end() && int(e->wave.size()) < cap_s;) {
@@ -182,13 +182,20 @@ bool launch_wave(plan_server* s, Executor* e) {
       ++it;
     }
   }
+  if (!e->wave.empty()) e->busy = true;
+  return int(e->wave.size());
+}
+
+// Upload and launch a taken wave (called without the lock: it reads only the
+// executor's own wave and buffers; waves of different executors hold
+// different episodes, so their table rows do not overlap).
+int run_wave(plan_server* s, Executor* e) {
   const int S = int(e->wave.size());
-  if (S == 0) return false;
   std::vector<plan_scene> scenes(S);
   std::vector<int> B(S), gather(S), scatter(S);
   int st = PLAN_OK;
   for (int i = 0; i < S && st == PLAN_OK; ++i) {
-    Request& r = e->wave[i];
+    const Request& r = e->wave[i];
     scenes[i] = r.scene;
     scenes[i].obs = r.obs.empty() ? nullptr : r.obs.data();
     scenes[i].road = r.road.empty() ? nullptr : r.road.data();
@@ -207,6 +214,11 @@ bool launch_wave(plan_server* s, Executor* e) {
     cudaGetLastError();
     st = PLAN_ECUDA;
   }
+  return st;
+}
+
+// Book a launched wave, or fail its tickets (caller holds the lock).
+void post_wave(plan_server* s, Executor* e, int st) {
   if (st != PLAN_OK) {
     const double t = now_us();
     for (auto& r : e->wave) {
@@ -218,41 +230,86 @@ bool launch_wave(plan_server* s, Executor* e) {
     }
     s->err = ctx_error(e->ctx);
     e->wave.clear();
+    e->busy = false;
     s->cv_done.notify_all();
-    return false;
+    return;
   }
-  e->busy = true;
   ++s->n_waves;
-  s->max_wave = std::max<uint64_t>(s->max_wave, uint64_t(S));
-  return true;
+  s->max_wave = std::max<uint64_t>(s->max_wave, uint64_t(e->wave.size()));
 }
 
+// Fail the pending requests of horizon m (no executor could be made for it).
+void fail_pending(plan_server* s, int m, int st) {
+  const double t = now_us();
+  for (auto it = s->pending.begin(); it != s->pending.end();) {
+    if (it->m == m) {
+      Ticket& tk = s->tickets[it->ticket];
+      tk.status = st;
+      tk.done = true;
+      tk.t_done = t;
+      s->done_q.push_back(it->ticket);
+      it = s->pending.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  s->cv_done.notify_all();
+}
+
+// The scheduler thread.  It holds the lock only to pick work and to book it:
+// a wave's uploads and launches and the creation of an executor run unlocked,
+// so that submissions and polls are not held up behind CUDA calls.
 void scheduler(plan_server* s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
   while (!s->stop) {
     for (auto& e : s->execs)
       if (e->busy && e->done.load()) finalize(s, e.get());
-    // admit pending requests, oldest first
-    bool progress = true;
-    while (progress && !s->pending.empty()) {
-      progress = false;
+    // admit pending requests, oldest first, one wave or one new executor at a
+    // time (the queue may change while unlocked: rescan after each)
+    while (!s->stop) {
+      Executor* idle = nullptr;
+      int want_m = -1;
       std::vector<int> tried;
       for (const Request& r : s->pending) {
         if (std::find(tried.begin(), tried.end(), r.m) != tried.end()) continue;
         tried.push_back(r.m);
-        Executor* idle = nullptr;
         for (auto& e : s->execs)
           if (!e->busy && e->m == r.m) { idle = e.get(); break; }
-        if (!idle && int(s->execs.size()) < s->max_exec) {
+        if (idle) break;
+        if (want_m < 0 && int(s->execs.size()) < s->max_exec) {
           // admission by memory: estimate from an executor of any horizon
-          size_t est = s->execs.empty() ? 0 : s->execs.front()->bytes;
-          if (s->bytes_used + est <= s->budget) {
-            if (create_executor(s, r.m, &idle) != PLAN_OK) idle = nullptr;
-          }
+          const size_t est = s->execs.empty() ? 0 : s->execs.front()->bytes;
+          if (s->bytes_used + est <= s->budget) want_m = r.m;
         }
-        if (idle && launch_wave(s, idle)) { progress = true; break; }
       }
+      if (idle) {
+        if (take_wave(s, idle) == 0) break;
+        lk.unlock();
+        const int st = run_wave(s, idle);
+        lk.lock();
+        post_wave(s, idle, st);
+        continue;
+      }
+      if (want_m >= 0) {
+        lk.unlock();
+        std::unique_ptr<Executor> e;
+        const int st = make_executor(s, want_m, &e);
+        lk.lock();
+        if (st == PLAN_OK) {
+          s->bytes_used += e->bytes;
+          s->execs.push_back(std::move(e));
+          continue;
+        }
+        // no more executors; requests of a horizon without one cannot run
+        s->max_exec = int(s->execs.size());
+        s->err = "could not create an executor";
+        bool have = false;
+        for (auto& x : s->execs) have |= x->m == want_m;
+        if (!have) fail_pending(s, want_m, st);
+        continue;
+      }
+      break;
     }
     bool busy = false;
     for (auto& e : s->execs) busy |= e->busy;
