@@ -115,7 +115,7 @@ int make_executor(plan_server* s, int m, std::unique_ptr<Executor>* out) {
   // a fixed kernel shape per executor: a scene's arithmetic must not depend on
   // how many other samples share its wave
   if (cfg.prec == PLAN_PREC_FP32) {
-    st = m > 128 ? plan_set_tuning(ctx, 2, 1) : plan_set_tuning(ctx, 1, 4);
+    st = m > 128 ? plan_set_tuning(ctx, 2, 2) : plan_set_tuning(ctx, 1, 4);
     if (st != PLAN_OK) {
       plan_destroy(ctx);
       return st;
