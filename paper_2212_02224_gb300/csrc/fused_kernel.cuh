@@ -115,8 +115,8 @@ __device__ __forceinline__ void group_barrier(int grp, int nthreads) {
 // One sample per group of WPS warps (32 WPS lanes); a CTA holds blockDim.x /
 // (32 WPS) groups (up to 4 with two warps per sample, one with four).  Larger
 // CTAs share one staged copy of the basis among more samples.  Timestep t = s * 32 WPS +
-// (warp-in-group) * 32 + lane for slot s; lanes with t >= m compute on the
-// last timestep's data and contribute nothing.
+// (warp-in-group) * 32 + lane for slot s; lanes with t >= m read a zero basis
+// row, sit far from every obstacle and contribute nothing.
 template <int NC, int SLOTS, int WPS, bool ROAD>
 struct RegCap {
   // registers per thread: one timestep slot per 32 lanes needs about 70, the
@@ -218,6 +218,10 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     ib_max = fmaxf(ib_max, __shfl_xor_sync(kFull, ib_max, o));
   }
   float moved = 0.f;   // bound on the scaled movement of any point since iteration 0
+  // warp maximum of the last xi-step's scaled movement; it is added to `moved`
+  // just before the next obstacle test, so the reduction's latency overlaps the
+  // kinematics of the next iteration
+  float moved_step = 0.f;
 
   // ---- per-lane coefficient slot: Step 1 and the row of M
   const int axis = lane >> 4, kk = lane & 15;
@@ -278,6 +282,11 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     for (int s = 0; s < SLOTS; ++s) {
       float o[6];
       kin<NC>(sW + tcl[s] * ST, xv, yv, o);
+      // a lane past the horizon is placed 10^15 m down the road: every obstacle
+      // test sees it outside (its scaled squared distance stays finite, far
+      // above 1), so the tests need no per-slot mask.  Its other kinematics
+      // and residual rows stay zero.
+      if (act[s] == 0.f) o[0] = 1.0e15f;
 #pragma unroll
       for (int q = 0; q < 6; ++q) {
         if constexpr (kRegState) rref[s][q] = o[q];
@@ -360,11 +369,15 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       break;
     }
 
+    moved += 1.41422f * moved_step;
     // ---- B: obstacle projection, accumulated residual sum_i (h_o,i - p).
     // For every obstacle within reach, one pass computes the scaled offsets of
-    // all slots, re-arms the obstacle's skip level from the warp minimum of the
-    // scaled distance, and gives the points inside its ellipse (d < 1) the
-    // correction (x - x_o, y - y_o)(1/d - 1).
+    // all slots and gives the points inside its ellipse (d < 1) the correction
+    // (x - x_o, y - y_o)(1/d - 1).  An obstacle that holds a point stays within
+    // reach for the next iteration whatever its exact level (min d < 1), so it
+    // is re-armed without a warp reduction; otherwise its skip level is
+    // re-armed from the warp minimum of the scaled distance.  Either way the
+    // next iteration tests the same obstacles.
     float ex[SLOTS], ey[SLOTS];
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) { ex[s] = 0.f; ey[s] = 0.f; }
@@ -403,25 +416,26 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
         }
 #pragma unroll
         for (int s = 0; s < SLOTS; ++s) {
-          dmin = fminf(dmin, act[s] > 0.f ? d2s[s] : 3.0e38f);
-          in_any |= act[s] > 0.f && d2s[s] < 1.f;
+          dmin = fminf(dmin, d2s[s]);
+          in_any |= d2s[s] < 1.f;
         }
-        // warp minimum of a nonnegative float: integer order of its bits
-        dmin = __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(dmin)));
-        if (lane == 0) thr[i0 + ii] = fast_sqrt(dmin) + moved;
         if (__any_sync(kFull, in_any)) {
+          if (lane == 0) thr[i0 + ii] = -3.0e38f;
 #pragma unroll
           for (int s = 0; s < SLOTS; ++s) {
-            if (act[s] > 0.f && d2s[s] < 1.f) {
-              if (d2s[s] > 0.f) {
-                const float g = rsqrtf(d2s[s]) - 1.f;
-                ex[s] = fmaf(g * q3.x, sxs[s], ex[s]);
-                ey[s] = fmaf(g * q3.y, sys[s], ey[s]);
-              } else {
-                ex[s] += q3.x;     // atan2(0, 0) = 0: h = (x_o + a, y_o)
-              }
-            }
+            // inside (d < 1): scale the offset onto the ellipse; at the centre
+            // atan2(0, 0) = 0 gives h = (x_o + a, y_o); outside: no change
+            const bool in = d2s[s] < 1.f;
+            const bool pos = d2s[s] > 0.f;
+            const float rs = rsqrtf(d2s[s]);
+            const float g = (in && pos) ? rs - 1.f : 0.f;
+            ex[s] = fmaf(g * q3.x, sxs[s], ex[s]) + ((in && !pos) ? q3.x : 0.f);
+            ey[s] = fmaf(g * q3.y, sys[s], ey[s]);
           }
+        } else {
+          // warp minimum of a nonnegative float: integer order of its bits
+          dmin = __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(dmin)));
+          if (lane == 0) thr[i0 + ii] = fast_sqrt(dmin) + moved;
         }
       }
     }
@@ -558,7 +572,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     {
       // scaled bound on how far any point moves in this step
       const float mv = valid ? fabsf(acc_step) * (axis ? ib_max : ia_max) : 0.f;
-      moved += 1.41422f * __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(mv)));
+      moved_step = __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(mv)));
     }
   }
 
