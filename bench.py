@@ -49,8 +49,8 @@ SM_COUNT_NOMINAL = 152
 # (warps per sample, samples per CTA), from the ncu captures summarised in
 # profiles/fused_kernel_dense_traffic_B1000.md (traffic section); must be re-taken when the
 # kernel changes.
-FUSED_TRAFFIC_BYTES = {(1, 1): 102656, (1, 2): 93696, (1, 4): 90112, (1, 8): 88320, (2, 1): 90624,
-                       (4, 1): 97024}
+FUSED_TRAFFIC_BYTES = {(1, 1): 103168, (1, 2): 96000, (1, 4): 91648, (1, 8): 89344, (2, 1): 93440,
+                       (4, 1): 91648}
 
 
 def algorithmic_flops_per_sample_iter(m, n, N, n_eq=3):
