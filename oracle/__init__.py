@@ -28,4 +28,7 @@ forms, invariants of the constraint sets, library routines or brute force.
 The exact values of the Alg. 2 iterates beyond those invariants (a
 non-convex alternating minimisation) have no independent closed form; the
 convex special case (lane bounds only) is pinned against a general QP solve.
+Status of ``lower.solve`` on a general scene: parity unpinned for the exact
+iterate values (only the invariants above and the oracle-vs-GPU agreement
+hold them); every other function is pinned.
 """

@@ -27,6 +27,13 @@ Readings of the paper adopted here:
     lambda <- lambda - rho/2 F^T (F xi - h) - rho/2 G^T (G xi - e + s).
   * Alg. 2 start: xi^0 = xi_bar, lambda^0 = 0, d_a^{-1} = min(|a(xi^0)|, a_max),
     then alpha^0, d^0, s^0 from xi^0 by the same steps as an iteration.
+
+Pins: Step 1, the projections, the slack, the xi-step and the scoring are
+pinned by closed forms and invariants (tests/test_oracle_lower.py).  The
+exact iterate values of Alg. 2 on a general non-convex scene are parity
+unpinned: beyond its invariants (A xi = b every iteration, the fixed point
+at a feasible xi_bar, the convex lane case) only the oracle-vs-GPU agreement
+holds them.
 """
 from __future__ import annotations
 
