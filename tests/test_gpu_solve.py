@@ -83,6 +83,44 @@ def test_edge_cases(prec, case):
     compare(prec, prm, *_run(prec, prm, sc, p, max_obs=max(sc.n_obs, 1)), *_oracle(prm, sc, p))
 
 
+@pytest.mark.parametrize("prec,shape", [("fp64", None), ("fp32", None), ("fp32", (2, 1)),
+                                         ("fp32", (4, 1))])
+def test_maximum_obstacle_count(prec, shape):
+    """64 obstacles, the largest scene the library accepts: the fused kernel
+    walks its obstacle tables in two chunks of 32, and points of the
+    trajectories fall inside obstacles of both chunks."""
+    prm = sg.Params(m=100, n_coef=11, inner_iters=20)
+    sc = scene_with(64064, 4, 64, obs_x=(8.0, 260.0))
+    p = sg.make_samples(65, sc, 40, 1)
+    pl = planner(prm, prec, max_obs=64, max_samples=len(p))
+    if shape:
+        pl.set_tuning(*shape)
+    xi, r, cu = pl.solve(sc, to_dev(p))
+    torch.cuda.synchronize()
+    out = xi.cpu().numpy(), r.cpu().numpy(), cu.cpu().numpy()
+    pl.close()
+    compare(prec, prm, *out, *_oracle(prm, sc, p))
+
+
+@pytest.mark.parametrize("prec,shape", [("fp64", None), ("fp32", None), ("fp32", (1, 8)),
+                                         ("fp32", (2, 4))])
+def test_longest_horizon(prec, shape):
+    """m = 256 timesteps with 16 coefficients, the largest horizon and basis
+    the fused kernel takes: eight full timestep slots per lane for one warp
+    per sample, and the most shared memory per CTA at eight samples per CTA."""
+    prm = sg.Params(m=256, n_coef=16, inner_iters=20)
+    sc = scene_with(256, 4, 10, obs_x=(10.0, 200.0))
+    p = sg.make_samples(257, sc, 16, 1)
+    pl = planner(prm, prec, max_obs=10, max_samples=len(p))
+    if shape:
+        pl.set_tuning(*shape)
+    xi, r, cu = pl.solve(sc, to_dev(p))
+    torch.cuda.synchronize()
+    out = xi.cpu().numpy(), r.cpu().numpy(), cu.cpu().numpy()
+    pl.close()
+    compare(prec, prm, *out, *_oracle(prm, sc, p))
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_batched_scenes_uneven(prec):
     """Several scenes of uneven obstacle and sample counts in one call."""
