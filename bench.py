@@ -498,7 +498,7 @@ def reference_arm(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "parallelism": "none (CPU oracle)"},
         "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
-                         "sample": vals[0]["sample"].replace("40 samples", "20 samples")},
+                         "sample": vals[0]["sample"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
