@@ -181,6 +181,17 @@ class ClockSampler:
                     reasons=reasons, samples=len(rows))
 
 
+def clocks_rejected(clocks) -> bool:
+    """True when a timed region's clock record rejects it: a hardware or thermal
+    slowdown was active, or the SM clock sat below 90 % of its maximum with no
+    reason given (a clock held by an earlier user).  sw_power_cap alone is kept."""
+    if not clocks:
+        return False
+    if set(clocks["reasons"]) & {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}:
+        return True
+    return not clocks["reasons"] and clocks["sm_mhz"] < 0.9 * clocks["sm_max_mhz"]
+
+
 # ----------------------------------------------------------------------------- replicas
 
 class Ranks:
@@ -343,9 +354,7 @@ def gpu_arm(args):
         return [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)], lat, clk.summary()
 
     step_ms, lat_ms, clocks = measure()
-    bad = bool(clocks) and bool(
-        set(clocks["reasons"]) & {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
-        or (not clocks["reasons"] and clocks["sm_mhz"] < 0.9 * clocks["sm_max_mhz"]))
+    bad = clocks_rejected(clocks)
     remeasured = False
     if ranks.max(1.0 if bad else 0.0) > 0.5:      # decided together: measure() has barriers
         # a slowdown, or clocks held below their maximum with no reason: measure once more
