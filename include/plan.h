@@ -394,6 +394,18 @@ int plan_qp_backward(plan_ctx* ctx, const double* g, int B, double* grad_p, doub
  * the roofline's denominators.  Errors: EINVAL (NULL out), ECUDA. */
 int plan_probe_alu(double* out, void* stream);
 
+/* Diagnostic of the bounded waits of the tensor-core solve; the paper has no
+ * counterpart.  Every mbarrier wait of that kernel gives up after a bound;
+ * the kernel then raises an error flag, and the solve calls return
+ * PLAN_ETIMEOUT while the device and every context stay usable.  This call
+ * runs the same wait on an mbarrier that expects one arrival and gets none,
+ * with a bound of wait_us microseconds (1..100000) of SM clock cycles at
+ * 2.1 GHz.  It returns PLAN_ETIMEOUT when the wait gave up, which is the
+ * expected outcome, and PLAN_OK only if the wait completed.  Synchronous on
+ * `stream`; allocates and frees a 4-byte flag.  Errors: EINVAL (wait_us out
+ * of range), ECUDA. */
+int plan_probe_wait_timeout(int wait_us, void* stream);
+
 /* ------------------------------------------------ allocation-free lower level */
 
 /* The float64 lower-level solve of plan_solve (same kernels, same results) for

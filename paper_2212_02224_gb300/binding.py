@@ -89,7 +89,7 @@ EXPORTS = ("plan_init", "plan_destroy", "plan_status_str", "plan_last_error", "p
            "plan_update_distribution", "plan_sample", "plan_set_tuning", "plan_autotune",
            "plan_solve_fp64_noalloc", "plan_advance", "plan_server_create", "plan_server_destroy",
            "plan_submit", "plan_poll", "plan_poll_any", "plan_end_episode", "plan_server_info",
-           "plan_qp_forward", "plan_qp_backward", "plan_probe_alu")
+           "plan_qp_forward", "plan_qp_backward", "plan_probe_alu", "plan_probe_wait_timeout")
 
 _lib = None
 
@@ -142,6 +142,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "plan_qp_forward": (I, [V, V, V, I, V, V]),
         "plan_qp_backward": (I, [V, V, I, V, V, V]),
         "plan_probe_alu": (I, [P(D), V]),
+        "plan_probe_wait_timeout": (I, [I, V]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -325,6 +326,12 @@ def plan_probe_alu(stream: int = 0) -> dict:
     check(load().plan_probe_alu(out, stream), None)
     return dict(fp32_tflops=out[0], fp32x2_tflops=out[1], fp64_tflops=out[2],
                 rsqrt_tops=out[3], sms=int(out[4]))
+
+
+def plan_probe_wait_timeout(wait_us: int, stream: int = 0) -> int:
+    """Run one bounded wait that receives no arrival (see include/plan.h) and
+    return its status: PLAN_ETIMEOUT is the expected outcome."""
+    return int(load().plan_probe_wait_timeout(int(wait_us), stream))
 
 
 def plan_set_tuning(ctx, warps_per_sample: int, samples_per_cta: int):

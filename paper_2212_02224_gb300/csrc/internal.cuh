@@ -190,6 +190,9 @@ cudaError_t launch_tc(int prec, const DevScene* scenes, const Layout* layout, co
                       const Tile* tiles, int n_tiles, const double* p, const Consts& c,
                       const Params& prm, double* xi, double* r, double* cu, int* err,
                       cudaStream_t s);
+// One bounded mbarrier wait that receives no arrival (k_tc.cu): *timed_out = 1
+// when it gave up after `limit` SM cycles.  Synchronous on s.
+cudaError_t wait_probe(long long limit, cudaStream_t s, int* timed_out);
 
 // Arithmetic throughput probe (k_peaks.cu): out[0..4] as plan_probe_alu.
 int probe_alu(double* out, cudaStream_t s);

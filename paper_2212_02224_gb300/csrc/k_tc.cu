@@ -105,8 +105,9 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                :: "r"(bar) : "memory");
 }
 
-// Bounded wait for the phase `parity` of an mbarrier; false after about a second.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait for the phase `parity` of an mbarrier; false after `limit` SM
+// clock cycles (about a second by default).
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit = kWaitCycles) {
   const long long t0 = clock64();
   while (true) {
     uint32_t done;
@@ -114,8 +115,21 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
                  "selp.u32 %0, 1, 0, p;\n\t}\n"
                  : "=r"(done) : "r"(bar), "r"(parity) : "memory");
     if (done) return true;
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
+}
+
+// Diagnostic of the bounded wait: one thread waits for the first phase of an
+// mbarrier that expects one arrival and gets none.  The wait gives up after
+// `limit` cycles and the kernel raises the error flag the solve uses.
+__global__ void wait_probe_kernel(long long limit, int* err) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(smem_addr(&bar), 0, limit)) atomicExch(err, 1);
 }
 
 __device__ __forceinline__ void fence_before() {
@@ -662,6 +676,24 @@ bool tc_supported(int n, int m, int max_obs) {
 }
 
 int tc_samples_per_cta() { return kTcSamples; }
+
+cudaError_t wait_probe(long long limit, cudaStream_t s, int* timed_out) {
+  *timed_out = 0;
+  int* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(int));
+  if (e != cudaSuccess) return e;
+  int h = 0;
+  e = cudaMemsetAsync(d, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    wait_probe_kernel<<<1, 32, 0, s>>>(limit, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d);
+  *timed_out = h;
+  return e;
+}
 
 cudaError_t launch_tc(int prec, const DevScene* scenes, const Layout* layout, const double* obs,
                       const Tile* tiles, int n_tiles, const double* p, const Consts& c,

@@ -882,6 +882,26 @@ int plan_probe_alu(double* out, void* stream) {
   return PLAN_OK;
 }
 
+int plan_probe_wait_timeout(int wait_us, void* stream) {
+  if (wait_us < 1 || wait_us > 100000) {
+    set_unbound_error("wait_us must be in [1, 100000]");
+    return PLAN_EINVAL;
+  }
+  int timed_out = 0;
+  // SM clock cycles: 2.1 per nanosecond bounds the wait from above at the maximum clock
+  const cudaError_t e = wait_probe(2100LL * wait_us, static_cast<cudaStream_t>(stream), &timed_out);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_unbound_error(cudaGetErrorString(e));
+    return PLAN_ECUDA;
+  }
+  if (timed_out) {
+    set_unbound_error("the bounded wait gave up: no arrival on the mbarrier");
+    return PLAN_ETIMEOUT;
+  }
+  return PLAN_OK;
+}
+
 int plan_qp_forward(plan_ctx* ctx, const double* p, const double* b0, int B, double* xi,
                     void* stream) {
   if (!ctx) return PLAN_EINVAL;

@@ -145,3 +145,15 @@ def test_repeat_is_bitwise_deterministic():
     b = _run("tf32x3", prm, sc, p)
     for u, v in zip(a, b):
         assert np.array_equal(u, v)
+
+
+def test_bounded_wait_gives_up_and_the_device_stays_usable():
+    """The tensor-core solve's mbarrier wait, run on a barrier that nothing
+    arrives at, gives up after its bound and reports PLAN_ETIMEOUT through the
+    error flag; the device then still runs a tensor-core solve to parity."""
+    assert binding.plan_probe_wait_timeout(0) == binding.PLAN_EINVAL
+    for _ in range(2):
+        assert binding.plan_probe_wait_timeout(2000) == binding.PLAN_ETIMEOUT
+    prm, sc, B = sg.workload(0, inner_iters=20)
+    p = sg.make_samples(303, sc, 40, prm.n_seg)
+    _check("tf32x3", prm, _run("tf32x3", prm, sc, p), _oracle(prm, sc, p))
