@@ -95,3 +95,11 @@ def test_unknown_precision_is_rejected():
     ctx = ctypes.c_void_p()
     assert lib.plan_init(ctypes.byref(cfg), ctypes.byref(ctx)) == binding.PLAN_EINVAL
     assert "prec" in binding.last_error(None)
+
+
+def test_diagnostics_check_their_arguments_before_the_device():
+    lib = _lib()
+    assert lib.plan_probe_alu(None, None) == binding.PLAN_EINVAL
+    for bad in (0, 100001):
+        assert lib.plan_probe_wait_timeout(bad, None) == binding.PLAN_EINVAL
+        assert "wait_us" in binding.last_error(None)
