@@ -25,10 +25,12 @@ breaks, the first-iteration distribution) are stated at each function.
 
 Pinning: every function here is pinned by the not-gpu tests against closed
 forms, invariants of the constraint sets, library routines or brute force.
-The exact values of the Alg. 2 iterates beyond those invariants (a
-non-convex alternating minimisation) have no independent closed form; the
-convex special case (lane bounds only) is pinned against a general QP solve.
-Status of ``lower.solve`` on a general scene: parity unpinned for the exact
-iterate values (only the invariants above and the oracle-vs-GPU agreement
-hold them); every other function is pinned.
+The Alg. 2 iterates (a non-convex alternating minimisation) have no closed
+form; beyond the invariants (A xi = b every iteration, the fixed point at a
+feasible xi_bar, the convex lane case against a general QP solve) the
+iteration map is pinned by a second statement of Alg. 2 written row by row
+from the paper (its own assembly, projections and a null-space xi-step),
+which fixes the multiplier step rho/2 and the lagged curvature of the
+velocity clip.  Where the paper is garbled both statements take the same
+reading (stated at each function); a reading is a choice, not a pin.
 """

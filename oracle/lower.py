@@ -30,10 +30,13 @@ Readings of the paper adopted here:
 
 Pins: Step 1, the projections, the slack, the xi-step and the scoring are
 pinned by closed forms and invariants (tests/test_oracle_lower.py).  The
-exact iterate values of Alg. 2 on a general non-convex scene are parity
-unpinned: beyond its invariants (A xi = b every iteration, the fixed point
-at a feasible xi_bar, the convex lane case) only the oracle-vs-GPU agreement
-holds them.
+iteration of Alg. 2 as a whole -- including the multiplier step rho/2 of
+Eq. update_lagrange and the curvature lag kappa(^k xi) of Eq. clip_d_v, which
+no invariant fixes -- is pinned by a second, row-by-row statement of the
+algorithm written independently (per-row F/G assembly, math.atan2 projections,
+a null-space xi-step) on a scene where every block is active
+(tests/test_oracle_alg2_rowwise.py).  Both statements follow the same readings
+of the garbled passages listed above; those readings are choices, not pins.
 """
 from __future__ import annotations
 

@@ -9,6 +9,7 @@ import textwrap
 
 import pytest
 
+import test_oracle_alg2_rowwise as ta
 import test_oracle_basis as tb
 import test_oracle_lower as tl
 import test_oracle_qp_layer as tq
@@ -57,6 +58,14 @@ MUTATIONS = [
      "lam = lam - 0.5 * prm.rho * (rf @ F) - 0.5 * prm.rho * (rg @ G)",
      "lam = lam + 0.5 * prm.rho * (rf @ F) + 0.5 * prm.rho * (rg @ G)",
      [tl.test_projection_reduces_residual_on_static_obstacles, tl.test_convex_lane_case_limit]),
+    ("multiplier step rho instead of the printed rho/2", lower, "project",
+     "lam = lam - 0.5 * prm.rho * (rf @ F) - 0.5 * prm.rho * (rg @ G)",
+     "lam = lam - 1.0 * prm.rho * (rf @ F) - 1.0 * prm.rho * (rg @ G)",
+     [lambda: ta.test_project_matches_rowwise_restatement(2)]),
+    ("road curvature of the velocity clip at the current iterate", lower, "project",
+     "h, da, _ = alpha_d_step(xi, scene, prm, basis, da, x_prev)",
+     "h, da, _ = alpha_d_step(xi, scene, prm, basis, da, x)",
+     [lambda: ta.test_project_matches_rowwise_restatement(2)]),
     ("score: lane rows swapped", lower, "score",
      "np.maximum(0.0, y - yub) + np.maximum(0.0, ylb - y)",
      "np.maximum(0.0, y - ylb) + np.maximum(0.0, yub - y)",
