@@ -13,8 +13,12 @@ Readings of the paper adopted here:
   * PD tracking (Eq. cost, printed with unbalanced parentheses): stable
     tracking c_l = (ydd + kp (y - y_d) + kv yd)^2, c_v = (xdd + kp (xd - v_d))^2,
     weights of c_s, c_l, c_v all one.
-  * Equality constraints: initial state b0 only (the goal rows of
-    Eq. final_boundary are not part of p in the paper's MPC-Bi-Level).
+  * Equality constraints: the initial state b0 (Eq. boundary_cond_initial)
+    and, when p carries goal entries (prm.goal, Eq. behaviour_param's x_f,
+    y_f), the final rows of Eq. final_boundary: x(t_f) = x_f on the x axis,
+    y(t_f) = y_f and ydot(t_f) = 0 on the y axis.  The goal positions enter
+    only b(p) (Sec. IV-A, after Eq. lower_eq); the paper's MPC-Bi-Level runs
+    use set-points alone (goal off).
   * Ellipse: a, b are the semi-axes used in Table I's collision expression;
     h_y uses y_o + b d sin(alpha) (the printed "x_o + a d sin" is a slip).
   * v_min-bar of Eq. (clip_d_v): max(v_min, sqrt(d_a |sin(a_a - a_v)| / kappa_max)),
@@ -55,9 +59,10 @@ def segment_lengths(m: int, n_seg: int):
 
 def setpoint_vectors(p: np.ndarray, m: int, n_seg: int):
     """y_d, v_d (B, m): each segment's set-point repeated over its steps
-    (Sec. III-C, the sentence after the cost terms; p per Eq. behaviour_param)."""
+    (Sec. III-C, the sentence after the cost terms; p per Eq. behaviour_param,
+    p = [y_d,1..n_seg, v_d,1..n_seg(, x_f, y_f)])."""
     seg_of_t = np.repeat(np.arange(n_seg), segment_lengths(m, n_seg))
-    return p[:, :n_seg][:, seg_of_t], p[:, n_seg:][:, seg_of_t]
+    return p[:, :n_seg][:, seg_of_t], p[:, n_seg:2 * n_seg][:, seg_of_t]
 
 
 def lane_bounds(scene, prm):
@@ -115,30 +120,60 @@ def initial_rows(basis):
     return np.stack([W[0], Wd[0], Wdd[0]])
 
 
+def equality_rows(basis, goal: bool = False):
+    """(A_x, A_y) of Eq. lower_eq: the initial rows of Eq. boundary_cond_initial
+    and, with goal entries in p, the final rows of Eq. final_boundary
+    (x(t_f) on the x axis; y(t_f) and ydot(t_f) on the y axis)."""
+    W, Wd, Wdd = basis
+    A0 = initial_rows(basis)
+    if not goal:
+        return A0, A0
+    return np.vstack([A0, W[-1]]), np.vstack([A0, W[-1], Wd[-1]])
+
+
+def equality_rhs(p, scene, prm):
+    """b(p) of Eq. lower_eq per axis, (B, ne_x) and (B, ne_y): b0 of the ego
+    state, then x_f (x axis) and y_f, 0 (y axis) from the goal entries of p."""
+    p = np.atleast_2d(np.asarray(p, dtype=np.float64))
+    B = p.shape[0]
+    x0, y0, vx0, vy0, ax0, ay0 = np.asarray(scene.ego, dtype=np.float64)
+    bx = np.tile([x0, vx0, ax0], (B, 1))
+    by = np.tile([y0, vy0, ay0], (B, 1))
+    if getattr(prm, "goal", False):
+        ns = prm.n_seg
+        bx = np.column_stack([bx, p[:, 2 * ns]])
+        by = np.column_stack([by, p[:, 2 * ns + 1], np.zeros(B)])
+    return bx, by
+
+
 def kkt_solve(Q, A, rhs_top, rhs_bot):
     """Solve [[Q, A^T], [A, 0]] [z; mu] = [rhs_top; rhs_bot] for B columns
-    (LU with partial pivoting via numpy); returns z (B, n)."""
+    (LU with partial pivoting via numpy); rhs_bot is (ne,), shared by the
+    columns, or (B, ne), one per column.  Returns z (B, n)."""
     n, ne = Q.shape[0], A.shape[0]
+    B = rhs_top.shape[0]
     K = np.zeros((n + ne, n + ne))
     K[:n, :n] = Q
     K[:n, n:] = A.T
     K[n:, :n] = A
-    R = np.concatenate([rhs_top.T, np.broadcast_to(np.asarray(rhs_bot, float).reshape(ne, -1),
-                                                     (ne, rhs_top.shape[0]))], axis=0)
+    bot = np.asarray(rhs_bot, dtype=np.float64)
+    bot = np.broadcast_to(bot if bot.ndim == 2 else bot[None, :], (B, ne))
+    R = np.concatenate([rhs_top.T, bot.T], axis=0)
     return np.linalg.solve(K, R)[:n].T
 
 
 def step1(p, scene, prm, basis):
     """xi_bar (B, 2n): the equality-constrained QP of Alg. 1 line 7 for each p_j."""
     m = basis[0].shape[0]
-    yd, vd = setpoint_vectors(np.atleast_2d(p), m, prm.n_seg)
+    p = np.atleast_2d(p)
+    yd, vd = setpoint_vectors(p, m, prm.n_seg)
     (Qx, Lx), (Qy, Ly) = step1_cost_matrices(basis, prm)
-    A = initial_rows(basis)
-    x0, y0, vx0, vy0, ax0, ay0 = np.asarray(scene.ego, dtype=np.float64)
+    Ax, Ay = equality_rows(basis, getattr(prm, "goal", False))
+    bx, by = equality_rhs(p, scene, prm)
     qx = -2.0 * prm.kp_lon * (vd @ Lx)          # (B, n) rows are (L^T v_d)^T
     qy = -2.0 * prm.kp_lat * (yd @ Ly)
-    cx = kkt_solve(Qx, A, -qx, [x0, vx0, ax0])
-    cy = kkt_solve(Qy, A, -qy, [y0, vy0, ay0])
+    cx = kkt_solve(Qx, Ax, -qx, bx)
+    cy = kkt_solve(Qy, Ay, -qy, by)
     return np.concatenate([cx, cy], axis=1)
 
 
@@ -150,14 +185,22 @@ def step1_layer(p, b0, prm, basis):
     p = np.atleast_2d(np.asarray(p, dtype=np.float64))
     b0 = np.atleast_2d(np.asarray(b0, dtype=np.float64))
     m = basis[0].shape[0]
-    yd, vd = setpoint_vectors(p, m, prm.n_seg)
+    goal = getattr(prm, "goal", False)
+    ns = prm.n_seg
+    yd, vd = setpoint_vectors(p, m, ns)
     (Qx, Lx), (Qy, Ly) = step1_cost_matrices(basis, prm)
-    A = initial_rows(basis)
+    Ax, Ay = equality_rows(basis, goal)
     qx = -2.0 * prm.kp_lon * (vd @ Lx)
     qy = -2.0 * prm.kp_lat * (yd @ Ly)
-    cx = np.stack([kkt_solve(Qx, A, -qx[j:j + 1], b0[j, [0, 2, 4]])[0] for j in range(len(p))])
-    cy = np.stack([kkt_solve(Qy, A, -qy[j:j + 1], b0[j, [1, 3, 5]])[0] for j in range(len(p))])
-    return np.concatenate([cx, cy], axis=1)
+    cx, cy = [], []
+    for j in range(len(p)):
+        bx, by = list(b0[j, [0, 2, 4]]), list(b0[j, [1, 3, 5]])
+        if goal:
+            bx += [p[j, 2 * ns]]
+            by += [p[j, 2 * ns + 1], 0.0]
+        cx.append(kkt_solve(Qx, Ax, -qx[j:j + 1], bx)[0])
+        cy.append(kkt_solve(Qy, Ay, -qy[j:j + 1], by)[0])
+    return np.concatenate([np.stack(cx), np.stack(cy)], axis=1)
 
 
 def step1_layer_vjp(g, prm, basis):
@@ -165,18 +208,22 @@ def step1_layer_vjp(g, prm, basis):
     (dL/dp (B, d_p), dL/db0 (B, 6)).  Implicit differentiation of the KKT
     system K [z; mu] = [-q; b] (K symmetric): [u; w] = K^-1 [g_z; 0] gives
     dL/d(-q) = u and dL/db = w; -q = 2 k L^T s(p) with s the set-point vector,
-    so dL/ds = 2 k L u and each entry of p collects dL/ds over its segment."""
+    so dL/ds = 2 k L u and each entry of p collects dL/ds over its segment.
+    A goal entry of p (x_f, y_f) is an entry of b: its gradient is the matching
+    entry of w."""
     g = np.atleast_2d(np.asarray(g, dtype=np.float64))
     n = basis[0].shape[1]
     m = basis[0].shape[0]
+    goal = getattr(prm, "goal", False)
     (Qx, Lx), (Qy, Ly) = step1_cost_matrices(basis, prm)
-    A = initial_rows(basis)
-    ne = A.shape[0]
+    Ax, Ay = equality_rows(basis, goal)
     seg_of_t = np.repeat(np.arange(prm.n_seg), segment_lengths(m, prm.n_seg))
     B = len(g)
-    grad_p = np.zeros((B, 2 * prm.n_seg))
+    grad_p = np.zeros((B, 2 * prm.n_seg + (2 if goal else 0)))
     grad_b = np.zeros((B, 6))
-    for axis, (Q, L, k, off) in enumerate([(Qx, Lx, prm.kp_lon, prm.n_seg), (Qy, Ly, prm.kp_lat, 0)]):
+    for axis, (Q, L, k, off, A) in enumerate([(Qx, Lx, prm.kp_lon, prm.n_seg, Ax),
+                                              (Qy, Ly, prm.kp_lat, 0, Ay)]):
+        ne = A.shape[0]
         K = np.zeros((n + ne, n + ne))
         K[:n, :n] = Q
         K[:n, n:] = A.T
@@ -187,7 +234,9 @@ def step1_layer_vjp(g, prm, basis):
         ds = 2.0 * k * (u @ L.T)                # (B, m)
         for j in range(prm.n_seg):
             grad_p[:, off + j] = ds[:, seg_of_t == j].sum(axis=1)
-        grad_b[:, [axis, axis + 2, axis + 4]] = w
+        grad_b[:, [axis, axis + 2, axis + 4]] = w[:, :3]
+        if goal:
+            grad_p[:, 2 * prm.n_seg + axis] = w[:, 3]     # x_f (x axis) or y_f (y axis)
     return grad_p, grad_b
 
 
@@ -195,7 +244,7 @@ def step1_layer_vjp(g, prm, basis):
 # Alg. 2: batch projection
 # ----------------------------------------------------------------------------
 
-def projection_operators(basis, n_obs: int):
+def projection_operators(basis, n_obs: int, goal: bool = False):
     """F (Eq. after lane_reform), G (lane rows, y block) and A_eq, literal."""
     W, Wd, Wdd = basis
     m, n = W.shape
@@ -204,9 +253,8 @@ def projection_operators(basis, n_obs: int):
     F = np.block([[Fax, Z], [Z, Fax]])
     Zm = np.zeros_like(W)
     G = np.block([[Zm, W], [Zm, -W]])
-    Aax = initial_rows(basis)
-    Za = np.zeros_like(Aax)
-    A = np.block([[Aax, Za], [Za, Aax]])
+    Ax, Ay = equality_rows(basis, goal)
+    A = np.block([[Ax, np.zeros((Ax.shape[0], n))], [np.zeros((Ay.shape[0], n)), Ay]])
     return F, G, A
 
 
@@ -306,17 +354,26 @@ def xi_step(xi_bar, lam, h, s, ops, e, b_eq, rho):
     return kkt_solve(H, A, rhs, b_eq)
 
 
-def project(xi_bar, scene, prm, basis, iters: int | None = None, trace: bool = False):
+def project(xi_bar, scene, prm, basis, iters: int | None = None, trace: bool = False, p=None):
     """Alg. 2 for every row of xi_bar; returns xi^K (and a per-iteration trace).
+    With goal entries in p (prm.goal) the equality rows of Eq. split_xy carry
+    each sample's b(p_j), so p (B, d_p) is required.
 
     The trace holds, per iteration, the mean over samples of
     ||F xi - h|| + ||G xi - e + s|| (the residual the multipliers drive to zero).
     """
     K = prm.inner_iters if iters is None else iters
-    ops = projection_operators(basis, scene.n_obs)
+    goal = getattr(prm, "goal", False)
+    ops = projection_operators(basis, scene.n_obs, goal)
     F, G, A = ops
-    x0, y0, vx0, vy0, ax0, ay0 = np.asarray(scene.ego, dtype=np.float64)
-    b_eq = [x0, vx0, ax0, y0, vy0, ay0]
+    if goal:
+        if p is None:
+            raise ValueError("goal entries: project needs p for b(p)")
+        bx, by = equality_rhs(p, scene, prm)
+        b_eq = np.concatenate([bx, by], axis=1)                         # (B, ne_x + ne_y)
+    else:
+        x0, y0, vx0, vy0, ax0, ay0 = np.asarray(scene.ego, dtype=np.float64)
+        b_eq = [x0, vx0, ax0, y0, vy0, ay0]
 
     xi = np.array(xi_bar, dtype=np.float64, copy=True)
     lam = np.zeros_like(xi)
@@ -374,6 +431,6 @@ def score(xi, scene, prm, basis):
 def solve(p, scene, prm, basis, iters: int | None = None):
     """Alg. 1 lines 6-9 for every p_j: Step 1, Step 2 (Alg. 2), residual and cost."""
     xb = step1(p, scene, prm, basis)
-    xs = project(xb, scene, prm, basis, iters)
+    xs = project(xb, scene, prm, basis, iters, p=p)
     r, cu = score(xs, scene, prm, basis)
     return xs, r, cu

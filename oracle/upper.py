@@ -12,7 +12,9 @@ and MPC episode step; entry e of p_j uses word e % 4 of block e // 4.
 
 Readings adopted (the paper leaves these open):
   * first iteration of a fresh episode draws y_d uniformly over lane centres
-    and v_d ~ U[v_des_lo, v_des_hi] per segment; its mu^0 / Sigma^0 are the
+    and v_d ~ U[v_des_lo, v_des_hi] per segment; with goal entries, x_f =
+    x0 + v t_f with v ~ U[v_des_lo, v_des_hi] (t_f = (m - 1) dt, x0 the ego
+    position) and y_f uniformly over lane centres.  mu^0 / Sigma^0 are the
     moments of that distribution.  Later iterations, and the first iteration
     of a warm-started cycle, draw N(mu, Sigma + cov_eps I).
   * ties in both selections go to the lower sample index.
@@ -89,21 +91,38 @@ def initial_moments(scene, prm):
     """mu^0, Sigma^0 of the first-iteration uniform distribution."""
     ns = prm.n_seg
     L, w = scene.n_lanes, scene.lane_width
-    mu = np.concatenate([np.full(ns, L * w / 2.0), np.full(ns, 0.5 * (prm.v_des_lo + prm.v_des_hi))])
-    var = np.concatenate([np.full(ns, w * w * (L * L - 1) / 12.0),
-                          np.full(ns, (prm.v_des_hi - prm.v_des_lo) ** 2 / 12.0)])
-    return mu, np.diag(var)
+    lane_mu, lane_var = L * w / 2.0, w * w * (L * L - 1) / 12.0
+    v_mu, v_var = 0.5 * (prm.v_des_lo + prm.v_des_hi), (prm.v_des_hi - prm.v_des_lo) ** 2 / 12.0
+    mu = [lane_mu] * ns + [v_mu] * ns
+    var = [lane_var] * ns + [v_var] * ns
+    if getattr(prm, "goal", False):
+        tf = (prm.m - 1) * prm.dt
+        mu += [float(scene.ego[0]) + tf * v_mu, lane_mu]
+        var += [tf * tf * v_var, lane_var]
+    return np.array(mu), np.diag(var)
 
 
 def draw_initial(B, scene, prm, seed, step):
-    """First iteration of a fresh episode: lane-centre y_d, uniform v_d."""
+    """First iteration of a fresh episode: lane-centre y_d, uniform v_d (and,
+    with goal entries, x_f = x0 + U[v_des_lo, v_des_hi] t_f, lane-centre y_f)."""
     ns = prm.n_seg
-    u = uniforms(raw_words(B, 2 * ns, 1, seed, step))[:, :2 * ns]
+    goal = getattr(prm, "goal", False)
+    d_p = 2 * ns + (2 if goal else 0)
+    u = uniforms(raw_words(B, d_p, 1, seed, step))[:, :d_p]
     centres = (np.arange(scene.n_lanes) + 0.5) * scene.lane_width
-    p = np.empty((B, 2 * ns))
-    idx = np.minimum(np.floor(u[:, :ns] * scene.n_lanes).astype(np.int64), scene.n_lanes - 1)
-    p[:, :ns] = centres[idx]
-    p[:, ns:] = prm.v_des_lo + (prm.v_des_hi - prm.v_des_lo) * u[:, ns:]
+
+    def lane(uu):
+        return centres[np.minimum(np.floor(uu * scene.n_lanes).astype(np.int64), scene.n_lanes - 1)]
+
+    def speed(uu):
+        return prm.v_des_lo + (prm.v_des_hi - prm.v_des_lo) * uu
+
+    p = np.empty((B, d_p))
+    p[:, :ns] = lane(u[:, :ns])
+    p[:, ns:2 * ns] = speed(u[:, ns:2 * ns])
+    if goal:
+        p[:, 2 * ns] = float(scene.ego[0]) + (prm.m - 1) * prm.dt * speed(u[:, 2 * ns])
+        p[:, 2 * ns + 1] = lane(u[:, 2 * ns + 1])
     return p
 
 

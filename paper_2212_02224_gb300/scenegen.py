@@ -109,7 +109,7 @@ class Params:
 
     m: int = 100               # timesteps in the horizon
     n_coef: int = 11           # Bernstein coefficients per axis (degree 10)
-    n_seg: int = 1             # set-point segments; p has 2*n_seg entries
+    n_seg: int = 1             # set-point segments; p has 2*n_seg set-point entries
     inner_iters: int = 50      # K, projection iterations
     outer_iters: int = 5       # L, CEM iterations
     n_elite_c: int = 30        # ConstraintEliteSet size
@@ -130,10 +130,11 @@ class Params:
     lane_margin: float = 1.0
     v_des_lo: float = 5.0      # first-iteration uniform range of v_d
     v_des_hi: float = 25.0
+    goal: bool = False         # p also carries the goal positions x_f, y_f
 
     @property
     def d_p(self) -> int:
-        return 2 * self.n_seg
+        return 2 * self.n_seg + (2 if self.goal else 0)
 
 
 def make_scene(seed: int, n_lanes: int, n_obs: int, lane_width: float = 3.5,
@@ -175,14 +176,19 @@ def curved_road(n_lanes: int, lane_width: float = 3.5, kappa: float = 0.01,
 
 
 def make_samples(seed: int, scene: Scene, B: int, n_seg: int,
-                 v_range=(5.0, 25.0)) -> np.ndarray:
+                 v_range=(5.0, 25.0), goal_tf: float | None = None) -> np.ndarray:
     """B behavioural inputs p = [y_d,1..n_seg, v_d,1..n_seg] (Eq. behaviour_param):
-    lateral set-points on lane centres, velocity set-points uniform."""
+    lateral set-points on lane centres, velocity set-points uniform.  With
+    goal_tf (the horizon t_f in seconds) two goal entries follow: x_f = ego x +
+    v t_f with v uniform in v_range, and y_f on a lane centre."""
     s = Stream(seed)
     centres = scene.lane_centres()
-    p = np.empty((B, 2 * n_seg))
+    p = np.empty((B, 2 * n_seg + (2 if goal_tf is not None else 0)))
     p[:, :n_seg] = centres[s.integers(0, scene.n_lanes - 1, B * n_seg)].reshape(B, n_seg)
-    p[:, n_seg:] = s.uniform(*v_range, B * n_seg).reshape(B, n_seg)
+    p[:, n_seg:2 * n_seg] = s.uniform(*v_range, B * n_seg).reshape(B, n_seg)
+    if goal_tf is not None:
+        p[:, 2 * n_seg] = float(scene.ego[0]) + goal_tf * s.uniform(*v_range, B)
+        p[:, 2 * n_seg + 1] = centres[s.integers(0, scene.n_lanes - 1, B)]
     return p
 
 

@@ -101,7 +101,7 @@ def _angle(sy, cx):
 class _Sample:
     """One sample's Alg. 2 state, row by row."""
 
-    def __init__(self, xi_bar, sc, prm):
+    def __init__(self, xi_bar, sc, prm, goal=None):
         self.prm, self.sc = prm, sc
         self.m, self.n = prm.m, prm.n_coef
         self.W, self.Wd, self.Wdd = _basis_rows(self.m, self.n, prm.dt)
@@ -117,6 +117,12 @@ class _Sample:
                 row[axis * n:(axis + 1) * n] = mat[0]
                 self.A.append(row)
                 self.b.append(float(sc.ego[axis + comp]))
+        if goal is not None:
+            # Eq. final_boundary: x(t_f) = x_f, y(t_f) = y_f, ydot(t_f) = 0
+            x_f, y_f = goal
+            for axis, mat, val in ((0, self.W, x_f), (1, self.W, y_f), (1, self.Wd, 0.0)):
+                self.A.append(self._row(axis, mat[self.m - 1]))
+                self.b.append(float(val))
 
     def _row(self, axis, basis_row, sign=1.0):
         r = [0.0] * (2 * self.n)

@@ -11,6 +11,7 @@ import pytest
 
 import test_oracle_alg2_rowwise as ta
 import test_oracle_basis as tb
+import test_oracle_goal as tg
 import test_oracle_lower as tl
 import test_oracle_qp_layer as tq
 import test_oracle_road as tr
@@ -33,8 +34,8 @@ MUTATIONS = [
      "np.stack([W[0], Wd[0], Wdd[0]])", "np.stack([W[0], Wd[0], Wd[0]])",
      [lambda: tl.test_step1_is_constrained_minimiser(1), tl.test_step1_closed_form_steady_state]),
     ("set-points: y_d and v_d halves swapped", lower, "setpoint_vectors",
-     "return p[:, :n_seg][:, seg_of_t], p[:, n_seg:][:, seg_of_t]",
-     "return p[:, n_seg:][:, seg_of_t], p[:, :n_seg][:, seg_of_t]",
+     "return p[:, :n_seg][:, seg_of_t], p[:, n_seg:2 * n_seg][:, seg_of_t]",
+     "return p[:, n_seg:2 * n_seg][:, seg_of_t], p[:, :n_seg][:, seg_of_t]",
      [tl.test_setpoint_segments]),
     ("obstacle h_y with a instead of b", lower, "alpha_d_step",
      "hoy = yo[None] + b[None] * d_o * np.sin(al_o)", "hoy = yo[None] + a[None] * d_o * np.sin(al_o)",
@@ -66,6 +67,19 @@ MUTATIONS = [
      "h, da, _ = alpha_d_step(xi, scene, prm, basis, da, x_prev)",
      "h, da, _ = alpha_d_step(xi, scene, prm, basis, da, x)",
      [lambda: ta.test_project_matches_rowwise_restatement(2)]),
+    ("goal: x_f and y_f swapped in b(p)", lower, "equality_rhs",
+     "bx = np.column_stack([bx, p[:, 2 * ns]])", "bx = np.column_stack([bx, p[:, 2 * ns + 1]])",
+     [tg.test_goal_cruise_closed_form, tg.test_goal_rows_hold_every_iteration]),
+    ("goal: final lateral acceleration row instead of velocity", lower, "equality_rows",
+     "np.vstack([A0, W[-1], Wd[-1]])", "np.vstack([A0, W[-1], Wdd[-1]])",
+     [tg.test_goal_rows_hold_every_iteration, tg.test_goal_step1_null_space_method_agrees]),
+    ("goal prior: x_f without the horizon length", upper, "draw_initial",
+     "float(scene.ego[0]) + (prm.m - 1) * prm.dt * speed(u[:, 2 * ns])",
+     "float(scene.ego[0]) + speed(u[:, 2 * ns])",
+     [tg.test_goal_initial_draws_and_moments]),
+    ("goal VJP: x_f and y_f gradients swapped", lower, "step1_layer_vjp",
+     "grad_p[:, 2 * prm.n_seg + axis] = w[:, 3]", "grad_p[:, 2 * prm.n_seg + 1 - axis] = w[:, 3]",
+     [tg.test_goal_layer_vjp_matches_central_differences]),
     ("score: lane rows swapped", lower, "score",
      "np.maximum(0.0, y - yub) + np.maximum(0.0, ylb - y)",
      "np.maximum(0.0, y - ylb) + np.maximum(0.0, yub - y)",
