@@ -80,6 +80,16 @@ typedef enum {
  *                paper uses a 10th-order polynomial, n_coef = 11 (Sec. V-A)
  *   n_seg        set-point segments of p (Eq. behaviour_param), 1..4;
  *                p = [y_d,1..y_d,n_seg, v_d,1..v_d,n_seg] has d_p = 2 n_seg entries
+ *   goal         0 or 1.  With 1, p also carries the goal positions of
+ *                Eq. behaviour_param, p = [y_d.., v_d.., x_f, y_f]
+ *                (d_p = 2 n_seg + 2), and the lower level adds the final
+ *                boundary rows of Eq. final_boundary, (x(t_f), y(t_f),
+ *                ydot(t_f)) = (x_f, y_f, 0), to its equality constraints
+ *                A_eq xi = b(p) (Eq. lower_eq: the goal positions enter b,
+ *                the set-points the cost).  x_f is in the scene's frame.
+ *                In the first iteration of a fresh episode x_f = x0 + v t_f
+ *                with v ~ U[v_des_lo, v_des_hi] (t_f = (m - 1) dt) and y_f is
+ *                a lane centre drawn uniformly.
  *   inner_iters  K, iterations of Alg. 2 (>= 1)
  *   outer_iters  L, iterations of Alg. 1 (>= 1)
  *   n_elite_c    size of ConstraintEliteSet (Alg. 1 line 10); <= 0 means
@@ -102,7 +112,7 @@ typedef struct {
     int m, n_coef, n_seg, inner_iters, outer_iters, n_elite_c, n_elite;
     int prec;
     int max_obs, max_samples, max_scenes;
-    int reserved0;
+    int goal;
     double dt, rho, kp_lat, kv_lat, kp_lon, gamma, eta, cov_eps;
     double v_min, v_max, a_max, kappa_max, c_max, lane_margin, v_des_lo, v_des_hi;
 } plan_config;
@@ -143,15 +153,23 @@ typedef struct {
     double road_origin;   /* arc length of x = 0 along the road profile */
 } plan_scene;
 
+/* Largest d_p: four set-point segments per axis plus the two goal entries. */
+#define PLAN_MAX_DP 10
+
 /* Sampling distribution of p carried between MPC cycles (Alg. 1 lines 2, 14).
- * mu[0..d_p-1] and sigma (d_p x d_p, row-major, leading dimension 8) are
- * used when fresh == 0; when fresh != 0 the first iteration draws y_d
- * uniformly over lane centres and v_d ~ U[v_des_lo, v_des_hi] and mu, sigma
- * start at that distribution's moments.  seed and episode_step select the
- * Philox4x32-10 stream (key = seed, counter = (j, l | c << 16, step)). */
+ * mu[0..d_p-1] and sigma (d_p x d_p, row-major, leading dimension
+ * PLAN_MAX_DP) are used when fresh == 0; when fresh != 0 the first iteration
+ * draws y_d uniformly over lane centres and v_d ~ U[v_des_lo, v_des_hi] (and
+ * the goal entries as described at plan_config.goal) and mu, sigma start at
+ * that distribution's moments.  seed and episode_step select the
+ * Philox4x32-10 stream (key = seed, counter = (j, l | c << 16, step)).
+ * With goal entries, a warm start carries x_f as a position in the scene's
+ * frame; plan_advance re-centres the frame on the ego, so a caller that
+ * keeps an absolute goal across cycles shifts mu[x_f] by the distance
+ * travelled. */
 typedef struct {
-    double mu[8];
-    double sigma[64];
+    double mu[PLAN_MAX_DP];
+    double sigma[PLAN_MAX_DP * PLAN_MAX_DP];
     uint64_t seed;
     uint64_t episode_step;
     int fresh;
@@ -160,7 +178,7 @@ typedef struct {
 
 /* Best pair of the final EliteSet (the return line of Alg. 1). */
 typedef struct {
-    double p[8];         /* d_p entries                                      */
+    double p[PLAN_MAX_DP]; /* d_p entries                                    */
     double xi[32];       /* 2 n_coef entries: (c_x, c_y)                      */
     double cost;         /* c_u + r_j                                         */
     double resid;        /* r_j, Alg. 1 line 9                                */
@@ -197,17 +215,22 @@ int plan_last_error(const plan_ctx* ctx, char* buf, size_t len);
  *   xi      device, B x 2 n_coef, or NULL
  *   resid   device, B
  *   cu      device, B
+ *   status  device, B ints, or NULL: per sample PLAN_OK when its solution
+ *           xi*_j (all 2 n_coef coefficients, written or not), r_j and c_u
+ *           are finite, PLAN_ENONFINITE otherwise.  A non-finite input p_j
+ *           (or a solve that overflows) affects only its own sample.
  * Errors: EINVAL (bad scene or B < 0), ECAPACITY (B > max_samples or
- * n_obs > max_obs).  B == 0 is a no-op. */
+ * n_obs > max_obs).  B == 0 is a no-op.  Per-sample failures are reported
+ * only through `status` (the call itself does not wait for the result). */
 int plan_solve(plan_ctx* ctx, const plan_scene* scene, const double* p, int B,
-               double* xi, double* resid, double* cu, void* stream);
+               double* xi, double* resid, double* cu, int* status, void* stream);
 
 /* As plan_solve for S scenes in one launch.  Scene s owns samples
- * [off_s, off_s + B[s]) of the concatenated p / xi / resid / cu, with
- * off_s = B[0] + ... + B[s-1].  `B` is host memory. */
+ * [off_s, off_s + B[s]) of the concatenated p / xi / resid / cu / status,
+ * with off_s = B[0] + ... + B[s-1].  `B` is host memory. */
 int plan_solve_batch(plan_ctx* ctx, const plan_scene* scenes, const int* B, int S,
                      const double* p, double* xi, double* resid, double* cu,
-                     void* stream);
+                     int* status, void* stream);
 
 /* ---------------------------------------------------------- Alg. 1 (MPC cycle) */
 

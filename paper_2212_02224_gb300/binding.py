@@ -28,6 +28,7 @@ PLAN_PREC_FP32 = 1
 PLAN_PREC_TF32 = 2
 PLAN_PREC_BF16 = 3
 PLAN_PREC_TF32X3 = 4
+PLAN_MAX_DP = 10
 PRECISIONS = {"fp64": PLAN_PREC_FP64, "fp32": PLAN_PREC_FP32, "tf32": PLAN_PREC_TF32,
               "bf16": PLAN_PREC_BF16, "tf32x3": PLAN_PREC_TF32X3}
 
@@ -35,7 +36,7 @@ PRECISIONS = {"fp64": PLAN_PREC_FP64, "fp32": PLAN_PREC_FP32, "tf32": PLAN_PREC_
 class PlanConfig(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in (
         "m", "n_coef", "n_seg", "inner_iters", "outer_iters", "n_elite_c", "n_elite", "prec",
-        "max_obs", "max_samples", "max_scenes", "reserved0")] + [(n, ctypes.c_double) for n in (
+        "max_obs", "max_samples", "max_scenes", "goal")] + [(n, ctypes.c_double) for n in (
         "dt", "rho", "kp_lat", "kv_lat", "kp_lon", "gamma", "eta", "cov_eps", "v_min", "v_max",
         "a_max", "kappa_max", "c_max", "lane_margin", "v_des_lo", "v_des_hi")]
 
@@ -60,7 +61,7 @@ class PlanScene(ctypes.Structure):
 
 
 class PlanCemState(ctypes.Structure):
-    _fields_ = [("mu", ctypes.c_double * 8), ("sigma", ctypes.c_double * 64),
+    _fields_ = [("mu", ctypes.c_double * PLAN_MAX_DP), ("sigma", ctypes.c_double * (PLAN_MAX_DP ** 2)),
                 ("seed", ctypes.c_uint64), ("episode_step", ctypes.c_uint64),
                 ("fresh", ctypes.c_int), ("reserved0", ctypes.c_int)]
 
@@ -78,7 +79,7 @@ class PlanServerStats(ctypes.Structure):
 
 
 class PlanResult(ctypes.Structure):
-    _fields_ = [("p", ctypes.c_double * 8), ("xi", ctypes.c_double * 32),
+    _fields_ = [("p", ctypes.c_double * PLAN_MAX_DP), ("xi", ctypes.c_double * 32),
                 ("cost", ctypes.c_double), ("resid", ctypes.c_double), ("cu", ctypes.c_double),
                 ("index", ctypes.c_int), ("reserved0", ctypes.c_int)]
 
@@ -117,8 +118,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "plan_destroy": (I, [V]),
         "plan_status_str": (ctypes.c_char_p, [I]),
         "plan_last_error": (I, [V, ctypes.c_char_p, ctypes.c_size_t]),
-        "plan_solve": (I, [V, P(PlanScene), V, I, V, V, V, V]),
-        "plan_solve_batch": (I, [V, P(PlanScene), P(I), I, V, V, V, V, V]),
+        "plan_solve": (I, [V, P(PlanScene), V, I, V, V, V, V, V]),
+        "plan_solve_batch": (I, [V, P(PlanScene), P(I), I, V, V, V, V, V, V]),
         "plan_upload_scenes": (I, [V, P(PlanScene), I, V]),
         "plan_set_state": (I, [V, I, P(PlanCemState), V]),
         "plan_get_state": (I, [V, I, P(PlanCemState), V]),
@@ -182,6 +183,7 @@ def make_config(prm, prec: int, max_obs: int, max_samples: int, max_scenes: int 
         setattr(c, name, float(getattr(prm, name)))
     c.prec = int(prec)
     c.max_obs, c.max_samples, c.max_scenes = int(max_obs), int(max_samples), int(max_scenes)
+    c.goal = int(bool(getattr(prm, "goal", False)))
     return c
 
 
@@ -225,13 +227,13 @@ def make_state(d_p: int, mu=None, sigma=None, seed: int = 0, step: int = 0, fres
         for a in range(d_p):
             st.mu[a] = float(mu[a])
             for b in range(d_p):
-                st.sigma[a * 8 + b] = float(sigma[a][b])
+                st.sigma[a * PLAN_MAX_DP + b] = float(sigma[a][b])
     return st
 
 
 def state_arrays(st: PlanCemState, d_p: int):
     mu = [st.mu[a] for a in range(d_p)]
-    sigma = [[st.sigma[a * 8 + b] for b in range(d_p)] for a in range(d_p)]
+    sigma = [[st.sigma[a * PLAN_MAX_DP + b] for b in range(d_p)] for a in range(d_p)]
     return mu, sigma
 
 
@@ -247,15 +249,18 @@ def plan_destroy(ctx) -> None:
     check(load().plan_destroy(ctx), None)
 
 
-def plan_solve(ctx, scene, p_ptr: int, B: int, xi_ptr, r_ptr: int, cu_ptr: int, stream: int = 0):
+def plan_solve(ctx, scene, p_ptr: int, B: int, xi_ptr, r_ptr: int, cu_ptr: int, status_ptr=None,
+               stream: int = 0):
     arr, keep = make_scenes([scene])
-    check(load().plan_solve(ctx, arr, p_ptr, B, xi_ptr, r_ptr, cu_ptr, stream), ctx)
+    check(load().plan_solve(ctx, arr, p_ptr, B, xi_ptr, r_ptr, cu_ptr, status_ptr, stream), ctx)
 
 
-def plan_solve_batch(ctx, scenes, Bs, p_ptr: int, xi_ptr, r_ptr: int, cu_ptr: int, stream: int = 0):
+def plan_solve_batch(ctx, scenes, Bs, p_ptr: int, xi_ptr, r_ptr: int, cu_ptr: int, status_ptr=None,
+                     stream: int = 0):
     arr, keep = make_scenes(scenes)
     b = (ctypes.c_int * len(Bs))(*[int(x) for x in Bs])
-    check(load().plan_solve_batch(ctx, arr, b, len(Bs), p_ptr, xi_ptr, r_ptr, cu_ptr, stream), ctx)
+    check(load().plan_solve_batch(ctx, arr, b, len(Bs), p_ptr, xi_ptr, r_ptr, cu_ptr, status_ptr,
+                                  stream), ctx)
 
 
 def plan_upload_scenes(ctx, scenes, stream: int = 0):

@@ -136,7 +136,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
              const double* __restrict__ obs, const Tile* __restrict__ tiles,
              const double* __restrict__ pin, Consts c, Params prm,
              double* __restrict__ xi_out, double* __restrict__ r_out,
-             double* __restrict__ cu_out) {
+             double* __restrict__ cu_out, int* __restrict__ st_out) {
   constexpr int NCP = basis32_ncp(NC);
   constexpr int NP = NCP / 2;              // coefficient pairs
   constexpr int ST = basis32_stride(NC);
@@ -187,7 +187,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   }
   for (int e = threadIdx.x; e < 2 * NC * NC; e += blockDim.x) {
     const int ax_ = e / (NC * NC), k_ = (e / NC) % NC, i_ = e % NC;
-    sM[e] = c.pj32[size_t((N * 2 + ax_) * NC + k_) * (2 * NC + 3) + i_];
+    sM[e] = c.pj32[size_t((N * 2 + ax_) * NC + k_) * (2 * NC + c.ne) + i_];
   }
   __syncthreads();
 
@@ -239,14 +239,16 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   if (valid) {
     // xi_bar = Gs p_axis + Hs b_axis (x uses the v_d entries, y the y_d entries),
     // applied in float64: at high polynomial degree the Step-1 map has entries
-    // of order 1e3 whose products cancel to the coefficients' size
-    const double* s1 = c.s1_64 + size_t(axis * NC + kk) * (ns + 3);
-    const double* pj = pin + size_t(j) * (2 * ns);
+    // of order 1e3 whose products cancel to the coefficients' size.  With goal
+    // entries b_axis also holds x_f (x) or y_f (y); the final ydot = 0 adds nothing.
+    const double* s1 = c.s1_64 + size_t(axis * NC + kk) * (ns + c.ne);
+    const double* pj = pin + size_t(j) * prm.d_p;
     double xb = 0.0;
     for (int q = 0; q < ns; ++q) xb = fma(s1[q], pj[(axis == 0 ? ns : 0) + q], xb);
     xb = fma(s1[ns], sc.ego[axis], xb);
     xb = fma(s1[ns + 1], sc.ego[axis + 2], xb);
     xb = fma(s1[ns + 2], sc.ego[axis + 4], xb);
+    if (prm.goal) xb = fma(s1[ns + 3], pj[2 * ns + axis], xb);
     xb_l = float(xb);
   }
   xbuf[lane] = xb_l;     // padding slots hold 0: they meet zero basis columns
@@ -593,6 +595,12 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     for (int w = 0; w < WPS; ++w) { r_acc += sc2[2 * w]; cu_acc += sc2[2 * w + 1]; }
   }
   if (wig == 0) {
+    if (st_out != nullptr) {
+      // per-sample status: the solution, its residual and its cost are finite
+      const bool bad_xi = __any_sync(kFull, valid && !(isfinite(xb_l) && isfinite(dl)));
+      if (lane == 0)
+        st_out[j] = (bad_xi || !isfinite(r_acc) || !isfinite(cu_acc)) ? PLAN_ENONFINITE : PLAN_OK;
+    }
     if (lane == 0) {
       r_out[j] = double(r_acc);
       cu_out[j] = double(cu_acc);
@@ -614,10 +622,10 @@ size_t smem_bytes(const Params& prm, int spc) {
 template <int NC, int SLOTS, int WPS, bool ROAD>
 cudaError_t launch_t(const DevScene* scenes, const Layout* layout, const double* obs,
                      const Tile* tiles, int n_tiles, int spc, const double* p, const Consts& c,
-                     const Params& prm, double* xi, double* r, double* cu, cudaStream_t s) {
+                     const Params& prm, double* xi, double* r, double* cu, int* st, cudaStream_t s) {
   return launch_pdl(fused_kernel<NC, SLOTS, WPS, ROAD>, dim3(n_tiles), dim3(spc * WPS * 32),
                     smem_bytes<NC, SLOTS, WPS>(prm, spc), s, scenes, layout, obs, tiles, p, c, prm,
-                    xi, r, cu);
+                    xi, r, cu, st);
 }
 
 template <int NC, int SLOTS, int WPS, bool ROAD>
@@ -641,10 +649,10 @@ void set_attr_nc() {
 template <int NC, bool ROAD>
 cudaError_t launch_nc(int wps, const DevScene* scenes, const Layout* layout, const double* obs,
                       const Tile* tiles, int n_tiles, int spc, const double* p, const Consts& c,
-                      const Params& prm, double* xi, double* r, double* cu, cudaStream_t s) {
+                      const Params& prm, double* xi, double* r, double* cu, int* st, cudaStream_t s) {
   const int m = prm.m;
 #define PLAN_L(SL, W) \
-  launch_t<NC, SL, W, ROAD>(scenes, layout, obs, tiles, n_tiles, spc, p, c, prm, xi, r, cu, s)
+  launch_t<NC, SL, W, ROAD>(scenes, layout, obs, tiles, n_tiles, spc, p, c, prm, xi, r, cu, st, s)
   if (wps == 1) return m <= 128 ? PLAN_L(4, 1) : PLAN_L(8, 1);
   if (wps == 2) return m <= 128 ? PLAN_L(2, 2) : PLAN_L(4, 2);
   if (wps == 4) return m <= 128 ? PLAN_L(1, 4) : PLAN_L(2, 4);
@@ -656,10 +664,10 @@ template <bool ROAD>
 cudaError_t launch_road(const DevScene* scenes, const Layout* layout, const double* obs,
                         const Tile* tiles, int n_tiles, int wps, int spc, const double* p,
                         const Consts& c, const Params& prm, double* xi, double* r, double* cu,
-                        cudaStream_t s) {
-  if (prm.n == 8) return launch_nc<8, ROAD>(wps, scenes, layout, obs, tiles, n_tiles, spc, p, c, prm, xi, r, cu, s);
-  if (prm.n == 11) return launch_nc<11, ROAD>(wps, scenes, layout, obs, tiles, n_tiles, spc, p, c, prm, xi, r, cu, s);
-  if (prm.n == 16) return launch_nc<16, ROAD>(wps, scenes, layout, obs, tiles, n_tiles, spc, p, c, prm, xi, r, cu, s);
+                        int* st, cudaStream_t s) {
+  if (prm.n == 8) return launch_nc<8, ROAD>(wps, scenes, layout, obs, tiles, n_tiles, spc, p, c, prm, xi, r, cu, st, s);
+  if (prm.n == 11) return launch_nc<11, ROAD>(wps, scenes, layout, obs, tiles, n_tiles, spc, p, c, prm, xi, r, cu, st, s);
+  if (prm.n == 16) return launch_nc<16, ROAD>(wps, scenes, layout, obs, tiles, n_tiles, spc, p, c, prm, xi, r, cu, st, s);
   return cudaErrorInvalidValue;
 }
 
@@ -677,6 +685,6 @@ void fused_setup_road();
 cudaError_t launch_fused_f32_road(const DevScene* scenes, const Layout* layout, const double* obs,
                                   const Tile* tiles, int n_tiles, int wps, int spc, const double* p,
                                   const Consts& c, const Params& prm, double* xi, double* r,
-                                  double* cu, cudaStream_t s);
+                                  double* cu, int* st, cudaStream_t s);
 
 }  // namespace plan

@@ -1,6 +1,7 @@
 // Internal declarations of the planner library (device structs, launchers).
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -9,7 +10,7 @@
 namespace plan {
 
 constexpr int kMaxCoef = 16;     // coefficients per axis
-constexpr int kMaxDp = 8;        // entries of p
+constexpr int kMaxDp = PLAN_MAX_DP;   // entries of p (4 + 4 set-points, 2 goal entries)
 constexpr int kMaxObs = 64;      // obstacles per scene
 constexpr int kMaxM = 256;       // timesteps
 constexpr int kMaxEliteC = 2048; // ConstraintEliteSet size
@@ -58,6 +59,49 @@ inline const char* road_invalid(const plan_scene& s, double lane_margin) {
   return nullptr;
 }
 
+// The parameters of cfg that the lower-level solve uses: NULL when valid, else
+// the reason (host side; shared by every entry point that takes a config).
+inline const char* lower_config_invalid(const plan_config& c) {
+  if (c.m < 8 || c.m > kMaxM) return "m must be in [8, 256]";
+  if (c.n_coef < 4 || c.n_coef > kMaxCoef) return "n_coef must be in [4, 16]";
+  if (c.n_seg < 1 || c.n_seg > 4 || c.n_seg > c.m) return "n_seg must be in [1, 4]";
+  if (c.goal != 0 && c.goal != 1) return "goal must be 0 or 1";
+  if (c.goal && c.n_coef < 6) return "goal entries need n_coef >= 6 (five equality rows on the y axis)";
+  if (c.inner_iters < 1) return "inner_iters must be >= 1";
+  if (!(c.dt > 0) || !(c.rho > 0) || !std::isfinite(c.dt) || !std::isfinite(c.rho))
+    return "dt and rho must be finite and > 0";
+  if (!std::isfinite(c.kp_lat) || !std::isfinite(c.kv_lat) || !std::isfinite(c.kp_lon))
+    return "the tracking gains must be finite";
+  if (!(c.v_min >= 0) || !(c.v_max > c.v_min) || !std::isfinite(c.v_max))
+    return "need 0 <= v_min < v_max (finite)";
+  if (!(c.a_max > 0) || !(c.kappa_max > 0) || !(c.c_max > 0) || !std::isfinite(c.a_max) ||
+      !std::isfinite(c.kappa_max) || !std::isfinite(c.c_max))
+    return "a_max, kappa_max, c_max must be finite and > 0";
+  if (!(c.lane_margin >= 0) || !std::isfinite(c.lane_margin)) return "lane_margin must be >= 0";
+  return nullptr;
+}
+
+// A scene's geometry: NULL when valid, else the reason (host side; the
+// obstacle capacity is the caller's check).
+inline const char* scene_invalid(const plan_scene& s, double lane_margin) {
+  if (s.n_lanes < 1) return "n_lanes must be >= 1";
+  if (!(s.lane_width > 0) || !std::isfinite(s.lane_width)) return "lane_width must be > 0";
+  if (!(s.n_lanes * s.lane_width - 2 * lane_margin > 0)) return "road narrower than twice lane_margin";
+  if (s.n_obs < 0) return "n_obs < 0";
+  if (s.n_obs > 0 && !s.obs) return "obs is NULL";
+  const double* e = &s.ego.x;
+  for (int i = 0; i < 6; ++i)
+    if (!std::isfinite(e[i])) return "ego state not finite";
+  if (!std::isfinite(s.kappa_road)) return "kappa_road not finite";
+  for (int i = 0; i < s.n_obs; ++i) {
+    const plan_obstacle& o = s.obs[i];
+    if (!(o.a > 0) || !(o.b > 0) || !std::isfinite(o.a) || !std::isfinite(o.b) ||
+        !std::isfinite(o.x0) || !std::isfinite(o.y0) || !std::isfinite(o.vx) || !std::isfinite(o.vy))
+      return "obstacle invalid (finite entries, axes > 0)";
+  }
+  return road_invalid(s, lane_margin);
+}
+
 // Road curvature and lane limits at x (linear between knots, constant beyond).
 template <class T>
 __host__ __device__ inline void road_eval(const DevScene& sc, T x, T* kappa, T* ylb, T* yub) {
@@ -100,7 +144,7 @@ struct DevCem {
 struct Params {
   int m, n, n_seg, K;
   int L, n_c, q, d_p;
-  int max_obs, pad;
+  int max_obs, goal;   // goal: p ends with x_f, y_f (Eq. final_boundary rows)
   double dt, rho, kp_lat, kv_lat, kp_lon, gamma, eta, cov_eps;
   double v_min, v_max, a_max, kappa_max, c_max, lane_margin, v_des_lo, v_des_hi;
 };
@@ -111,10 +155,14 @@ struct Params {
 //           to ncp = 4 ceil(n / 4) floats, row stride basis32_stride(n) floats
 //           (an odd multiple of 4, so 16-byte loads of 8 consecutive t are
 //           free of shared-memory bank conflicts)
-//   s1_*    [2][n][n_seg + 3]  Step-1 maps: xi_bar_axis = Gs p_axis + Hs b_axis
-//   pj_*    [N + 1][2][n][2n + 3]  per obstacle count N and axis, row k:
+//   s1_*    [2][n][n_seg + ne]  Step-1 maps: xi_bar_axis = Gs p_axis + Hs b_axis
+//   pj_*    [N + 1][2][n][2n + ne]  per obstacle count N and axis, row k:
 //           M[k][:], MP[k][:], C[k][:] with xi = M r + C b (KKT inverse of
 //           the xi-step) and MP = rho M P, P = F^T F + G^T G of that axis.
+// b of an axis (the columns of Hs and C): the initial rows (position,
+// velocity, acceleration at t0) and, with goal entries, the final rows of
+// Eq. final_boundary: x(t_f) on the x axis; y(t_f), ydot(t_f) on the y axis.
+// ne = 3 without goal entries, 5 with them (the x axis leaves column 4 zero).
 struct Consts {
   double* basis64;
   float* basis32;
@@ -123,7 +171,13 @@ struct Consts {
   double* pj64;
   float* pj32;
   int m, n, n_seg, max_obs;
+  int ne, goal;
 };
+
+// Equality rows per axis: 3 initial rows, plus 1 (x) or 2 (y) final rows.
+__host__ __device__ constexpr int eq_rows(int axis, int goal) {
+  return 3 + (goal ? (axis == 0 ? 1 : 2) : 0);
+}
 
 // Layout of one call: scene s owns samples [off, off + B).
 struct Layout {
@@ -179,7 +233,7 @@ bool fused_shape_ok(int wps, int spc);
 cudaError_t launch_fused_f32(const DevScene* scenes, const Layout* layout, const double* obs,
                              const Tile* tiles, int n_tiles, int wps, int spc, const double* p,
                              const Consts& c, const Params& prm, double* xi, double* r,
-                             double* cu, bool road, cudaStream_t s);
+                             double* cu, int* st, bool road, cudaStream_t s);
 
 // Tensor-core modes (PLAN_PREC_TF32, _BF16, _TF32X3): tiles of
 // tc_samples_per_cta() samples; err is set to 1 if a wait timed out.
@@ -188,7 +242,7 @@ void tc_setup();
 int tc_samples_per_cta();
 cudaError_t launch_tc(int prec, const DevScene* scenes, const Layout* layout, const double* obs,
                       const Tile* tiles, int n_tiles, const double* p, const Consts& c,
-                      const Params& prm, double* xi, double* r, double* cu, int* err,
+                      const Params& prm, double* xi, double* r, double* cu, int* st, int* err,
                       cudaStream_t s);
 // One bounded mbarrier wait that receives no arrival (k_tc.cu): *timed_out = 1
 // when it gave up after `limit` SM cycles.  Synchronous on s.
@@ -217,7 +271,7 @@ struct Plain64Work {   // HBM intermediates of the FP64 path
 cudaError_t launch_plain64(const DevScene* scenes, const Layout* layout, const int* sample_scene,
                            const double* obs, int total_B, const double* p, const Consts& c,
                            const Params& prm, const Plain64Work& w, double* xi_out, double* r,
-                           double* cu, cudaStream_t s);
+                           double* cu, int* st, cudaStream_t s);
 
 // pdl = false: a full dependency on the preceding work of the stream
 cudaError_t launch_sample(const DevScene* scenes, const Layout* layout, const DevCem* cem, int S,
@@ -260,7 +314,7 @@ namespace plan {
 size_t ctx_bytes(const plan_ctx* ctx);
 const char* ctx_error(const plan_ctx* ctx);
 int ctx_make_state(plan_ctx* ctx, const plan_cem_state* st, int n_lanes, double lane_width,
-                   DevCem* out);
+                   double ego_x, DevCem* out);
 // One Alg. 1 run over S scenes, launched directly (no graph) on `s`: scene
 // slots, states init[s] (or table[gather[s]] where gather[s] >= 0), L outer
 // iterations, then table[scatter[s]] = final state and results (pinned host,

@@ -60,6 +60,15 @@ __global__ void sample_kernel(const DevScene* scenes, const Layout* layout, cons
     }
     for (int e = ns; e < 2 * ns; ++e)
       out[e] = prm.v_des_lo + (prm.v_des_hi - prm.v_des_lo) * unit_open(w[e]);
+    if (prm.goal) {
+      // goal entries: x_f = x0 + v t_f with v ~ U[v_des_lo, v_des_hi], y_f a lane centre
+      const double tf = (prm.m - 1) * prm.dt;
+      const double v = prm.v_des_lo + (prm.v_des_hi - prm.v_des_lo) * unit_open(w[2 * ns]);
+      out[2 * ns] = sc.ego[0] + tf * v;
+      int idx = int(floor(unit_open(w[2 * ns + 1]) * sc.n_lanes));
+      if (idx > sc.n_lanes - 1) idx = sc.n_lanes - 1;
+      out[2 * ns + 1] = (idx + 0.5) * sc.lane_width;
+    }
   } else {
     double z[kMaxDp];
     for (int q = 0; 2 * q < d_p; ++q) {
@@ -277,7 +286,7 @@ __device__ void update_moments(PE p_e, CE c_e, double cmin, int q, int d_p, doub
   __syncthreads();
 }
 
-// Lower Cholesky factor of sigma + eps I (d_p <= 8), single thread.
+// Lower Cholesky factor of sigma + eps I (d_p <= kMaxDp), single thread.
 __device__ void cholesky(const double* sigma, double eps, int d, double* L) {
   for (int i = 0; i < kMaxDp * kMaxDp; ++i) L[i] = 0.0;
   for (int jc = 0; jc < d; ++jc) {

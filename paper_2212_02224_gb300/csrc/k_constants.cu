@@ -1,9 +1,12 @@
 // Per-configuration constants, formed and inverted in float64 on the GPU:
 //   * the Bernstein basis W, Wd, Wdd of the trajectory parametrisation (Eq. param),
 //   * the KKT inverse of the Step-1 QP (Alg. 1 line 7, Eq. over_2), folded into
-//     the maps xi_bar = Gs p + Hs b0 per axis,
+//     the maps xi_bar = Gs p + Hs b per axis,
 //   * the KKT inverse of the projection xi-step (Alg. 2, Eq. split_xy) for every
-//     obstacle count N, folded into xi = M r + C b0 and MP = rho M P.
+//     obstacle count N, folded into xi = M r + C b and MP = rho M P.
+// The equality rows A of an axis (Eq. lower_eq) are the initial rows of
+// Eq. boundary_cond_initial and, with goal entries in p, the final rows of
+// Eq. final_boundary: x(t_f) = x_f; y(t_f) = y_f, ydot(t_f) = 0.
 #include "internal.cuh"
 
 namespace plan {
@@ -88,6 +91,14 @@ __device__ void gauss_jordan(double* a, int sz, int ld, int* piv_row) {
   }
 }
 
+// Entry i of equality row e of an axis: e = 0, 1, 2 are the rows of W, Wd,
+// Wdd at t0; e = 3 the row of W at t_f; e = 4 the row of Wd at t_f.
+__device__ double eq_entry(const Consts& c, int e, int i) {
+  const int m = c.m, n = c.n;
+  if (e < 3) return c.basis64[size_t(e) * m * n + i];
+  return c.basis64[size_t(e - 3) * m * n + size_t(m - 1) * n + i];
+}
+
 // One block per job: job 0/1 = Step-1 x/y, job 2 + 2N + axis = projection.
 __global__ void kkt_kernel(Consts c, Params p) {
   const int m = c.m, n = c.n, ns = c.n_seg;
@@ -96,16 +107,18 @@ __global__ void kkt_kernel(Consts c, Params p) {
   const double* Wd = c.basis64 + m * n;
   const double* Wdd = c.basis64 + 2 * m * n;
 
-  extern __shared__ double sh[];
-  const int sz = n + 3, ld = 2 * sz;
-  double* a = sh;                      // sz x ld
-  double* gram = a + sz * ld;          // n x n (P or Q/2 pieces)
-  double* ext = gram + n * n;          // n x ns (L^T S) for step 1
-  __shared__ int piv;
-
   const bool step1 = job < 2;
   const int axis = step1 ? job : (job - 2) % 2;
   const int N = step1 ? 0 : (job - 2) / 2;
+  const int ne = eq_rows(axis, c.goal);   // equality rows of this axis
+
+  extern __shared__ double sh[];
+  const int sz = n + ne, ld = 2 * sz;
+  const int szmax = n + c.ne;
+  double* a = sh;                      // sz x ld (room for szmax x 2 szmax)
+  double* gram = a + szmax * 2 * szmax;   // n x n (P or Q/2 pieces)
+  double* ext = gram + n * n;          // n x ns (L^T S) for step 1
+  __shared__ int piv;
 
   // Gram matrix of the axis.
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
@@ -154,11 +167,9 @@ __global__ void kkt_kernel(Consts c, Params p) {
       if (r < n && j < n) {
         v = step1 ? gram[r * n + j] : p.rho * gram[r * n + j] + (r == j ? 1.0 : 0.0);
       } else if (r < n && j >= n) {
-        const double* Arow = c.basis64 + (j - n) * m * n;  // row 0 of W / Wd / Wdd
-        v = Arow[r];
+        v = eq_entry(c, j - n, r);        // A^T
       } else if (r >= n && j < n) {
-        const double* Arow = c.basis64 + (r - n) * m * n;
-        v = Arow[j];
+        v = eq_entry(c, r - n, j);        // A
       }
     } else {
       v = (j - sz == r) ? 1.0 : 0.0;
@@ -171,7 +182,7 @@ __global__ void kkt_kernel(Consts c, Params p) {
   const double* inv = a + sz;
   if (step1) {
     const double kp = axis == 0 ? p.kp_lon : p.kp_lat;
-    const int stride = ns + 3;
+    const int stride = ns + c.ne;
     double* o64 = c.s1_64 + axis * n * stride;
     float* o32 = c.s1_32 + axis * n * stride;
     for (int e = threadIdx.x; e < n * stride; e += blockDim.x) {
@@ -182,13 +193,13 @@ __global__ void kkt_kernel(Consts c, Params p) {
         v = 0.0;
         for (int i = 0; i < n; ++i) v += inv[k * ld + i] * 2.0 * kp * ext[i * ns + j];
       } else {
-        v = inv[k * ld + n + (j - ns)];
+        v = (j - ns < ne) ? inv[k * ld + n + (j - ns)] : 0.0;
       }
       o64[e] = v;
       o32[e] = float(v);
     }
   } else {
-    const int stride = 2 * n + 3;
+    const int stride = 2 * n + c.ne;
     double* o64 = c.pj64 + (N * 2 + axis) * n * stride;
     float* o32 = c.pj32 + (N * 2 + axis) * n * stride;
     for (int e = threadIdx.x; e < n * stride; e += blockDim.x) {
@@ -202,7 +213,7 @@ __global__ void kkt_kernel(Consts c, Params p) {
         for (int i = 0; i < n; ++i) v += inv[k * ld + i] * gram[i * n + jj];
         v *= p.rho;
       } else {
-        v = inv[k * ld + n + (j - 2 * n)];
+        v = (j - 2 * n < ne) ? inv[k * ld + n + (j - 2 * n)] : 0.0;
       }
       o64[e] = v;
       o32[e] = float(v);
@@ -219,7 +230,7 @@ cudaError_t build_constants(const Consts& c, const Params& p, cudaStream_t s) {
   basis_kernel<<<(mn + 127) / 128, 128, 0, s>>>(c.m, c.n, p.dt, c.basis64, c.basis32);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  int sz = c.n + 3;
+  const int sz = c.n + c.ne;
   size_t shm = sizeof(double) * (sz * 2 * sz + c.n * c.n + c.n * c.n_seg);
   int jobs = 2 + 2 * (c.max_obs + 1);
   kkt_kernel<<<jobs, 256, shm, s>>>(c, p);

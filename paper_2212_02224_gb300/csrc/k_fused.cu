@@ -23,13 +23,13 @@ bool fused_shape_ok(int wps, int spc) {
 cudaError_t launch_fused_f32(const DevScene* scenes, const Layout* layout, const double* obs,
                              const Tile* tiles, int n_tiles, int wps, int spc, const double* p,
                              const Consts& c, const Params& prm, double* xi, double* r,
-                             double* cu, bool road, cudaStream_t s) {
+                             double* cu, int* st, bool road, cudaStream_t s) {
   if (n_tiles == 0) return cudaSuccess;
   if (!fused_shape_ok(wps, spc)) return cudaErrorInvalidValue;
   if (road)
     return launch_fused_f32_road(scenes, layout, obs, tiles, n_tiles, wps, spc, p, c, prm, xi, r,
-                                 cu, s);
-  return launch_road<false>(scenes, layout, obs, tiles, n_tiles, wps, spc, p, c, prm, xi, r, cu, s);
+                                 cu, st, s);
+  return launch_road<false>(scenes, layout, obs, tiles, n_tiles, wps, spc, p, c, prm, xi, r, cu, st, s);
 }
 
 }  // namespace plan

@@ -13,32 +13,36 @@ namespace {
 __device__ __forceinline__ int scene_of(const int* sample_scene, int j) { return sample_scene[j]; }
 
 // Step 1 (xi_bar = Gs p_axis + Hs b_axis), xi^0 = xi_bar, lambda^0 = 0 and the
-// constant part M xi_bar + C b0 of the xi-step.  One 32-thread block per sample,
-// thread = coefficient slot (axis = slot / 16, k = slot % 16).
+// constant part M xi_bar + C b of the xi-step.  b_axis: the initial state and,
+// with goal entries, x_f (x axis) or y_f and ydot_f = 0 (y axis), per sample.
+// One 32-thread block per sample, thread = coefficient slot (axis = slot / 16,
+// k = slot % 16).
 __global__ void step1_kernel(const DevScene* scenes, const int* sample_scene, const double* p,
                              Consts c, Params prm, Plain64Work w) {
   const int j = blockIdx.x;
   const int lane = threadIdx.x;
-  const int n = prm.n, ns = prm.n_seg;
+  const int n = prm.n, ns = prm.n_seg, ne = c.ne;
   const int axis = lane >> 4, k = lane & 15;
   const bool valid = k < n;
   const DevScene& sc = scenes[scene_of(sample_scene, j)];
+  const double* pj = p + size_t(j) * prm.d_p;
   __shared__ double xb[32];
-  double b0 = sc.ego[axis], b1 = sc.ego[axis + 2], b2 = sc.ego[axis + 4];
+  double b[5] = {sc.ego[axis], sc.ego[axis + 2], sc.ego[axis + 4], 0.0, 0.0};
+  if (prm.goal) b[3] = pj[2 * ns + axis];
   if (valid) {
-    const double* s1 = c.s1_64 + size_t(axis * n + k) * (ns + 3);
-    const double* pj = p + size_t(j) * 2 * ns;
+    const double* s1 = c.s1_64 + size_t(axis * n + k) * (ns + ne);
     double v = 0.0;
     for (int q = 0; q < ns; ++q) v += s1[q] * pj[(axis == 0 ? ns : 0) + q];
-    v += s1[ns] * b0 + s1[ns + 1] * b1 + s1[ns + 2] * b2;
+    for (int e = 0; e < ne; ++e) v += s1[ns + e] * b[e];
     xb[lane] = v;
     w.xi[size_t(j) * 32 + lane] = v;
     w.lam[size_t(j) * 32 + lane] = 0.0;
   }
   __syncthreads();
   if (valid) {
-    const double* row = c.pj64 + size_t((sc.n_obs * 2 + axis) * n + k) * (2 * n + 3);
-    double v = row[2 * n] * b0 + row[2 * n + 1] * b1 + row[2 * n + 2] * b2;
+    const double* row = c.pj64 + size_t((sc.n_obs * 2 + axis) * n + k) * (2 * n + ne);
+    double v = 0.0;
+    for (int e = 0; e < ne; ++e) v += row[2 * n + e] * b[e];
     for (int i = 0; i < n; ++i) v += row[i] * xb[axis * 16 + i];
     w.xibarp[size_t(j) * 32 + lane] = v;
   }
@@ -170,17 +174,18 @@ __global__ void update_kernel(const DevScene* scenes, const int* sample_scene, C
   }
   __syncthreads();
   if (valid) {
-    const double* row = c.pj64 + size_t((sc.n_obs * 2 + axis) * n + k) * (2 * n + 3);
+    const double* row = c.pj64 + size_t((sc.n_obs * 2 + axis) * n + k) * (2 * n + c.ne);
     double acc = w.xibarp[size_t(j) * 32 + lane];
     for (int i = 0; i < n; ++i) acc += row[i] * v[axis * 16 + i] + row[n + i] * xo[axis * 16 + i];
     w.xi[size_t(j) * 32 + lane] = acc;
   }
 }
 
-// r_j and c_u of xi^K (one warp per sample, lanes over t), and the xi output.
+// r_j and c_u of xi^K (one warp per sample, lanes over t), the xi output and
+// the per-sample status (solution, residual and cost finite).
 __global__ void score_kernel(const DevScene* scenes, const int* sample_scene, const double* obs,
                              Params prm, Plain64Work w, double* xi_out, double* r_out,
-                             double* cu_out) {
+                             double* cu_out, int* st_out) {
   const int j = blockIdx.x, lane = threadIdx.x;
   const int m = prm.m, n = prm.n;
   const DevScene& sc = scenes[scene_of(sample_scene, j)];
@@ -213,7 +218,12 @@ __global__ void score_kernel(const DevScene* scenes, const int* sample_scene, co
   }
   if (lane == 0) { r_out[j] = r; cu_out[j] = cu; }
   const int axis = lane >> 4, k = lane & 15;
-  if (xi_out != nullptr && k < n) xi_out[size_t(j) * 2 * n + axis * n + k] = w.xi[size_t(j) * 32 + lane];
+  const double xv = k < n ? w.xi[size_t(j) * 32 + lane] : 0.0;
+  if (xi_out != nullptr && k < n) xi_out[size_t(j) * 2 * n + axis * n + k] = xv;
+  if (st_out != nullptr) {
+    const bool bad = __any_sync(0xffffffffu, !isfinite(xv)) || !isfinite(r) || !isfinite(cu);
+    if (lane == 0) st_out[j] = bad ? PLAN_ENONFINITE : PLAN_OK;
+  }
 }
 
 }  // namespace
@@ -221,7 +231,7 @@ __global__ void score_kernel(const DevScene* scenes, const int* sample_scene, co
 cudaError_t launch_plain64(const DevScene* scenes, const Layout* layout, const int* sample_scene,
                            const double* obs, int total_B, const double* p, const Consts& c,
                            const Params& prm, const Plain64Work& w, double* xi_out, double* r,
-                           double* cu, cudaStream_t s) {
+                           double* cu, int* st, cudaStream_t s) {
   (void)layout;
   if (total_B == 0) return cudaSuccess;
   const int tm = total_B * prm.m;
@@ -234,7 +244,7 @@ cudaError_t launch_plain64(const DevScene* scenes, const Layout* layout, const i
     update_kernel<<<total_B, 32, 0, s>>>(scenes, sample_scene, c, prm, w, it);
   }
   forward_kernel<<<grid, blk, 0, s>>>(total_B, c, prm, w);
-  score_kernel<<<total_B, 32, 0, s>>>(scenes, sample_scene, obs, prm, w, xi_out, r, cu);
+  score_kernel<<<total_B, 32, 0, s>>>(scenes, sample_scene, obs, prm, w, xi_out, r, cu, st);
   return cudaGetLastError();
 }
 

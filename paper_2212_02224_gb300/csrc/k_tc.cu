@@ -197,7 +197,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 tc_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ layout,
           const double* __restrict__ obs, const Tile* __restrict__ tiles,
           const double* __restrict__ pin, Consts c, Params prm, double* __restrict__ xi_out,
-          double* __restrict__ r_out, double* __restrict__ cu_out, int* __restrict__ err) {
+          double* __restrict__ r_out, double* __restrict__ cu_out, int* __restrict__ st_out,
+          int* __restrict__ err) {
   using T = Tc<MODE>;
   using LY = TcLayout<NC, MODE>;
   constexpr int NCP = basis32_ncp(NC);
@@ -212,6 +213,7 @@ tc_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ layout
   __shared__ float sMoved[kTcSamples];
   __shared__ float sScore[8][4][2];
   __shared__ float sIab[2];
+  __shared__ int sBadXi[kTcSamples];      // a coefficient of the sample's solution is not finite
 
   const int m = prm.m, ns = prm.n_seg;
   const int mK = LY::mk(m);
@@ -255,10 +257,10 @@ tc_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ layout
   for (int e = tid; e < 2 * kMaxCoef * kMaxCoef; e += kTcThreads) {
     const int ax_ = e / (kMaxCoef * kMaxCoef), k_ = (e / kMaxCoef) % kMaxCoef, i_ = e % kMaxCoef;
     sM[ax_][k_][i_] = (k_ < NC && i_ < NC)
-                          ? c.pj32[size_t((N * 2 + ax_) * NC + k_) * (2 * NC + 3) + i_]
+                          ? c.pj32[size_t((N * 2 + ax_) * NC + k_) * (2 * NC + c.ne) + i_]
                           : 0.f;
   }
-  if (tid < kTcSamples) sMoved[tid] = 0.f;
+  if (tid < kTcSamples) { sMoved[tid] = 0.f; sBadXi[tid] = 0; }
   if (warp == 0) {
     float ia_max = 0.f, ib_max = 0.f;
     for (int i = lane; i < N; i += 32) {
@@ -281,14 +283,16 @@ tc_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ layout
   const int jcol = layout[tile.scene].off + tile.first + cs;   // sample of this column
   float xb_l = 0.f;
   if (slot) {
-    // xi_bar = Gs p_axis + Hs b_axis in float64 (Step 1, Eq. over_3)
-    const double* s1 = c.s1_64 + size_t(caxis * NC + kk) * (ns + 3);
-    const double* pj = pin + size_t(jcol) * (2 * ns);
+    // xi_bar = Gs p_axis + Hs b_axis in float64 (Step 1, Eq. over_3); with goal
+    // entries b_axis also holds x_f (x) or y_f (y)
+    const double* s1 = c.s1_64 + size_t(caxis * NC + kk) * (ns + c.ne);
+    const double* pj = pin + size_t(jcol) * prm.d_p;
     double xb = 0.0;
     for (int q = 0; q < ns; ++q) xb = fma(s1[q], pj[(caxis == 0 ? ns : 0) + q], xb);
     xb = fma(s1[ns], sc.ego[caxis], xb);
     xb = fma(s1[ns + 1], sc.ego[caxis + 2], xb);
     xb = fma(s1[ns + 2], sc.ego[caxis + 4], xb);
+    if (prm.goal) xb = fma(s1[ns + 3], pj[2 * ns + caxis], xb);
     xb_l = float(xb);
   }
   sXb[col][kk] = xb_l;
@@ -600,6 +604,7 @@ tc_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ layout
       if (lane == 0) { sScore[warp][sl][0] = r_acc[sl]; sScore[warp][sl][1] = cu_acc[sl]; }
     }
   }
+  if (slot && !(isfinite(xb_l) && isfinite(dl))) sBadXi[cs] = 1;
   __syncthreads();
   if (tid < kTcSamples && tid < tile.count) {
     const int g4 = tid >> 2, sl = tid & 3;
@@ -609,6 +614,9 @@ tc_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ layout
     for (int qq = 0; qq < 4; ++qq) { rs += sScore[4 * g4 + qq][sl][0]; cs_ += sScore[4 * g4 + qq][sl][1]; }
     r_out[j] = failed ? __longlong_as_double(0x7ff8000000000000ll) : double(rs);
     cu_out[j] = failed ? __longlong_as_double(0x7ff8000000000000ll) : double(cs_);
+    if (st_out != nullptr)
+      st_out[j] = (failed || sBadXi[tid] || !isfinite(rs) || !isfinite(cs_)) ? PLAN_ENONFINITE
+                                                                               : PLAN_OK;
   }
   if (xi_out != nullptr && slot)
     xi_out[size_t(jcol) * 2 * NC + caxis * NC + kk] = double(xb_l) + double(dl);
@@ -632,22 +640,22 @@ size_t tc_smem(const Params& prm) {
 template <int NC, int MODE>
 cudaError_t tc_launch(const DevScene* scenes, const Layout* layout, const double* obs,
                       const Tile* tiles, int n_tiles, const double* p, const Consts& c,
-                      const Params& prm, double* xi, double* r, double* cu, int* err,
+                      const Params& prm, double* xi, double* r, double* cu, int* st, int* err,
                       cudaStream_t s) {
   const size_t bytes = tc_smem<NC, MODE>(prm);
   tc_kernel<NC, MODE><<<n_tiles, kTcThreads, bytes, s>>>(scenes, layout, obs, tiles, p, c, prm, xi,
-                                                          r, cu, err);
+                                                          r, cu, st, err);
   return cudaGetLastError();
 }
 
 template <int MODE>
 cudaError_t tc_launch_mode(const DevScene* scenes, const Layout* layout, const double* obs,
                            const Tile* tiles, int n_tiles, const double* p, const Consts& c,
-                           const Params& prm, double* xi, double* r, double* cu, int* err,
+                           const Params& prm, double* xi, double* r, double* cu, int* st, int* err,
                            cudaStream_t s) {
-  if (prm.n == 8) return tc_launch<8, MODE>(scenes, layout, obs, tiles, n_tiles, p, c, prm, xi, r, cu, err, s);
-  if (prm.n == 11) return tc_launch<11, MODE>(scenes, layout, obs, tiles, n_tiles, p, c, prm, xi, r, cu, err, s);
-  if (prm.n == 16) return tc_launch<16, MODE>(scenes, layout, obs, tiles, n_tiles, p, c, prm, xi, r, cu, err, s);
+  if (prm.n == 8) return tc_launch<8, MODE>(scenes, layout, obs, tiles, n_tiles, p, c, prm, xi, r, cu, st, err, s);
+  if (prm.n == 11) return tc_launch<11, MODE>(scenes, layout, obs, tiles, n_tiles, p, c, prm, xi, r, cu, st, err, s);
+  if (prm.n == 16) return tc_launch<16, MODE>(scenes, layout, obs, tiles, n_tiles, p, c, prm, xi, r, cu, st, err, s);
   return cudaErrorInvalidValue;
 }
 
@@ -697,15 +705,15 @@ cudaError_t wait_probe(long long limit, cudaStream_t s, int* timed_out) {
 
 cudaError_t launch_tc(int prec, const DevScene* scenes, const Layout* layout, const double* obs,
                       const Tile* tiles, int n_tiles, const double* p, const Consts& c,
-                      const Params& prm, double* xi, double* r, double* cu, int* err,
+                      const Params& prm, double* xi, double* r, double* cu, int* st, int* err,
                       cudaStream_t s) {
   if (n_tiles == 0) return cudaSuccess;
   if (prec == PLAN_PREC_TF32)
-    return tc_launch_mode<PLAN_PREC_TF32>(scenes, layout, obs, tiles, n_tiles, p, c, prm, xi, r, cu, err, s);
+    return tc_launch_mode<PLAN_PREC_TF32>(scenes, layout, obs, tiles, n_tiles, p, c, prm, xi, r, cu, st, err, s);
   if (prec == PLAN_PREC_TF32X3)
-    return tc_launch_mode<PLAN_PREC_TF32X3>(scenes, layout, obs, tiles, n_tiles, p, c, prm, xi, r, cu, err, s);
+    return tc_launch_mode<PLAN_PREC_TF32X3>(scenes, layout, obs, tiles, n_tiles, p, c, prm, xi, r, cu, st, err, s);
   if (prec == PLAN_PREC_BF16)
-    return tc_launch_mode<PLAN_PREC_BF16>(scenes, layout, obs, tiles, n_tiles, p, c, prm, xi, r, cu, err, s);
+    return tc_launch_mode<PLAN_PREC_BF16>(scenes, layout, obs, tiles, n_tiles, p, c, prm, xi, r, cu, st, err, s);
   return cudaErrorInvalidValue;
 }
 

@@ -18,6 +18,7 @@ constexpr int kNaMaxM = 128;      // timesteps
 constexpr int kNaMaxObs = 32;     // obstacles
 constexpr int kNaMaxN = kMaxCoef; // coefficients per axis
 constexpr int kNaMaxSeg = 4;
+constexpr int kNaMaxNe = 5;       // equality rows per axis (with goal entries)
 
 namespace {
 
@@ -30,10 +31,10 @@ constexpr size_t kLayout = al(sizeof(Layout));
 constexpr size_t kSampleScene = al(sizeof(int) * kNaMaxB);
 constexpr size_t kBasis64 = al(sizeof(double) * 3 * kNaMaxM * kNaMaxN);
 constexpr size_t kBasis32 = al(sizeof(float) * kNaMaxM * basis32_stride(kNaMaxN));
-constexpr size_t kS1_64 = al(sizeof(double) * 2 * kNaMaxN * (kNaMaxSeg + 3));
-constexpr size_t kS1_32 = al(sizeof(float) * 2 * kNaMaxN * (kNaMaxSeg + 3));
-constexpr size_t kPj64 = al(sizeof(double) * (kNaMaxObs + 1) * 2 * kNaMaxN * (2 * kNaMaxN + 3));
-constexpr size_t kPj32 = al(sizeof(float) * (kNaMaxObs + 1) * 2 * kNaMaxN * (2 * kNaMaxN + 3));
+constexpr size_t kS1_64 = al(sizeof(double) * 2 * kNaMaxN * (kNaMaxSeg + kNaMaxNe));
+constexpr size_t kS1_32 = al(sizeof(float) * 2 * kNaMaxN * (kNaMaxSeg + kNaMaxNe));
+constexpr size_t kPj64 = al(sizeof(double) * (kNaMaxObs + 1) * 2 * kNaMaxN * (2 * kNaMaxN + kNaMaxNe));
+constexpr size_t kPj32 = al(sizeof(float) * (kNaMaxObs + 1) * 2 * kNaMaxN * (2 * kNaMaxN + kNaMaxNe));
 constexpr size_t kVec = al(sizeof(double) * kNaMaxB * 32);
 constexpr size_t kState = al(sizeof(double) * kNaMaxB * 6 * kNaMaxM);
 constexpr size_t kEps = al(sizeof(double) * kNaMaxB * 7 * kNaMaxM);
@@ -84,22 +85,12 @@ extern "C" int plan_solve_fp64_noalloc(const plan_config* cfg, const plan_scene*
   if (!cfg || !scene) return na_fail(PLAN_EINVAL, "cfg and scene must be non-NULL");
   if (B < 0) return na_fail(PLAN_EINVAL, "B < 0");
   if (B > kNaMaxB) return na_fail(PLAN_ECAPACITY, "B exceeds 256 samples");
-  if (cfg->m < 8 || cfg->m > kNaMaxM) return na_fail(PLAN_ECAPACITY, "m must be in [8, 128]");
-  if (cfg->n_coef < 4 || cfg->n_coef > kNaMaxN) return na_fail(PLAN_EINVAL, "n_coef must be in [4, 16]");
-  if (cfg->n_seg < 1 || cfg->n_seg > kNaMaxSeg) return na_fail(PLAN_EINVAL, "n_seg must be in [1, 4]");
-  if (cfg->inner_iters < 1) return na_fail(PLAN_EINVAL, "inner_iters must be >= 1");
-  if (!(cfg->dt > 0) || !(cfg->rho > 0) || !(cfg->kappa_max > 0) || !(cfg->v_max > cfg->v_min))
-    return na_fail(PLAN_EINVAL, "need dt, rho, kappa_max > 0 and v_min < v_max");
-  if (scene->n_obs < 0 || scene->n_obs > kNaMaxObs)
-    return na_fail(PLAN_ECAPACITY, "n_obs must be in [0, 32]");
-  if (scene->n_obs > 0 && !scene->obs) return na_fail(PLAN_EINVAL, "obs is NULL");
-  if (scene->n_lanes < 1 || !(scene->lane_width > 0) ||
-      !(scene->n_lanes * scene->lane_width - 2 * cfg->lane_margin > 0))
-    return na_fail(PLAN_EINVAL, "invalid lanes");
-  for (int i = 0; i < scene->n_obs; ++i)
-    if (!(scene->obs[i].a > 0) || !(scene->obs[i].b > 0))
-      return na_fail(PLAN_EINVAL, "obstacle axes must be > 0");
-  if (const char* why = road_invalid(*scene, cfg->lane_margin)) return na_fail(PLAN_EINVAL, why);
+  if (cfg->m > kNaMaxM) return na_fail(PLAN_ECAPACITY, "m must be in [8, 128]");
+  // the same checks of the lower-level parameters and of the scene as plan_init
+  // and plan_solve make
+  if (const char* why = lower_config_invalid(*cfg)) return na_fail(PLAN_EINVAL, why);
+  if (scene->n_obs > kNaMaxObs) return na_fail(PLAN_ECAPACITY, "n_obs must be in [0, 32]");
+  if (const char* why = scene_invalid(*scene, cfg->lane_margin)) return na_fail(PLAN_EINVAL, why);
   if (B == 0) return PLAN_OK;
   if (!p || !resid || !cu) return na_fail(PLAN_EINVAL, "p, resid and cu must be non-NULL");
 
@@ -141,6 +132,8 @@ extern "C" int plan_solve_fp64_noalloc(const plan_config* cfg, const plan_scene*
   c.n = cfg->n_coef;
   c.n_seg = cfg->n_seg;
   c.max_obs = scene->n_obs;
+  c.goal = cfg->goal;
+  c.ne = 3 + 2 * cfg->goal;
   Plain64Work w{};
   w.xibarp = reinterpret_cast<double*>(take(kVec));
   w.xi = reinterpret_cast<double*>(take(kVec));
@@ -153,7 +146,8 @@ extern "C" int plan_solve_fp64_noalloc(const plan_config* cfg, const plan_scene*
 
   Params prm{};
   prm.m = cfg->m; prm.n = cfg->n_coef; prm.n_seg = cfg->n_seg; prm.K = cfg->inner_iters;
-  prm.L = 1; prm.d_p = 2 * cfg->n_seg; prm.max_obs = scene->n_obs;
+  prm.L = 1; prm.d_p = 2 * cfg->n_seg + 2 * cfg->goal; prm.max_obs = scene->n_obs;
+  prm.goal = cfg->goal;
   prm.dt = cfg->dt; prm.rho = cfg->rho; prm.kp_lat = cfg->kp_lat; prm.kv_lat = cfg->kv_lat;
   prm.kp_lon = cfg->kp_lon; prm.v_min = cfg->v_min; prm.v_max = cfg->v_max;
   prm.a_max = cfg->a_max; prm.kappa_max = cfg->kappa_max; prm.c_max = cfg->c_max;
@@ -184,7 +178,7 @@ extern "C" int plan_solve_fp64_noalloc(const plan_config* cfg, const plan_scene*
   cudaError_t err = cudaGetLastError();
   if (err == cudaSuccess) err = build_constants(c, prm, s);
   if (err == cudaSuccess)
-    err = launch_plain64(d_sc, d_lay, d_ss, d_obs, B, p, c, prm, w, xi, resid, cu, s);
+    err = launch_plain64(d_sc, d_lay, d_ss, d_obs, B, p, c, prm, w, xi, resid, cu, nullptr, s);
   if (err != cudaSuccess) return na_fail(PLAN_ECUDA, cudaGetErrorString(err));
   return PLAN_OK;
 }

@@ -151,10 +151,7 @@ int validate_config(const plan_config* cfg, std::string* why) {
   char b[256];
   auto bad = [&](const char* m) { *why = m; return PLAN_EINVAL; };
   if (!cfg) return bad("cfg is NULL");
-  if (cfg->m < 8 || cfg->m > kMaxM) return bad("m must be in [8, 256]");
-  if (cfg->n_coef < 4 || cfg->n_coef > kMaxCoef) return bad("n_coef must be in [4, 16]");
-  if (cfg->n_seg < 1 || cfg->n_seg > 4 || cfg->n_seg > cfg->m) return bad("n_seg must be in [1, 4]");
-  if (cfg->inner_iters < 1) return bad("inner_iters must be >= 1");
+  if (const char* why_lower = lower_config_invalid(*cfg)) return bad(why_lower);
   if (cfg->outer_iters < 1 || cfg->outer_iters > 65535) return bad("outer_iters must be in [1, 65535]");
   if (cfg->n_elite < 1) return bad("n_elite must be >= 1");
   if (cfg->n_elite_c > kMaxEliteC || (cfg->n_elite_c <= 0 && 3 * cfg->n_elite > kMaxEliteC))
@@ -168,40 +165,22 @@ int validate_config(const plan_config* cfg, std::string* why) {
   if (cfg->max_obs < 0 || cfg->max_obs > kMaxObs) return bad("max_obs must be in [0, 64]");
   if (cfg->max_samples < 1 || cfg->max_samples > (1 << 24)) return bad("max_samples must be in [1, 2^24]");
   if (cfg->max_scenes < 1 || cfg->max_scenes > 65535) return bad("max_scenes must be in [1, 65535]");
-  if (!(cfg->dt > 0) || !(cfg->rho > 0) || !(cfg->gamma > 0)) return bad("dt, rho, gamma must be > 0");
+  if (!(cfg->gamma > 0)) return bad("gamma must be > 0");
   if (!(cfg->eta > 0 && cfg->eta <= 1)) return bad("eta must be in (0, 1]");
   if (!(cfg->cov_eps >= 0)) return bad("cov_eps must be >= 0");
-  if (!(cfg->v_min >= 0) || !(cfg->v_max > cfg->v_min)) return bad("need 0 <= v_min < v_max");
-  if (!(cfg->a_max > 0) || !(cfg->kappa_max > 0) || !(cfg->c_max > 0))
-    return bad("a_max, kappa_max, c_max must be > 0");
-  if (!(cfg->lane_margin >= 0)) return bad("lane_margin must be >= 0");
-  if (!(cfg->v_des_hi >= cfg->v_des_lo)) return bad("v_des_hi must be >= v_des_lo");
+  if (!(cfg->v_des_hi >= cfg->v_des_lo) || !std::isfinite(cfg->v_des_lo) ||
+      !std::isfinite(cfg->v_des_hi))
+    return bad("v_des_hi must be >= v_des_lo (finite)");
   (void)b;
   return PLAN_OK;
 }
 
 int check_scene(plan_ctx* ctx, const plan_scene* s, int idx) {
   if (!s) return fail(ctx, PLAN_EINVAL, "scene %d is NULL", idx);
-  if (s->n_lanes < 1) return fail(ctx, PLAN_EINVAL, "scene %d: n_lanes must be >= 1", idx);
-  if (!(s->lane_width > 0)) return fail(ctx, PLAN_EINVAL, "scene %d: lane_width must be > 0", idx);
-  if (!(s->n_lanes * s->lane_width - 2 * ctx->cfg.lane_margin > 0))
-    return fail(ctx, PLAN_EINVAL, "scene %d: road narrower than twice lane_margin", idx);
-  if (s->n_obs < 0) return fail(ctx, PLAN_EINVAL, "scene %d: n_obs < 0", idx);
   if (s->n_obs > ctx->cfg.max_obs)
     return fail(ctx, PLAN_ECAPACITY, "scene %d: n_obs %d exceeds max_obs %d", idx, s->n_obs,
                 ctx->cfg.max_obs);
-  if (s->n_obs > 0 && !s->obs) return fail(ctx, PLAN_EINVAL, "scene %d: obs is NULL", idx);
-  const double* e = &s->ego.x;
-  for (int i = 0; i < 6; ++i)
-    if (!std::isfinite(e[i])) return fail(ctx, PLAN_EINVAL, "scene %d: ego state not finite", idx);
-  if (!std::isfinite(s->kappa_road)) return fail(ctx, PLAN_EINVAL, "scene %d: kappa_road", idx);
-  for (int i = 0; i < s->n_obs; ++i) {
-    const plan_obstacle& o = s->obs[i];
-    if (!(o.a > 0) || !(o.b > 0) || !std::isfinite(o.x0) || !std::isfinite(o.y0) ||
-        !std::isfinite(o.vx) || !std::isfinite(o.vy))
-      return fail(ctx, PLAN_EINVAL, "scene %d: obstacle %d invalid (axes must be > 0)", idx, i);
-  }
-  if (const char* why = road_invalid(*s, ctx->cfg.lane_margin))
+  if (const char* why = scene_invalid(*s, ctx->cfg.lane_margin))
     return fail(ctx, PLAN_EINVAL, "scene %d: %s", idx, why);
   return PLAN_OK;
 }
@@ -329,19 +308,20 @@ int upload(plan_ctx* ctx, SceneSet& set, const plan_scene* scenes, int S, const 
 }
 
 // Lower-level solve of all samples described by `set` (Alg. 1 lines 6-9).
+// status: per-sample PLAN_OK / PLAN_ENONFINITE, or NULL.
 cudaError_t run_solve(plan_ctx* ctx, const SceneSet& set, const SceneSet& lay, int n_tiles,
                       int total_B, const double* p, double* xi, double* r, double* cu,
-                      cudaStream_t s) {
+                      int* status, cudaStream_t s) {
   if (ctx->cfg.prec == PLAN_PREC_FP32) {
     const Shape sh = pick_shape(ctx, total_B);
     return launch_fused_f32(set.scenes, lay.layout, set.obs, lay.tiles, n_tiles, sh.wps, sh.spc,
-                            p, ctx->c, ctx->prm, xi, r, cu, set.road, s);
+                            p, ctx->c, ctx->prm, xi, r, cu, status, set.road, s);
   }
   if (ctx->cfg.prec >= PLAN_PREC_TF32)
     return launch_tc(ctx->cfg.prec, set.scenes, lay.layout, set.obs, lay.tiles, n_tiles, p, ctx->c,
-                     ctx->prm, xi, r, cu, ctx->tc_err, s);
+                     ctx->prm, xi, r, cu, status, ctx->tc_err, s);
   return launch_plain64(set.scenes, lay.layout, lay.sample_scene, set.obs, total_B, p, ctx->c,
-                        ctx->prm, ctx->pw, xi, r, cu, s);
+                        ctx->prm, ctx->pw, xi, r, cu, status, s);
 }
 
 int n_tiles_of(const std::vector<int>& B, int warps) {
@@ -368,9 +348,12 @@ void chol_host(const double* A, double eps, int d, double* L, bool* ok) {
 }
 
 // DevCem from a host state; the initial moments of a fresh episode follow
-// from the uniform first-iteration distribution of the scene's lanes.
-int make_cem(plan_ctx* ctx, const plan_cem_state* st, int n_lanes, double lane_width, DevCem* out) {
-  const int ns = ctx->cfg.n_seg, d = 2 * ns;
+// from the uniform first-iteration distribution of the scene's lanes (and,
+// with goal entries, of x_f = ego_x + U[v_des_lo, v_des_hi] t_f and a
+// lane-centre y_f).
+int make_cem(plan_ctx* ctx, const plan_cem_state* st, int n_lanes, double lane_width, double ego_x,
+             DevCem* out) {
+  const int ns = ctx->cfg.n_seg, d = ctx->prm.d_p;
   DevCem c{};
   c.seed = st->seed;
   c.step = st->episode_step;
@@ -378,16 +361,25 @@ int make_cem(plan_ctx* ctx, const plan_cem_state* st, int n_lanes, double lane_w
   if (c.fresh) {
     const double L = n_lanes, w = lane_width;
     const double lo = ctx->cfg.v_des_lo, hi = ctx->cfg.v_des_hi;
+    const double lane_mu = L * w / 2.0, lane_var = w * w * (L * L - 1.0) / 12.0;
+    const double v_mu = 0.5 * (lo + hi), v_var = (hi - lo) * (hi - lo) / 12.0;
     for (int e = 0; e < ns; ++e) {
-      c.mu[e] = L * w / 2.0;
-      c.mu[ns + e] = 0.5 * (lo + hi);
-      c.sigma[e * kMaxDp + e] = w * w * (L * L - 1.0) / 12.0;
-      c.sigma[(ns + e) * kMaxDp + ns + e] = (hi - lo) * (hi - lo) / 12.0;
+      c.mu[e] = lane_mu;
+      c.mu[ns + e] = v_mu;
+      c.sigma[e * kMaxDp + e] = lane_var;
+      c.sigma[(ns + e) * kMaxDp + ns + e] = v_var;
+    }
+    if (ctx->cfg.goal) {
+      const double tf = (ctx->cfg.m - 1) * ctx->cfg.dt;
+      c.mu[2 * ns] = ego_x + tf * v_mu;
+      c.sigma[(2 * ns) * kMaxDp + 2 * ns] = tf * tf * v_var;
+      c.mu[2 * ns + 1] = lane_mu;
+      c.sigma[(2 * ns + 1) * kMaxDp + 2 * ns + 1] = lane_var;
     }
   } else {
     for (int a = 0; a < d; ++a) {
       c.mu[a] = st->mu[a];
-      for (int b = 0; b < d; ++b) c.sigma[a * kMaxDp + b] = st->sigma[a * 8 + b];
+      for (int b = 0; b < d; ++b) c.sigma[a * kMaxDp + b] = st->sigma[a * PLAN_MAX_DP + b];
     }
   }
   for (int a = 0; a < d; ++a)
@@ -410,8 +402,8 @@ size_t plan::ctx_bytes(const plan_ctx* ctx) { return ctx->arena_bytes; }
 const char* plan::ctx_error(const plan_ctx* ctx) { return ctx->err.c_str(); }
 
 int plan::ctx_make_state(plan_ctx* ctx, const plan_cem_state* st, int n_lanes, double lane_width,
-                         DevCem* out) {
-  return make_cem(ctx, st, n_lanes, lane_width, out);
+                         double ego_x, DevCem* out) {
+  return make_cem(ctx, st, n_lanes, lane_width, ego_x, out);
 }
 
 int plan::ctx_wave(plan_ctx* ctx, const plan_scene* scenes, const int* B, int S,
@@ -443,7 +435,8 @@ int plan::ctx_wave(plan_ctx* ctx, const plan_scene* scenes, const int* B, int S,
   const int nt = n_tiles_of(Bv, pick_warps(ctx, int(total)));
   for (int l = 1; l <= ctx->cfg.outer_iters; ++l) {
     CU(ctx, launch_sample(ctx->res.scenes, ctx->res.layout, ctx->cem, S, max_B, l, ctx->prm, ctx->p, s));
-    CU(ctx, run_solve(ctx, ctx->res, ctx->res, nt, int(total), ctx->p, ctx->xi, ctx->r, ctx->cu, s));
+    CU(ctx, run_solve(ctx, ctx->res, ctx->res, nt, int(total), ctx->p, ctx->xi, ctx->r, ctx->cu,
+                      nullptr, s));
     CU(ctx, launch_select_update(ctx->res.layout, ctx->cem, S, l, ctx->prm, ctx->p, ctx->xi,
                                  ctx->r, ctx->cu, ctx->elite, max_B, s));
   }
@@ -505,7 +498,7 @@ int plan_init(const plan_config* cfg, plan_ctx** out) {
   Params& p = ctx->prm;
   p.m = c.m; p.n = c.n_coef; p.n_seg = c.n_seg; p.K = c.inner_iters; p.L = c.outer_iters;
   p.q = c.n_elite; p.n_c = c.n_elite_c > 0 ? c.n_elite_c : 3 * c.n_elite;
-  p.d_p = 2 * c.n_seg; p.max_obs = c.max_obs;
+  p.d_p = 2 * c.n_seg + 2 * c.goal; p.max_obs = c.max_obs; p.goal = c.goal;
   p.dt = c.dt; p.rho = c.rho; p.kp_lat = c.kp_lat; p.kv_lat = c.kv_lat; p.kp_lon = c.kp_lon;
   p.gamma = c.gamma; p.eta = c.eta; p.cov_eps = c.cov_eps; p.v_min = c.v_min; p.v_max = c.v_max;
   p.a_max = c.a_max; p.kappa_max = c.kappa_max; p.c_max = c.c_max; p.lane_margin = c.lane_margin;
@@ -527,18 +520,19 @@ int plan_init(const plan_config* cfg, plan_ctx** out) {
     cudaGetLastError();
     return bail(PLAN_ECUDA);
   }
-  const int m = c.m, n = c.n_coef, ns = c.n_seg, d = 2 * ns;
+  const int m = c.m, n = c.n_coef, ns = c.n_seg, d = p.d_p;
   const size_t B = c.max_samples;
   Consts& k = ctx->c;
   k.m = m; k.n = n; k.n_seg = ns; k.max_obs = c.max_obs;
+  k.goal = c.goal; k.ne = 3 + 2 * c.goal;
   int st = PLAN_OK;
   auto A = [&](int s) { if (st == PLAN_OK) st = s; };
   A(dalloc(ctx, &k.basis64, size_t(3) * m * n));
   A(dalloc(ctx, &k.basis32, size_t(m) * basis32_stride(n)));
-  A(dalloc(ctx, &k.s1_64, size_t(2) * n * (ns + 3)));
-  A(dalloc(ctx, &k.s1_32, size_t(2) * n * (ns + 3)));
-  A(dalloc(ctx, &k.pj64, size_t(c.max_obs + 1) * 2 * n * (2 * n + 3)));
-  A(dalloc(ctx, &k.pj32, size_t(c.max_obs + 1) * 2 * n * (2 * n + 3)));
+  A(dalloc(ctx, &k.s1_64, size_t(2) * n * (ns + k.ne)));
+  A(dalloc(ctx, &k.s1_32, size_t(2) * n * (ns + k.ne)));
+  A(dalloc(ctx, &k.pj64, size_t(c.max_obs + 1) * 2 * n * (2 * n + k.ne)));
+  A(dalloc(ctx, &k.pj32, size_t(c.max_obs + 1) * 2 * n * (2 * n + k.ne)));
   if (st == PLAN_OK) A(alloc_set(ctx, ctx->tr, true));
   if (st == PLAN_OK) A(alloc_set(ctx, ctx->res, true));
   A(dalloc(ctx, &ctx->cem, c.max_scenes));
@@ -594,7 +588,7 @@ int plan_init(const plan_config* cfg, plan_ctx** out) {
 }
 
 int plan_solve_batch(plan_ctx* ctx, const plan_scene* scenes, const int* B, int S, const double* p,
-                     double* xi, double* resid, double* cu, void* stream) {
+                     double* xi, double* resid, double* cu, int* status, void* stream) {
   if (!ctx) return PLAN_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (S < 0 || (S > 0 && (!scenes || !B))) return fail(ctx, PLAN_EINVAL, "bad scenes / B");
@@ -612,14 +606,15 @@ int plan_solve_batch(plan_ctx* ctx, const plan_scene* scenes, const int* B, int 
   CU(ctx, cudaSetDevice(ctx->device));
   TRY(upload(ctx, ctx->tr, scenes, S, &Bv, s, nullptr));
   const int spc = pick_warps(ctx, int(total));
-  CU(ctx, run_solve(ctx, ctx->tr, ctx->tr, n_tiles_of(Bv, spc), int(total), p, xi, resid, cu, s));
+  CU(ctx, run_solve(ctx, ctx->tr, ctx->tr, n_tiles_of(Bv, spc), int(total), p, xi, resid, cu,
+                    status, s));
   return PLAN_OK;
 }
 
 int plan_solve(plan_ctx* ctx, const plan_scene* scene, const double* p, int B, double* xi,
-               double* resid, double* cu, void* stream) {
+               double* resid, double* cu, int* status, void* stream) {
   if (!ctx) return PLAN_EINVAL;
-  return plan_solve_batch(ctx, scene, &B, 1, p, xi, resid, cu, stream);
+  return plan_solve_batch(ctx, scene, &B, 1, p, xi, resid, cu, status, stream);
 }
 
 int plan_upload_scenes(plan_ctx* ctx, const plan_scene* scenes, int S, void* stream) {
@@ -639,7 +634,8 @@ int plan_set_state(plan_ctx* ctx, int slot, const plan_cem_state* st, void* stre
   if (slot < 0 || slot >= ctx->n_uploaded)
     return fail(ctx, PLAN_ESTATE, "slot %d has no uploaded scene", slot);
   DevCem c;
-  TRY(make_cem(ctx, st, ctx->res_host[slot].n_lanes, ctx->res_host[slot].lane_width, &c));
+  TRY(make_cem(ctx, st, ctx->res_host[slot].n_lanes, ctx->res_host[slot].lane_width,
+               ctx->res_host[slot].ego[0], &c));
   CU(ctx, cudaSetDevice(ctx->device));
   TRY(stage_acquire(ctx, sizeof(DevCem)));
   std::memcpy(ctx->stage, &c, sizeof c);
@@ -649,11 +645,11 @@ int plan_set_state(plan_ctx* ctx, int slot, const plan_cem_state* st, void* stre
 }
 
 void cem_to_state(const plan_ctx* ctx, const DevCem& c, plan_cem_state* st) {
-  const int d = 2 * ctx->cfg.n_seg;
+  const int d = ctx->prm.d_p;
   std::memset(st, 0, sizeof *st);
   for (int a = 0; a < d; ++a) {
     st->mu[a] = c.mu[a];
-    for (int b = 0; b < d; ++b) st->sigma[a * 8 + b] = c.sigma[a * kMaxDp + b];
+    for (int b = 0; b < d; ++b) st->sigma[a * PLAN_MAX_DP + b] = c.sigma[a * kMaxDp + b];
   }
   st->seed = c.seed;
   st->episode_step = c.step;
@@ -662,7 +658,7 @@ void cem_to_state(const plan_ctx* ctx, const DevCem& c, plan_cem_state* st) {
 
 void cem_to_result(const plan_ctx* ctx, const DevCem& c, plan_result* out) {
   std::memset(out, 0, sizeof *out);
-  for (int a = 0; a < 2 * ctx->cfg.n_seg; ++a) out->p[a] = c.best_p[a];
+  for (int a = 0; a < ctx->prm.d_p; ++a) out->p[a] = c.best_p[a];
   for (int a = 0; a < 2 * ctx->cfg.n_coef; ++a) out->xi[a] = c.best_xi[a];
   out->cost = c.best_cost;
   out->resid = c.best_r;
@@ -768,7 +764,7 @@ int run_cycle(plan_ctx* ctx, const int* B, int S, void* stream, bool io) {
                          ctx->capture, !(io && l == 1));
       if (ce == cudaSuccess)
         ce = run_solve(ctx, e.set, e.set, nt, int(total), ctx->p, ctx->xi, ctx->r, ctx->cu,
-                       ctx->capture);
+                       nullptr, ctx->capture);
       if (ce == cudaSuccess)
         ce = launch_select_update(e.set.layout, ctx->cem, S, l, ctx->prm, ctx->p, ctx->xi, ctx->r,
                                   ctx->cu, ctx->elite, max_B, ctx->capture);
@@ -811,7 +807,7 @@ int plan_step(plan_ctx* ctx, const plan_scene* scene, plan_cem_state* st, int B,
   TRY(check_scene(ctx, scene, 0));
   if (B < 1 || B > ctx->cfg.max_samples) return fail(ctx, PLAN_ECAPACITY, "B out of range");
   DevCem c0;
-  TRY(make_cem(ctx, st, scene->n_lanes, scene->lane_width, &c0));
+  TRY(make_cem(ctx, st, scene->n_lanes, scene->lane_width, scene->ego.x, &c0));
   CU(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // scene, obstacles and state go into the host-mapped staging buffer; the
@@ -864,7 +860,7 @@ int plan_update_distribution(plan_ctx* ctx, const double* p_elite, const double*
   if (!p_elite || !cost || !mu || !sigma) return fail(ctx, PLAN_EINVAL, "NULL buffer");
   if (q < 1 || q > kMaxEliteC) return fail(ctx, PLAN_EINVAL, "q must be in [1, 2048]");
   CU(ctx, cudaSetDevice(ctx->device));
-  CU(ctx, launch_update_only(p_elite, cost, q, 2 * ctx->cfg.n_seg, ctx->cfg.gamma, ctx->cfg.eta, mu,
+  CU(ctx, launch_update_only(p_elite, cost, q, ctx->prm.d_p, ctx->cfg.gamma, ctx->cfg.eta, mu,
                              sigma, static_cast<cudaStream_t>(stream)));
   return PLAN_OK;
 }
@@ -936,17 +932,17 @@ int plan_sample(plan_ctx* ctx, const plan_scene* scene, const double* mu, const 
   TRY(check_scene(ctx, scene, 0));
   if (B == 0) return PLAN_OK;
   plan_cem_state st{};
-  const int d = 2 * ctx->cfg.n_seg;
+  const int d = ctx->prm.d_p;
   if (!fresh)
     for (int a = 0; a < d; ++a) {
       st.mu[a] = mu[a];
-      for (int b = 0; b < d; ++b) st.sigma[a * 8 + b] = sigma[a * d + b];
+      for (int b = 0; b < d; ++b) st.sigma[a * PLAN_MAX_DP + b] = sigma[a * d + b];
     }
   st.seed = seed;
   st.episode_step = episode_step;
   st.fresh = fresh;
   DevCem c;
-  TRY(make_cem(ctx, &st, scene->n_lanes, scene->lane_width, &c));
+  TRY(make_cem(ctx, &st, scene->n_lanes, scene->lane_width, scene->ego.x, &c));
   CU(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::vector<int> Bv{B};
@@ -1024,10 +1020,10 @@ int plan_autotune(plan_ctx* ctx, const plan_scene* scene, int B, int* wps_out, i
     if (st_code != PLAN_OK) break;
     const int nt = n_tiles_of(Bv, cnd[1]);
     float times[3];
-    cudaError_t ce = run_solve(ctx, ctx->tr, ctx->tr, nt, B, ctx->p, nullptr, ctx->r, ctx->cu, s);
+    cudaError_t ce = run_solve(ctx, ctx->tr, ctx->tr, nt, B, ctx->p, nullptr, ctx->r, ctx->cu, nullptr, s);
     for (int rep = 0; rep < 3 && ce == cudaSuccess; ++rep) {
       cudaEventRecord(e0, s);
-      ce = run_solve(ctx, ctx->tr, ctx->tr, nt, B, ctx->p, nullptr, ctx->r, ctx->cu, s);
+      ce = run_solve(ctx, ctx->tr, ctx->tr, nt, B, ctx->p, nullptr, ctx->r, ctx->cu, nullptr, s);
       cudaEventRecord(e1, s);
       if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
       if (ce == cudaSuccess) ce = cudaEventElapsedTime(&times[rep], e0, e1);

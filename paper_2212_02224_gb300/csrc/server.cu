@@ -144,7 +144,7 @@ int make_executor(plan_server* s, int m, std::unique_ptr<Executor>* out) {
 // Complete the tickets of a finished wave (caller holds the lock).
 void finalize(plan_server* s, Executor* e) {
   const double t = now_us();
-  const int d_p = 2 * s->base.n_seg, nx = 2 * s->base.n_coef;
+  const int d_p = 2 * s->base.n_seg + 2 * s->base.goal, nx = 2 * s->base.n_coef;
   for (size_t i = 0; i < e->wave.size(); ++i) {
     const Request& r = e->wave[i];
     Ticket& tk = s->tickets[r.ticket];
@@ -203,7 +203,8 @@ int run_wave(plan_server* s, Executor* e) {
     plan_cem_state cs{};
     cs.seed = r.seed;
     cs.fresh = 1;
-    st = ctx_make_state(e->ctx, &cs, r.scene.n_lanes, r.scene.lane_width, &e->h_init[i]);
+    st = ctx_make_state(e->ctx, &cs, r.scene.n_lanes, r.scene.lane_width, r.scene.ego.x,
+                        &e->h_init[i]);
     gather[i] = r.fresh ? -1 : r.row;
     scatter[i] = r.row;
   }

@@ -43,7 +43,7 @@ class Planner:
         self.cfg = B.make_config(params, self.prec, max_obs, max_samples, max_scenes)
         self.ctx = B.plan_init(self.cfg)
         self.n = params.n_coef
-        self.d_p = 2 * params.n_seg
+        self.d_p = 2 * params.n_seg + (2 if getattr(params, "goal", False) else 0)
 
     def close(self):
         if self.ctx is not None:
@@ -57,24 +57,31 @@ class Planner:
             pass
 
     # -------------------------------------------------------------- lower level
-    def solve(self, scene, p: torch.Tensor, stream=None, want_xi: bool = True):
+    def solve(self, scene, p: torch.Tensor, stream=None, want_xi: bool = True,
+              want_status: bool = False):
+        """(xi, r, c_u) of plan_solve, and the per-sample status (int32, PLAN_OK or
+        PLAN_ENONFINITE) as a fourth entry when want_status."""
         Bn = p.shape[0]
         _need(p, (Bn, self.d_p), "p")
         dev = p.device
         xi = torch.empty((Bn, 2 * self.n), dtype=torch.float64, device=dev) if want_xi else None
         r = torch.empty(Bn, dtype=torch.float64, device=dev)
         cu = torch.empty(Bn, dtype=torch.float64, device=dev)
-        B.plan_solve(self.ctx, scene, _ptr(p), Bn, _ptr(xi), _ptr(r), _ptr(cu), _stream(stream))
-        return xi, r, cu
+        st = torch.empty(Bn, dtype=torch.int32, device=dev) if want_status else None
+        B.plan_solve(self.ctx, scene, _ptr(p), Bn, _ptr(xi), _ptr(r), _ptr(cu), _ptr(st) or None,
+                     _stream(stream))
+        return (xi, r, cu, st) if want_status else (xi, r, cu)
 
-    def solve_batch(self, scenes, Bs, p: torch.Tensor, stream=None):
+    def solve_batch(self, scenes, Bs, p: torch.Tensor, stream=None, want_status: bool = False):
         tot = int(sum(Bs))
         _need(p, (tot, self.d_p), "p")
         xi = torch.empty((tot, 2 * self.n), dtype=torch.float64, device=p.device)
         r = torch.empty(tot, dtype=torch.float64, device=p.device)
         cu = torch.empty(tot, dtype=torch.float64, device=p.device)
-        B.plan_solve_batch(self.ctx, scenes, Bs, _ptr(p), _ptr(xi), _ptr(r), _ptr(cu), _stream(stream))
-        return xi, r, cu
+        st = torch.empty(tot, dtype=torch.int32, device=p.device) if want_status else None
+        B.plan_solve_batch(self.ctx, scenes, Bs, _ptr(p), _ptr(xi), _ptr(r), _ptr(cu),
+                           _ptr(st) or None, _stream(stream))
+        return (xi, r, cu, st) if want_status else (xi, r, cu)
 
     # -------------------------------------------------------------- Alg. 1
     def upload(self, scenes, stream=None):
@@ -188,7 +195,8 @@ class Server:
         p = B.PRECISIONS[prec]
         self.cfg = B.make_config(params, p, max_obs, max_samples, max_scenes)
         self.srv = B.plan_server_create(self.cfg, max_executors, device_budget, max_episodes)
-        self.n, self.d_p = params.n_coef, 2 * params.n_seg
+        self.n = params.n_coef
+        self.d_p = 2 * params.n_seg + (2 if getattr(params, "goal", False) else 0)
 
     def submit(self, scene, Bn: int, m: int = 0, episode: int = 0, seed: int = 0, fresh: int = 0):
         return B.plan_submit(self.srv, scene, Bn, m, episode, seed, fresh)

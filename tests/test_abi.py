@@ -74,7 +74,7 @@ def test_fp32_kernel_coefficient_counts():
 
 def test_null_context_is_rejected():
     lib = _lib()
-    assert lib.plan_solve(None, None, None, 0, None, None, None, None) == binding.PLAN_EINVAL
+    assert lib.plan_solve(None, None, None, 0, None, None, None, None, None) == binding.PLAN_EINVAL
     assert lib.plan_destroy(None) == binding.PLAN_OK
 
 

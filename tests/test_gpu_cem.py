@@ -121,7 +121,7 @@ def test_mpc_cycle_fp32():
     xo, ro, co = lower.solve(np.array([res["p"]]), sc, prm, basis)
     xg, yg = positions(np.array([res["xi"]]), prm)
     xr, yr = positions(xo, prm)
-    assert max(np.abs(xg - xr).max(), np.abs(yg - yr).max()) <= FP32_POS_M
+    assert float(np.hypot(xg - xr, yg - yr).max()) <= FP32_POS_M
     assert abs(res["cost"] - (co[0] + ro[0])) <= 1e-4 * abs(co[0] + ro[0]) + 1e-3
     assert res["cost"] <= ref["cost"] * 1.05 + 1e-3
 

@@ -78,7 +78,7 @@ def test_server_episode_matches_plan_step():
         mu, sigma = r_p["mu"], r_p["sigma"]
         xs, ys = positions(np.array([r_s["xi"]]), prm)
         xp, yp = positions(np.array([r_p["xi"]]), prm)
-        assert max(np.abs(xs - xp).max(), np.abs(ys - yp).max()) <= FP32_POS_M
+        assert float(np.hypot(xs - xp, ys - yp).max()) <= FP32_POS_M
         assert abs(r_s["cost"] - r_p["cost"]) <= 1e-4 * abs(r_p["cost"]) + 1e-3
         sc_s = advance(prm, sc_s, r_s["xi"])
         sc_p = advance(prm, sc_p, r_p["xi"])

@@ -43,7 +43,7 @@ def _check(prec, prm, g, o):
     bp, br, bc = BARS[prec]
     xg, yg = positions(g[0], prm)
     xo, yo = positions(o[0], prm)
-    e_pos = max(np.abs(xg - xo).max(), np.abs(yg - yo).max())
+    e_pos = float(np.hypot(xg - xo, yg - yo).max())
     e_r = np.abs(g[1] - o[1]).max()
     e_cu = (np.abs(g[2] - o[2]) / np.maximum(1e-12, np.abs(o[2]))).max()
     assert e_pos <= bp, f"{prec}: position err {e_pos} m"
@@ -133,7 +133,7 @@ def test_mpc_cycle_tf32x3():
     xo, ro, co = _oracle(prm, sc, np.array([res["p"]]))
     xg, yg = positions(np.array([res["xi"]]), prm)
     xr, yr = positions(xo, prm)
-    assert max(np.abs(xg - xr).max(), np.abs(yg - yr).max()) <= FP32_POS_M
+    assert float(np.hypot(xg - xr, yg - yr).max()) <= FP32_POS_M
     assert abs(res["cost"] - (co[0] + ro[0])) <= 1e-4 * abs(co[0] + ro[0]) + 1e-3
     assert res["cost"] <= ref["cost"] * 1.05 + 1e-3
 
