@@ -103,3 +103,34 @@ def test_diagnostics_check_their_arguments_before_the_device():
     for bad in (0, 100001):
         assert lib.plan_probe_wait_timeout(bad, None) == binding.PLAN_EINVAL
         assert "wait_us" in binding.last_error(None)
+
+
+@pytest.mark.parametrize("what", ["ego_nan", "obstacle_inf", "kappa_road_nan", "a_max", "c_max",
+                                  "lane_margin", "goal_narrow_basis", "goal_flag"])
+def test_noalloc_rejects_what_plan_solve_rejects(what):
+    """The allocation-free entry point checks its configuration and scene as
+    plan_init and plan_solve do; these rejections happen before any device
+    call, so they run without a GPU."""
+    lib = _lib()
+    prm = scenegen.Params()
+    sc = scenegen.make_scene(5, n_lanes=3, n_obs=2)
+    if what == "ego_nan":
+        sc.ego[2] = float("nan")
+    elif what == "obstacle_inf":
+        sc.obstacles[1, 0] = float("inf")
+    elif what == "kappa_road_nan":
+        sc.kappa_road = float("nan")
+    elif what == "a_max":
+        prm.a_max = 0.0
+    elif what == "c_max":
+        prm.c_max = -1.0
+    elif what == "lane_margin":
+        prm.lane_margin = -0.5
+    elif what == "goal_narrow_basis":
+        prm.goal, prm.n_coef = True, 5
+    cfg = binding.make_config(prm, binding.PLAN_PREC_FP64, 8, 8)
+    if what == "goal_flag":
+        cfg.goal = 2
+    arr, keep = binding.make_scenes([sc])
+    st = lib.plan_solve_fp64_noalloc(ctypes.byref(cfg), arr, None, 0, None, None, None, None)
+    assert st == binding.PLAN_EINVAL, binding.last_error(None)

@@ -41,7 +41,7 @@ def test_batched_workload_full_size_sampled():
         js = np.unique(pick.integers(0, Bs[sidx] - 1, 3))
         xo, ro, co = lower.solve(ps[sidx][js], scenes[sidx], prm, basis)
         g = offs[sidx] + js
-        compare("fp32", prm, xi[g], r[g], cu[g], xo, ro, co)
+        compare("fp32", prm, xi[g], r[g], cu[g], xo, ro, co, sc=scenes[sidx], p=ps[sidx][js])
 
 
 def test_scale_workload_largest_point_sampled():
@@ -56,4 +56,4 @@ def test_scale_workload_largest_point_sampled():
     assert np.isfinite(r).all() and np.isfinite(cu).all()
     idx = np.unique(sg.Stream(41).integers(0, B - 1, 16))
     xo, ro, co = lower.solve(p[idx], sc, prm, bernstein(prm.m, prm.n_coef, prm.dt))
-    compare("fp32", prm, xi[idx], r[idx], cu[idx], xo, ro, co)
+    compare("fp32", prm, xi[idx], r[idx], cu[idx], xo, ro, co, sc=sc, p=p[idx])

@@ -50,9 +50,9 @@ def test_goal_dense_traffic_parity(prec, n_seg):
     out = _run(prec, prm, sc, p)
     if prec == "tf32x3":
         # split-TF32 products are float32-level: the FP32 bar applies
-        compare("fp32", prm, *out, *_oracle(prm, sc, p))
+        compare("fp32", prm, *out, *_oracle(prm, sc, p), sc=sc, p=p)
     else:
-        compare(prec, prm, *out, *_oracle(prm, sc, p))
+        compare(prec, prm, *out, *_oracle(prm, sc, p), sc=sc, p=p)
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-8), ("fp32", FP32_POS_M)])
@@ -70,20 +70,21 @@ def test_goal_rows_met_by_gpu_plans(prec, tol):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_goal_full_batch_sampled(prec):
-    """B = 1000 goal samples solved together; 24 checked one by one."""
+def test_goal_full_batch(prec):
+    """B = 1000 goal samples solved together, every one compared with the oracle."""
     prm, sc, B = _goal_prm()
     p = _samples(505, sc, prm, B)
-    xi, r, cu = _run(prec, prm, sc, p)
-    idx = np.unique(sg.Stream(17).integers(0, B - 1, 24))
-    compare(prec, prm, xi[idx], r[idx], cu[idx], *_oracle(prm, sc, p[idx]))
+    out = compare(prec, prm, *_run(prec, prm, sc, p), *_oracle(prm, sc, p), sc=sc, p=p)
+    # a goal far short of the set-point speeds makes a few samples brake hard
+    # through the traffic; their outcome bifurcates under float32 rounding
+    assert out.get("ill_conditioned", 0) <= 5
 
 
 @pytest.mark.parametrize("shape", [(1, 8), (2, 2), (4, 1)])
 def test_goal_fused_shapes(shape):
     prm, sc, _ = _goal_prm(inner_iters=40, n_seg=2)
     p = _samples(606, sc, prm, 40)
-    compare("fp32", prm, *_run("fp32", prm, sc, p, shape), *_oracle(prm, sc, p))
+    compare("fp32", prm, *_run("fp32", prm, sc, p, shape), *_oracle(prm, sc, p), sc=sc, p=p)
 
 
 def test_goal_wide_basis_long_horizon():
@@ -91,7 +92,7 @@ def test_goal_wide_basis_long_horizon():
     prm, sc, _ = sg.workload(4, inner_iters=40, goal=True)
     p = _samples(707, sc, prm, 24)
     for prec in ("fp64", "fp32"):
-        compare(prec, prm, *_run(prec, prm, sc, p), *_oracle(prm, sc, p))
+        compare(prec, prm, *_run(prec, prm, sc, p), *_oracle(prm, sc, p), sc=sc, p=p)
 
 
 def test_goal_sampler_matches_oracle_draws():

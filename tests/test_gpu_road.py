@@ -5,11 +5,13 @@ allocation-free entry point, a whole Alg. 1 cycle and the MPC advance.
 
 On a sharp bend whose centripetal limit is far below the velocity set-points
 (kappa = 0.02, c_max = 3: 12 m/s against up to 25 m/s) Alg. 2's clipped
-iterates amplify rounding by about 1.15x per iteration for some samples, so
-float32 paths drift from the float64 oracle as K grows (6e-6 m at K = 10,
-8e-3 m at K = 60) while the float64 path stays within 1e-6.  The float32 paths
-are therefore checked on the sharp bend at K = 10 (the road semantics) and on
-a gentle bend at the full K."""
+iterates amplify rounding for some samples, so the float32 paths drift from
+the float64 oracle as K grows (fused kernel, largest sample of 40: 4.5e-6 m
+at K = 10, 1.4e-4 m at K = 60, 4.5e-4 m at K = 100).  The fused float32
+kernel is held to the float32 bar at the workloads' K = 100 on both bends.
+The split-TF32 tensor-core mode adds its operand rounding (2^-21) to that
+drift; its bar on the bends is derived from the operand-rounding error model
+(tests/error_model.py), never below the float32 bar."""
 import numpy as np
 import pytest
 import torch
@@ -19,7 +21,8 @@ from oracle.basis import bernstein
 from paper_2212_02224_gb300 import binding, scenegen as sg
 from paper_2212_02224_gb300.planner import Planner, advance
 
-from gpu_common import FP32_POS_M, compare, planner, positions, to_dev
+import error_model
+from gpu_common import FP32_COST_REL, FP32_POS_M, FP32_RESID, compare, planner, positions, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -57,21 +60,32 @@ def test_fp64_path_on_a_sharp_bend(origin):
     prm = _prm()
     sc = _road_scene(origin=origin)
     p = sg.make_samples(21, sc, 48, prm.n_seg, v_range=(12.0, 25.0))
-    compare("fp64", prm, *_run("fp64", prm, sc, p), *_oracle(prm, sc, p))
+    compare("fp64", prm, *_run("fp64", prm, sc, p), *_oracle(prm, sc, p), sc=sc, p=p)
 
 
-@pytest.mark.parametrize("prec,shape", [("fp32", (1, 1)), ("fp32", (1, 4)), ("fp32", (2, 1)),
-                                        ("fp32", (2, 2)), ("fp32", (4, 1)), ("tf32x3", None)])
-@pytest.mark.parametrize("bend", ["sharp, K=10", "gentle, K=60"])
+@pytest.mark.parametrize("prec,shape", [("fp32", (1, 1)), ("fp32", (1, 4)), ("fp32", (1, 8)),
+                                        ("fp32", (2, 1)), ("fp32", (2, 2)), ("fp32", (4, 1)),
+                                        ("tf32x3", None)])
+@pytest.mark.parametrize("bend", ["sharp", "gentle"])
 def test_float32_paths_on_curved_roads(prec, shape, bend):
-    if bend.startswith("sharp"):
-        prm = _prm(inner_iters=10)
+    """Both bends at K = 100, the workloads' number of Alg. 2 iterations."""
+    if bend == "sharp":
+        prm = _prm(inner_iters=100)
         sc = _road_scene(seed=12, origin=20.0)
     else:
-        prm = _prm(inner_iters=60, c_max=4.0)
+        prm = _prm(inner_iters=100, c_max=4.0)
         sc = _road_scene(seed=12, kappa=0.008)
     p = sg.make_samples(22, sc, 40, prm.n_seg, v_range=(12.0, 25.0))
-    compare("fp32", prm, *_run(prec, prm, sc, p, shape), *_oracle(prm, sc, p))
+    g, o = _run(prec, prm, sc, p, shape), _oracle(prm, sc, p)
+    if prec == "fp32":
+        compare("fp32", prm, *g, *o, sc=sc, p=p)
+        return
+    bp, br, bc = error_model.derived_bars(prm, sc, p, prec, (FP32_POS_M, FP32_RESID, FP32_COST_REL))
+    xg, yg = positions(g[0], prm)
+    xo, yo = positions(o[0], prm)
+    assert float(np.hypot(xg - xo, yg - yo).max()) <= bp
+    assert (np.abs(g[1] - o[1]) <= br).all()
+    assert (np.abs(g[2] - o[2]) / np.maximum(1e-12, np.abs(o[2]))).max() <= bc
 
 
 def test_noalloc_entry_matches_the_fp64_path_on_a_curved_road():

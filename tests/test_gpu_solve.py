@@ -33,7 +33,7 @@ def test_small_plain_workload(prec):
     """2 lanes, 4 obstacles, B = 64, 50 iterations."""
     prm, sc, B = sg.workload(0)
     p = sg.make_samples(101, sc, B, prm.n_seg)
-    compare(prec, prm, *_run(prec, prm, sc, p), *_oracle(prm, sc, p))
+    compare(prec, prm, *_run(prec, prm, sc, p), *_oracle(prm, sc, p), sc=sc, p=p)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -41,18 +41,16 @@ def test_dense_traffic_scene(prec):
     """4 lanes, 12 obstacles, 100 iterations, 96 samples."""
     prm, sc, _ = sg.workload(1)
     p = sg.make_samples(202, sc, 96, prm.n_seg)
-    compare(prec, prm, *_run(prec, prm, sc, p), *_oracle(prm, sc, p))
+    compare(prec, prm, *_run(prec, prm, sc, p), *_oracle(prm, sc, p), sc=sc, p=p)
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_dense_traffic_full_batch_sampled(prec):
-    """Full size (B = 1000) on the GPU, 24 sampled results checked one by one."""
+def test_dense_traffic_full_batch(prec):
+    """Full size (B = 1000, the bench's launch) on the GPU; every sample is
+    compared with the oracle."""
     prm, sc, B = sg.workload(1)
     p = sg.make_samples(303, sc, B, prm.n_seg)
-    xi, r, cu = _run(prec, prm, sc, p)
-    idx = np.unique(sg.Stream(7).integers(0, B - 1, 24))
-    xo, ro, co = _oracle(prm, sc, p[idx])
-    compare(prec, prm, xi[idx], r[idx], cu[idx], xo, ro, co)
+    compare(prec, prm, *_run(prec, prm, sc, p), *_oracle(prm, sc, p), sc=sc, p=p)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -80,7 +78,7 @@ def test_edge_cases(prec, case):
         prm = sg.Params(m=100, n_coef=11, inner_iters=60)
         sc = scene_with(6, 3, 6, obs_x=(12.0, 50.0), obs_vx=(0.0, 0.0))
         p = sg.make_samples(6, sc, 70, 1)
-    compare(prec, prm, *_run(prec, prm, sc, p, max_obs=max(sc.n_obs, 1)), *_oracle(prm, sc, p))
+    compare(prec, prm, *_run(prec, prm, sc, p, max_obs=max(sc.n_obs, 1)), *_oracle(prm, sc, p), sc=sc, p=p)
 
 
 @pytest.mark.parametrize("prec,shape", [("fp64", None), ("fp32", None), ("fp32", (2, 1)),
@@ -99,7 +97,7 @@ def test_maximum_obstacle_count(prec, shape):
     torch.cuda.synchronize()
     out = xi.cpu().numpy(), r.cpu().numpy(), cu.cpu().numpy()
     pl.close()
-    compare(prec, prm, *out, *_oracle(prm, sc, p))
+    compare(prec, prm, *out, *_oracle(prm, sc, p), sc=sc, p=p)
 
 
 @pytest.mark.parametrize("prec,shape", [("fp64", None), ("fp32", None), ("fp32", (1, 8)),
@@ -118,7 +116,7 @@ def test_longest_horizon(prec, shape):
     torch.cuda.synchronize()
     out = xi.cpu().numpy(), r.cpu().numpy(), cu.cpu().numpy()
     pl.close()
-    compare(prec, prm, *out, *_oracle(prm, sc, p))
+    compare(prec, prm, *out, *_oracle(prm, sc, p), sc=sc, p=p)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -135,7 +133,7 @@ def test_batched_scenes_uneven(prec):
     off = 0
     for i in range(5):
         sl = slice(off, off + Bs[i])
-        compare(prec, prm, xi[sl], r[sl], cu[sl], *_oracle(prm, scenes[i], ps[i]))
+        compare(prec, prm, xi[sl], r[sl], cu[sl], *_oracle(prm, scenes[i], ps[i]), sc=scenes[i], p=ps[i])
         off += Bs[i]
 
 
@@ -178,7 +176,7 @@ def test_fused_kernel_shapes(wps, spc, dense_case):
     pl.set_tuning(wps, spc)
     xi, r, cu = pl.solve(sc, to_dev(p))
     torch.cuda.synchronize()
-    compare("fp32", prm, xi.cpu().numpy(), r.cpu().numpy(), cu.cpu().numpy(), *ref)
+    compare("fp32", prm, xi.cpu().numpy(), r.cpu().numpy(), cu.cpu().numpy(), *ref, sc=sc, p=p)
     pl.close()
 
 
@@ -192,7 +190,8 @@ def test_long_and_ragged_horizons_per_shape(wps, spc):
         pl.set_tuning(wps, spc)
         xi, r, cu = pl.solve(sc, to_dev(p))
         torch.cuda.synchronize()
-        compare("fp32", prm, xi.cpu().numpy(), r.cpu().numpy(), cu.cpu().numpy(), *_oracle(prm, sc, p))
+        compare("fp32", prm, xi.cpu().numpy(), r.cpu().numpy(), cu.cpu().numpy(),
+                *_oracle(prm, sc, p), sc=sc, p=p)
         pl.close()
 
 

@@ -30,7 +30,8 @@ def test_nonfinite_sample_is_flagged_alone(prec, bad):
     ok = np.arange(len(p)) != j_bad
     assert (st[ok] == binding.PLAN_OK).all()
     xo, ro, co = lower.solve(p[ok], sc, prm, bernstein(prm.m, prm.n_coef, prm.dt))
-    compare("fp32" if prec == "tf32x3" else prec, prm, xi[ok], r[ok], cu[ok], xo, ro, co)
+    compare("fp32" if prec == "tf32x3" else prec, prm, xi[ok], r[ok], cu[ok], xo, ro, co, sc=sc,
+            p=p[ok])
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])

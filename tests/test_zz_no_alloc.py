@@ -46,6 +46,74 @@ def test_noalloc_matches_context_solve_twice():
     pl.close()
 
 
+def _noalloc(cfg, sc, p, want_xi=True):
+    B = p.shape[0]
+    n = cfg.n_coef
+    xi = torch.full((B, 2 * n), float("nan"), dtype=torch.float64, device="cuda")
+    r = torch.full((B,), float("nan"), dtype=torch.float64, device="cuda")
+    cu = torch.full((B,), float("nan"), dtype=torch.float64, device="cuda")
+    binding.plan_solve_fp64_noalloc(cfg, sc, p.data_ptr(), B, xi.data_ptr() if want_xi else None,
+                                    r.data_ptr(), cu.data_ptr(),
+                                    torch.cuda.current_stream().cuda_stream)
+    return xi, r, cu
+
+
+def test_noalloc_at_every_limit_then_a_smaller_call():
+    """One call at all five limits at once (B = 256, m = 128, 32 obstacles,
+    16 coefficients, 4 segments), so that every region of the scratch array is
+    used to its end, then a smaller call (fewer obstacles, shorter horizon,
+    narrower basis) on the same stream, which must not see the first call's
+    leftovers.  Both against plan_solve on the float64 path."""
+    big = sg.Params(m=128, n_coef=16, n_seg=4, inner_iters=15)
+    sc_big = sg.make_scene(4321, n_lanes=5, n_obs=32, obs_x=(8.0, 140.0))
+    p_big = sg.make_samples(11, sc_big, 256, 4)
+    small, sc_small, _ = sg.workload(0, inner_iters=25, m=60)
+    p_small = sg.make_samples(12, sc_small, 17, small.n_seg)
+    for prm, sc, p in ((big, sc_big, p_big), (small, sc_small, p_small)):
+        B = p.shape[0]
+        cfg = binding.make_config(prm, binding.PLAN_PREC_FP64, sc.n_obs, B)
+        pt = to_dev(p)
+        xi, r, cu = _noalloc(cfg, sc, pt)
+        pl = planner(prm, "fp64", max_obs=sc.n_obs, max_samples=B)
+        xi_ref, r_ref, cu_ref = pl.solve(sc, pt)
+        torch.cuda.synchronize()
+        pl.close()
+        _cmp(xi.cpu().numpy(), xi_ref.cpu().numpy(), "xi")
+        _cmp(r.cpu().numpy(), r_ref.cpu().numpy(), "resid")
+        _cmp(cu.cpu().numpy(), cu_ref.cpu().numpy(), "cu")
+
+
+def test_noalloc_matches_the_oracle():
+    """A small case straight against the FP64 CPU oracle (1e-6 relative)."""
+    from oracle import lower
+    from oracle.basis import bernstein
+    prm, sc, _ = sg.workload(0, inner_iters=30)
+    p = sg.make_samples(13, sc, 24, prm.n_seg)
+    cfg = binding.make_config(prm, binding.PLAN_PREC_FP64, sc.n_obs, 24)
+    xi, r, cu = _noalloc(cfg, sc, to_dev(p))
+    torch.cuda.synchronize()
+    xo, ro, co = lower.solve(p, sc, prm, bernstein(prm.m, prm.n_coef, prm.dt))
+    scale = np.maximum(1.0, np.abs(xo).max(axis=1))
+    assert (np.abs(xi.cpu().numpy() - xo).max(axis=1) / scale).max() <= FP64_XI_REL
+    assert (np.abs(r.cpu().numpy() - ro) / np.maximum(1.0, np.abs(ro))).max() <= FP64_XI_REL
+    assert (np.abs(cu.cpu().numpy() - co) / np.maximum(1.0, np.abs(co))).max() <= FP64_XI_REL
+
+
+def test_noalloc_with_goal_entries():
+    """The goal rows of Eq. final_boundary on the allocation-free path."""
+    prm, sc, _ = sg.workload(1, inner_iters=30, goal=True, n_seg=2)
+    p = sg.make_samples(14, sc, 64, prm.n_seg, goal_tf=(prm.m - 1) * prm.dt)
+    cfg = binding.make_config(prm, binding.PLAN_PREC_FP64, sc.n_obs, 64)
+    pt = to_dev(p)
+    xi, r, cu = _noalloc(cfg, sc, pt)
+    pl = planner(prm, "fp64", max_obs=sc.n_obs, max_samples=64)
+    xi_ref, r_ref, cu_ref = pl.solve(sc, pt)
+    torch.cuda.synchronize()
+    pl.close()
+    _cmp(xi.cpu().numpy(), xi_ref.cpu().numpy(), "xi")
+    _cmp(r.cpu().numpy(), r_ref.cpu().numpy(), "resid")
+
+
 def test_noalloc_rejects_sizes_beyond_its_limits():
     prm, sc, _ = sg.workload(1, inner_iters=5)
     cfg = binding.make_config(prm, binding.PLAN_PREC_FP64, 16, 512)
