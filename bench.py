@@ -21,6 +21,13 @@ latency_ms : p50 / p99 over --latency-cycles cycles after 50 warm-up cycles,
              on the device (graph) and through plan_step (host wall clock).
 cpu_baseline: the FP64 oracle on a bounded sample, one host thread;
 cpu_baseline_all_cores: the same with one process per host core.
+scale_point : the scale sweep's largest point (6 lanes, 30 obstacles, m = 200,
+              n = 16, B = 32 768): ms per cycle, value and the fused solve's
+              fraction of the FP32 pipe, with its own clock record.
+batched     : the 256-scene workload (N ~ U{4..20}, B ~ U{256..2048}): ms per
+              graph-captured step, value, solve fraction, clocks.
+precision   : one B = 1000 solve per arithmetic mode against the plain FP64 GPU
+              path, and the same with goal entries in p.
 
 --impl reference times the FP64 CPU oracle on the same metric instead.
 """
@@ -46,11 +53,30 @@ UNIT = "sample-iters/s"
 FP32_LANES_PER_SM = 128
 SM_COUNT_NOMINAL = 152
 # DRAM bytes (read + write) of one fused solve of this workload, by kernel shape
-# (warps per sample, samples per CTA), from the ncu captures summarised in
-# profiles/fused_kernel_dense_traffic_B1000.md (traffic section); must be re-taken when the
-# kernel changes.
-FUSED_TRAFFIC_BYTES = {(1, 1): 103168, (1, 2): 96000, (1, 4): 91648, (1, 8): 89344, (2, 1): 93440,
-                       (4, 1): 91648}
+# (warps per sample, samples per CTA), from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum; summary and command under profiles/), together with the
+# SHA-256 of the kernel source it was taken on.  bench.py reports the figure only
+# while the source still has that hash; otherwise traffic is null.
+FUSED_TRAFFIC = {"source_sha256": None, "capture": None, "bytes": {}}
+FUSED_KERNEL_SOURCES = ("paper_2212_02224_gb300/csrc/fused_kernel.cuh",
+                        "paper_2212_02224_gb300/csrc/k_fused.cu")
+
+
+def fused_source_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in FUSED_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def fused_traffic(shape):
+    """(bytes per launch or None, note) for the fused kernel of this shape."""
+    if FUSED_TRAFFIC["source_sha256"] != fused_source_sha256():
+        return None, "no ncu capture of the current kernel source"
+    b = FUSED_TRAFFIC["bytes"].get(tuple(shape))
+    return b, (FUSED_TRAFFIC["capture"] if b is not None else "shape not captured")
 
 
 def algorithmic_flops_per_sample_iter(m, n, N, n_eq=3):
@@ -279,13 +305,17 @@ def precision_modes(prm, sc, p, flush, stream, reps=10):
         pl.close()
         return ms, out
 
+    def pos_err(xi, ref_xi):
+        return float(np.hypot((xi[:, :n] - ref_xi[:, :n]) @ W.T, (xi[:, n:] - ref_xi[:, n:]) @ W.T).max())
+
     ms64, ref = solve("fp64")
     res = {"reference": "plain FP64 GPU path (itself within 1e-6 of the FP64 oracle)",
+           "errors": "largest over the samples: Euclidean distance between the two plans' "
+                     "points at any t, |r - r_ref|, |c_u - c_u,ref| / |c_u,ref|",
            "fp64": {"solve_ms": ms64}}
     for prec in ("fp32", "tf32x3", "tf32", "bf16"):
         ms, (xi, r, cu) = solve(prec)
-        pos = max(np.abs((xi[:, :n] - ref[0][:, :n]) @ W.T).max(),
-                  np.abs((xi[:, n:] - ref[0][:, n:]) @ W.T).max())
+        pos = pos_err(xi, ref[0])
         res[prec] = {"solve_ms": ms, "max_pos_err_m": float(pos),
                      "max_resid_err": float(np.abs(r - ref[1]).max()),
                      "max_cost_rel_err": float((np.abs(cu - ref[2]) /
@@ -293,6 +323,44 @@ def precision_modes(prm, sc, p, flush, stream, reps=10):
                      "contractions": "CUDA-core FP32 FMA" if prec == "fp32" else
                                      f"tcgen05 kind::{'f16 (bf16)' if prec == 'bf16' else 'tf32'}"
                                      f"{' x3 split' if prec == 'tf32x3' else ''}, FP32 accumulate"}
+    # goal entries of p (Eq. behaviour_param's x_f, y_f; Eq. final_boundary rows):
+    # the same scene and set-points with goals drawn as the first-iteration prior
+    import copy
+    from paper_2212_02224_gb300 import scenegen as sg
+    gprm = copy.copy(prm)
+    gprm.goal = True
+    pg = torch.tensor(sg.make_samples(303, sc, B, prm.n_seg, goal_tf=(prm.m - 1) * prm.dt),
+                      dtype=torch.float64, device="cuda")
+    goal = {}
+    outs = {}
+    for prec in ("fp64", "fp32"):
+        pl = Planner(gprm, prec=prec, max_obs=16, max_samples=B)
+        for _ in range(3):
+            pl.solve(sc, pg, want_xi=False)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            pl.solve(sc, pg, want_xi=False)
+            b.record(stream)
+        xi, r, cu = pl.solve(sc, pg)
+        torch.cuda.synchronize()
+        outs[prec] = (xi.cpu().numpy(), r.cpu().numpy(), cu.cpu().numpy())
+        goal[prec] = {"solve_ms": statistics.median(a.elapsed_time(b) for a, b in ev)}
+        pl.close()
+    xi, r, cu = outs["fp32"]
+    xr, rr, cr = outs["fp64"]
+    e = np.hypot((xi[:, :n] - xr[:, :n]) @ W.T, (xi[:, n:] - xr[:, n:]) @ W.T).max(axis=1)
+    goal["fp32"].update({
+        "max_pos_err_m": float(e.max()), "median_pos_err_m": float(np.median(e)),
+        "samples_over_1e-3_m": int((e > 1e-3).sum()),
+        "max_cost_rel_err": float((np.abs(cu - cr) / np.maximum(1e-12, np.abs(cr))).max())})
+    goal["config"] = ("p = [y_d, v_d, x_f, y_f] (d_p = 4), x_f = x0 + U[5, 25] t_f, y_f a lane "
+                      "centre; terminal rows x(t_f), y(t_f), ydot(t_f) in A_eq; errors against "
+                      "the plain FP64 GPU path; samples over 1e-3 m are the ill-conditioned "
+                      "ones (hard braking to the goal)")
+    res["goal"] = goal
     return res
 
 
@@ -379,10 +447,14 @@ def gpu_arm(args):
     e2e_total = ranks.max(sum(e2e_ms) / 1e3)
     e2e_value = replica_value(units, len(e2e_ms), e2e_total, world)
     # plan_step moves, per cycle, from pinned host memory to the device: the
-    # scene record (352 B), its obstacles (48 B each) and the sampling state
-    # (1464 B); back: the final state with the best pair (1464 B) and the
-    # timeout flag (8 B)
-    dev_scene, dev_cem = 352, 1464
+    # scene record, its obstacles (48 B each) and the sampling state; back: the
+    # final state with the best pair and the timeout flag (8 B).  Record sizes:
+    # scene 10 doubles + 4 ints + 8 road knots x 4 doubles; sampling state
+    # mu, best p (PLAN_MAX_DP each), sigma and its Cholesky factor (PLAN_MAX_DP^2
+    # each), best xi (32), 3 doubles, 2 uint64, 4 ints
+    from paper_2212_02224_gb300.binding import PLAN_MAX_DP as DPM
+    dev_scene = 8 * 10 + 4 * 4 + 8 * 32
+    dev_cem = 8 * (2 * DPM + 2 * DPM * DPM + 32 + 3) + 16 + 16
     h2d = dev_scene + 48 * sc.n_obs + dev_cem
     d2h = dev_cem + 8
 
@@ -406,8 +478,18 @@ def gpu_arm(args):
     peak = sms * FP32_LANES_PER_SM * 2 * peak_clock * 1e6 / 1e12
     achieved = flops / (kern_ms * 1e-3) / 1e12
     pl.close()
+    traffic_b, traffic_note = fused_traffic(shape)
     from paper_2212_02224_gb300 import binding
     probe = binding.plan_probe_alu()
+
+    # ---- the scale sweep's largest point (B = 32 768) and the 256-scene batched
+    # step, so that the default line reports them too (each with its own clocks)
+    extra = {}
+    if not args.skip_extra:
+        extra["scale_point"] = scale_point(32768, max(3, min(args.steps, 5)), args.warmup, flush,
+                                           stream, sms, local)
+        extra["batched"] = batched_point(max(3, min(args.steps, 5)), args.warmup, flush, stream,
+                                         sms, local)
 
     # ---- precision modes: one lower-level solve of the same B = 1000 samples per
     # mode, timed alone, and its error against the plain FP64 GPU path
@@ -469,7 +551,8 @@ def gpu_arm(args):
             "speedup_vs_plain_fp64": (value / plain["value"]) if plain else None,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
-                         "traffic": FUSED_TRAFFIC_BYTES.get(tuple(shape)),
+                         "traffic": traffic_b,
+                         "traffic_source": traffic_note,
                          "kernel": f"fused_kernel (n=11, {shape[0]} warp(s)/sample, "
                                    f"{shape[1]} sample(s)/CTA; one lower-level solve, B=1000, K=100)",
                          "kernel_ms": kern_ms,
@@ -482,6 +565,7 @@ def gpu_arm(args):
             "cpu_baseline_all_cores": cpu_all,
             "clocks": clocks,
             "precision": precision,
+            **extra,
         }
         print(json.dumps(line))
     ranks.close()
@@ -530,6 +614,90 @@ def _timed(fn, reps, flush, stream, prep=None):
         b.record(stream)
     torch.cuda.synchronize()
     return [a.elapsed_time(b) for a, b in ev]
+
+
+def fp32_peak_tflops(sms, clocks):
+    clk = (clocks or {}).get("sm_max_mhz") or 2070.0
+    return sms * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+
+
+def scale_point(B, steps, warmup, flush, stream, sms, index=0):
+    """One point of the scale sweep (6 lanes, 30 obstacles, m = 200, n = 16,
+    K = 100, L = 5): device time per graph-captured cycle (fresh planning calls,
+    L2 flushed), and the fused solve timed alone against the FP32 pipe."""
+    import torch
+    from paper_2212_02224_gb300 import scenegen as sg
+    from paper_2212_02224_gb300.planner import Planner
+    prm, sc, _ = sg.workload(4, B=B)
+    pl = Planner(prm, prec="fp32", max_obs=32, max_samples=B)
+    shape = pl.autotune(sc, B)
+    pl.upload([sc])
+
+    def fresh(i):
+        pl.set_state(0, seed=7, step=i)
+
+    for i in range(warmup):
+        fresh(i)
+        pl.step_resident([B])
+    p = torch.tensor(sg.make_samples(3, sc, B, prm.n_seg), device="cuda")
+    with ClockSampler(index) as clk:
+        ms = _timed(lambda: pl.step_resident([B]), steps, flush, stream, prep=fresh)
+        ks = _timed(lambda: pl.solve(sc, p, want_xi=False), 5, flush, stream)
+    clocks = clk.summary()
+    pl.close()
+    flops = algorithmic_flops_per_sample_iter(prm.m, prm.n_coef, sc.n_obs) * B * prm.inner_iters
+    solve_ms = statistics.median(ks)
+    tflops = flops / (solve_ms * 1e-3) / 1e12
+    peak = fp32_peak_tflops(sms, clocks)
+    return {"config": f"6 lanes, N=30, m=200, n=16, B={B}, K=100, L=5", "B": B,
+            "fused_shape": {"warps_per_sample": shape[0], "samples_per_cta": shape[1]},
+            "ms_per_cycle": statistics.median(ms), "cycles": len(ms),
+            "value": B * prm.inner_iters * prm.outer_iters / (statistics.median(ms) / 1e3),
+            "unit": UNIT, "solve_ms": solve_ms, "solve_tflops": tflops, "peak_tflops": peak,
+            "frac": tflops / peak, "clocks": clocks}
+
+
+def batched_point(steps, warmup, flush, stream, sms, index=0):
+    """The batched workload (256 scenes, N ~ U{4..20}, B ~ U{256..2048}): one
+    graph-captured Alg. 1 run over all scenes per step, and its fused solve
+    timed alone against the FP32 pipe."""
+    import torch
+    from paper_2212_02224_gb300 import scenegen as sg
+    from paper_2212_02224_gb300.planner import Planner
+    prm, scenes, Bs = sg.batched_workload(S=256)
+    tot = sum(Bs)
+    pl = Planner(prm, prec="fp32", max_obs=20, max_samples=tot, max_scenes=len(scenes))
+    pl.set_tuning(1, 2)
+    pl.upload(scenes)
+
+    def fresh(i):
+        for k in range(len(scenes)):
+            pl.set_state(k, seed=100 + k, step=i)
+
+    for i in range(warmup):
+        fresh(i)
+        pl.step_resident(Bs)
+    import numpy as np
+    p = torch.tensor(np.concatenate([sg.make_samples(9 + i, scenes[i], Bs[i], prm.n_seg)
+                                     for i in range(len(scenes))]), device="cuda")
+    with ClockSampler(index) as clk:
+        ms = _timed(lambda: pl.step_resident(Bs), steps, flush, stream, prep=fresh)
+        ks = _timed(lambda: pl.solve_batch(scenes, Bs, p), 3, flush, stream)
+    clocks = clk.summary()
+    pl.close()
+    flops = sum(algorithmic_flops_per_sample_iter(prm.m, prm.n_coef, sc.n_obs) * b * prm.inner_iters
+                for sc, b in zip(scenes, Bs))
+    solve_ms = statistics.median(ks)
+    tflops = flops / (solve_ms * 1e-3) / 1e12
+    peak = fp32_peak_tflops(sms, clocks)
+    units = tot * prm.inner_iters * prm.outer_iters
+    return {"config": "256 scenes, N~U{4..20}, B~U{256..2048} (total %d), m=100, n=11, K=100, "
+                      "L=5, one CUDA graph per step" % tot,
+            "ms_per_step": statistics.median(ms), "steps": len(ms),
+            "value": units / (statistics.median(ms) / 1e3), "unit": UNIT,
+            "scenes_per_s": len(scenes) / (statistics.median(ms) / 1e3),
+            "solve_ms": solve_ms, "solve_tflops": tflops, "peak_tflops": peak,
+            "frac": tflops / peak, "clocks": clocks}
 
 
 def batched_arm(args):
@@ -704,6 +872,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-extra", action="store_true",
+                    help="leave out the scale point and the batched step of the default line")
     ap.add_argument("--latency-cycles", type=int, default=1000,
                     help="cycles of the latency run after 50 warm-up cycles (0: none)")
     ap.add_argument("--workload", default="dense", choices=["dense", "batched", "scale", "serving"])

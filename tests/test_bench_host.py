@@ -57,3 +57,18 @@ def test_replica_value_is_whole_job_throughput():
 def test_algorithmic_flops_of_the_bench_workload():
     # 24 m n + 12 N m + 40 m + 4 n^2 + 4 n n_eq at m = 100, n = 11, N = 12, n_eq = 3
     assert bench.algorithmic_flops_per_sample_iter(100, 11, 12) == 26400 + 14400 + 4000 + 484 + 132
+
+
+def test_traffic_is_reported_only_for_the_captured_kernel_source(monkeypatch):
+    """The DRAM traffic of the roofline comes from an ncu capture; it is
+    reported only while the fused kernel's source still has the hash recorded
+    with the capture, and is null otherwise."""
+    import bench
+    sha = bench.fused_source_sha256()
+    monkeypatch.setattr(bench, "FUSED_TRAFFIC", {"source_sha256": sha, "capture": "cap",
+                                                 "bytes": {(1, 8): 12345}})
+    assert bench.fused_traffic((1, 8)) == (12345, "cap")
+    assert bench.fused_traffic((1, 4))[0] is None
+    monkeypatch.setattr(bench, "FUSED_TRAFFIC", {"source_sha256": "0" * 64, "capture": "cap",
+                                                 "bytes": {(1, 8): 12345}})
+    assert bench.fused_traffic((1, 8))[0] is None
