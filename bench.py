@@ -57,7 +57,14 @@ SM_COUNT_NOMINAL = 152
 # dram__bytes_write.sum; summary and command under profiles/), together with the
 # SHA-256 of the kernel source it was taken on.  bench.py reports the figure only
 # while the source still has that hash; otherwise traffic is null.
-FUSED_TRAFFIC = {"source_sha256": None, "capture": None, "bytes": {}}
+FUSED_TRAFFIC = {
+    "source_sha256": "ea7d57e0c9a783b07862f4d8646e437c12e402d49dcf821858396c6821499749",
+    "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum of the third solve of "
+               "python -m paper_2212_02224_gb300.profile_solve --prec fp32 --shape W S --reps 3 "
+               "(profiles/fused_kernel_dense_traffic_B1000.md)",
+    "bytes": {(1, 1): 103680, (1, 2): 97280, (1, 4): 91648, (1, 8): 89856, (2, 1): 92416,
+              (2, 2): 85760, (4, 1): 86528},
+}
 FUSED_KERNEL_SOURCES = ("paper_2212_02224_gb300/csrc/fused_kernel.cuh",
                         "paper_2212_02224_gb300/csrc/k_fused.cu")
 
