@@ -379,6 +379,7 @@ update_only_kernel(const double* p_elite, const double* cost, int q, int d_p, do
 constexpr int kSmallMaxB = 2048;
 constexpr int kSmallMaxC = 1024;
 constexpr int kSmallThreads = 256;
+constexpr int kSmallPre = 128;           // elites whose p is staged in shared memory
 
 struct SmallSel {
   unsigned long long key[kSmallMaxB];    // order keys of r, sorted in place
@@ -387,7 +388,41 @@ struct SmallSel {
   int idx[kSmallMaxC];                   // EliteSet, sorted by (cost, index)
   double sw[kSmallMaxC];
   double acc[kMaxDp * kMaxDp + kMaxDp + 1];
+  double ce[kSmallMaxC];                 // costs c_u + r of the elites
+  double pe[kSmallPre * kMaxDp];         // p of the first kSmallPre elites
+  double bestv[2 + kMaxDp + 2 * kMaxCoef];   // best sample: r, c_u, p, xi
+  int wsum[32];
+  int total;
 };
+
+// Exclusive prefix sum over the block (blockDim.x <= 1024) of one count per
+// thread, in thread order; *total is the block's sum.
+__device__ void small_block_scan(int v, int* before, int* total, SmallSel& sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) sh.wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int w = lane < nw ? sh.wsum[lane] : 0;
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < nw) sh.wsum[lane] = wi - w;
+    if (lane == 31) sh.total = wi;
+  }
+  __syncthreads();
+  *before = sh.wsum[warp] + incl - v;
+  *total = sh.total;
+  __syncthreads();
+}
 
 __device__ __forceinline__ bool pair_gt(unsigned long long ka, int ia, unsigned long long kb,
                                         int ib) {
@@ -482,6 +517,34 @@ __device__ void small_constraint_set(const double* r, const double* cu, int B, i
     const int e = E * tid + u;
     k[u] = e < B ? ord_key(r[e]) : ~0ull;    // padding sorts last
     x[u] = e;
+  }
+  // Feasible samples score exactly r = 0, the smallest possible r (a sum of
+  // max(0, .) terms).  When at least n_c of them exist, the n_c lowest
+  // (key, index) pairs are the n_c zero-score samples of lowest index: a
+  // block-wide compaction in index order gives the same set as the sort.
+  const unsigned long long kzero = ord_key(0.0);
+  int nzero = 0;
+#pragma unroll
+  for (int u = 0; u < E; ++u) nzero += k[u] == kzero ? 1 : 0;
+  int before = 0, total = 0;
+  small_block_scan(nzero, &before, &total, sh);
+  if (total >= n_c) {
+#pragma unroll
+    for (int u = 0; u < E; ++u) {
+      if (k[u] == kzero) {
+        if (before < n_c) {
+          sh.ckey[before] = ord_key(cu[x[u]] + r[x[u]]);
+          sh.idx[before] = x[u];
+        }
+        ++before;
+      }
+    }
+    for (int e = n_c + tid; e < P2; e += blockDim.x) {
+      sh.ckey[e] = ~0ull;
+      sh.idx[e] = B + e;
+    }
+    __syncthreads();
+    return;
   }
   block_bitonic<E>(k, x, sh.key, sh.kidx);
 #pragma unroll
@@ -580,22 +643,44 @@ select_update_small_kernel(const Layout* layout, DevCem* cem, int l, Params prm,
   const int d_p = prm.d_p;
   const double* ps = p + size_t(lay.off) * d_p;
   auto id_of = [&](int e) { const int id = sh.idx[e]; return (id >= 0 && id < B) ? id : 0; };
-  auto p_e = [&](int e, int a) { return ps[size_t(id_of(e)) * d_p + a]; };
-  auto c_e = [&](int e) { return cs[id_of(e)] + rs[id_of(e)]; };
+  // one parallel gather of everything the update and the best pair read (the
+  // elites' costs, the first kSmallPre elites' p, the best sample's r, c_u, p
+  // and xi), so that their global-memory latencies overlap
+  const int best = id_of(0);
+  const int qp = min(q, kSmallPre);
+  const int nx = 2 * prm.n;
+  const int n_gather = q + qp * d_p + 2 + d_p + nx;
+  for (int t = threadIdx.x; t < n_gather; t += blockDim.x) {
+    if (t < q) {
+      sh.ce[t] = cs[id_of(t)] + rs[id_of(t)];
+    } else if (t < q + qp * d_p) {
+      const int tt = t - q;
+      sh.pe[tt] = ps[size_t(id_of(tt / d_p)) * d_p + tt % d_p];
+    } else {
+      const int b = t - q - qp * d_p;
+      sh.bestv[b] = b == 0 ? rs[best]
+                  : b == 1 ? cs[best]
+                  : b < 2 + d_p ? ps[size_t(best) * d_p + (b - 2)]
+                                : xi[size_t(lay.off + best) * nx + (b - 2 - d_p)];
+    }
+  }
+  __syncthreads();
+  auto p_e = [&](int e, int a) {
+    return e < kSmallPre ? sh.pe[e * d_p + a] : ps[size_t(id_of(e)) * d_p + a];
+  };
+  auto c_e = [&](int e) { return sh.ce[e]; };
   update_moments(p_e, c_e, c_e(0), q, d_p, prm.gamma, prm.eta, st.mu, st.sigma, kMaxDp, sh.sw,
                  sh.acc);
-  const int best = id_of(0);
   if (threadIdx.x == 0) {
     cholesky(st.sigma, prm.cov_eps, d_p, st.chol);
     st.best_index = best;
-    st.best_r = rs[best];
-    st.best_cu = cs[best];
-    st.best_cost = cs[best] + rs[best];
+    st.best_r = sh.bestv[0];
+    st.best_cu = sh.bestv[1];
+    st.best_cost = sh.bestv[1] + sh.bestv[0];
     if (l == prm.L) { st.fresh = 0; st.step += 1ull; }
   }
-  for (int a = threadIdx.x; a < d_p; a += blockDim.x) st.best_p[a] = ps[size_t(best) * d_p + a];
-  for (int a = threadIdx.x; a < 2 * prm.n; a += blockDim.x)
-    st.best_xi[a] = xi[size_t(lay.off + best) * 2 * prm.n + a];
+  for (int a = threadIdx.x; a < d_p; a += blockDim.x) st.best_p[a] = sh.bestv[2 + a];
+  for (int a = threadIdx.x; a < nx; a += blockDim.x) st.best_xi[a] = sh.bestv[2 + d_p + a];
   if (elite_out != nullptr)
     for (int e = threadIdx.x; e < q; e += blockDim.x) elite_out[size_t(s) * prm.q + e] = sh.idx[e];
 }
