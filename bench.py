@@ -61,7 +61,7 @@ FUSED_TRAFFIC = {
     "source_sha256": "ddde34ce011fb21ff9dc0c109b56c3691175b2d4cf2236b65636730a9b28c2f5",
     "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum of the third solve of "
                "python -m paper_2212_02224_gb300.profile_solve --prec fp32 --shape W S --reps 3 "
-               "(profiles/fused_kernel_dense_traffic_B1000.md)",
+               "(summary and command under profiles/)",
     "bytes": {(1, 1): 100864, (1, 2): 92928, (1, 4): 89088, (1, 8): 86784, (2, 1): 91392,
               (2, 2): 83968, (4, 1): 107008},
 }

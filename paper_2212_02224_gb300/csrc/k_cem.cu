@@ -528,28 +528,13 @@ __device__ void small_constraint_set(const double* r, const double* cu, int B, i
   for (int u = 0; u < E; ++u) nzero += k[u] == kzero ? 1 : 0;
   int before = 0, total = 0;
   small_block_scan(nzero, &before, &total, sh);
-  if (total >= n_c) {
-#pragma unroll
-    for (int u = 0; u < E; ++u) {
-      if (k[u] == kzero) {
-        if (before < n_c) {
-          sh.ckey[before] = ord_key(cu[x[u]] + r[x[u]]);
-          sh.idx[before] = x[u];
-        }
-        ++before;
-      }
-    }
-    for (int e = n_c + tid; e < P2; e += blockDim.x) {
-      sh.ckey[e] = ~0ull;
-      sh.idx[e] = B + e;
-    }
-    __syncthreads();
-    return;
-  }
-  block_bitonic<E>(k, x, sh.key, sh.kidx);
+  const bool zero_set = total >= n_c;      // block-uniform
+  if (!zero_set) block_bitonic<E>(k, x, sh.key, sh.kidx);
 #pragma unroll
   for (int u = 0; u < E; ++u) {
-    const int e = E * tid + u;
+    // position in the set: the rank among zero scores, or the sorted position
+    int e = E * tid + u;
+    if (zero_set) e = k[u] == kzero ? before++ : n_c;
     if (e < n_c) {
       sh.ckey[e] = ord_key(cu[x[u]] + r[x[u]]);
       sh.idx[e] = x[u];
