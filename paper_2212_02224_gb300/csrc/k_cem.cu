@@ -85,11 +85,13 @@ __global__ void sample_kernel(const DevScene* scenes, const Layout* layout, cons
   }
 }
 
-// Total order on doubles: -0 is +0, NaN sorts after everything.
+// Total order on doubles: -0 is +0, NaN sorts after everything.  Integer
+// operations only (float64 compares would take the float64 pipe).
 __device__ __forceinline__ unsigned long long ord_key(double v) {
-  if (v != v) return 0xfff8000000000000ull;   // canonical NaN, after +inf
-  if (v == 0.0) v = 0.0;
-  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(v));
+  unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(v));
+  const unsigned long long mag = u & 0x7fffffffffffffffull;
+  if (mag > 0x7ff0000000000000ull) return 0xfff8000000000000ull;   // canonical NaN, after +inf
+  if (mag == 0ull) u = 0ull;                                        // -0 is +0
   return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
 
@@ -257,7 +259,7 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
 template <class PE, class CE>
 __device__ void update_moments(PE p_e, CE c_e, double cmin, int q, int d_p, double gamma,
                                double eta, double* mu, double* sigma, int ld, double* sw,
-                               double* accum) {
+                               double* accum, double* sig_copy = nullptr) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int e = tid; e < q; e += blockDim.x) sw[e] = exp(-(c_e(e) - cmin) / gamma);
   __syncthreads();
@@ -270,34 +272,46 @@ __device__ void update_moments(PE p_e, CE c_e, double cmin, int q, int d_p, doub
   }
   __syncthreads();
   double* mu_new = accum + 1;
-  const double inv_s = 1.0 / accum[0];       // one float64 division for the whole update
-  if (tid < d_p) mu_new[tid] = (1.0 - eta) * mu[tid] + eta * mu_new[tid] * inv_s;
+  if (warp == 0) {
+    // one float64 division for the whole update (float64 runs one warp
+    // instruction at a time per SM sub-partition: the other warps skip it)
+    const double inv = 1.0 / accum[0];
+    if (lane == 0) accum[1 + kMaxDp] = inv;
+    if (tid < d_p) mu_new[tid] = (1.0 - eta) * mu[tid] + eta * mu_new[tid] * inv;
+  }
   __syncthreads();
+  const double inv_s = accum[1 + kMaxDp];
   for (int j = warp; j < d_p * d_p; j += nw) {
     const int a = j / d_p, b = j % d_p;
     const double ma = mu_new[a], mb = mu_new[b];
     double part = 0.0;
     for (int e = lane; e < q; e += 32) part += sw[e] * (p_e(e, a) - ma) * (p_e(e, b) - mb);
     part = warp_sum_f64(part);
-    if (lane == 0) sigma[a * ld + b] = (1.0 - eta) * sigma[a * ld + b] + eta * part * inv_s;
+    if (lane == 0) {
+      const double v = (1.0 - eta) * sigma[a * ld + b] + eta * part * inv_s;
+      sigma[a * ld + b] = v;
+      if (sig_copy != nullptr) sig_copy[a * kMaxDp + b] = v;
+    }
   }
   __syncthreads();
   if (tid < d_p) mu[tid] = mu_new[tid];
   __syncthreads();
 }
 
-// Lower Cholesky factor of sigma + eps I (d_p <= kMaxDp), single thread.
-__device__ void cholesky(const double* sigma, double eps, int d, double* L) {
+// Lower Cholesky factor of sigma + eps I (d_p <= kMaxDp), single thread.  One
+// reciprocal square root per column r = 1/sqrt(s): L_jj = s r, L_ij = v r
+// (float64 division and square root are long instruction sequences here).
+__device__ __forceinline__ void cholesky(const double* sigma, double eps, int d, double* L) {
   for (int i = 0; i < kMaxDp * kMaxDp; ++i) L[i] = 0.0;
   for (int jc = 0; jc < d; ++jc) {
     double s = sigma[jc * kMaxDp + jc] + eps;
     for (int k = 0; k < jc; ++k) s -= L[jc * kMaxDp + k] * L[jc * kMaxDp + k];
-    const double dj = sqrt(s);
-    L[jc * kMaxDp + jc] = dj;
+    const double rj = rsqrt(s);
+    L[jc * kMaxDp + jc] = s * rj;
     for (int i = jc + 1; i < d; ++i) {
       double v = sigma[i * kMaxDp + jc];
       for (int k = 0; k < jc; ++k) v -= L[i * kMaxDp + k] * L[jc * kMaxDp + k];
-      L[i * kMaxDp + jc] = v / dj;
+      L[i * kMaxDp + jc] = v * rj;
     }
   }
 }
@@ -385,12 +399,15 @@ struct SmallSel {
   unsigned long long key[kSmallMaxB];    // order keys of r, sorted in place
   int kidx[kSmallMaxB];                  // their sample indices
   unsigned long long ckey[kSmallMaxC];   // order keys of cu + r of the candidates
+  unsigned ck32[kSmallMaxC];             // their upper 32 bits
   int idx[kSmallMaxC];                   // EliteSet, sorted by (cost, index)
   double sw[kSmallMaxC];
   double acc[kMaxDp * kMaxDp + kMaxDp + 1];
   double ce[kSmallMaxC];                 // costs c_u + r of the elites
   double pe[kSmallPre * kMaxDp];         // p of the first kSmallPre elites
   double bestv[2 + kMaxDp + 2 * kMaxCoef];   // best sample: r, c_u, p, xi
+  double sig[kMaxDp * kMaxDp];           // the new covariance
+  double chol[kMaxDp * kMaxDp];          // its Cholesky factor
   int wsum[32];
   int total;
 };
@@ -511,17 +528,21 @@ __device__ void small_constraint_set(const double* r, const double* cu, int B, i
                                      SmallSel& sh) {
   unsigned long long k[E];
   int x[E];
+  double c[E];      // c_u, loaded with r so that both latencies overlap
   const int tid = threadIdx.x;
 #pragma unroll
   for (int u = 0; u < E; ++u) {
     const int e = E * tid + u;
     k[u] = e < B ? ord_key(r[e]) : ~0ull;    // padding sorts last
+    c[u] = e < B ? cu[e] : 0.0;
     x[u] = e;
   }
   // Feasible samples score exactly r = 0, the smallest possible r (a sum of
   // max(0, .) terms).  When at least n_c of them exist, the n_c lowest
   // (key, index) pairs are the n_c zero-score samples of lowest index: a
   // block-wide compaction in index order gives the same set as the sort.
+  // Their cost key is that of c_u alone: with r = +-0, c_u + r has the key
+  // of c_u (keys take -0 as +0 and every NaN as one).
   const unsigned long long kzero = ord_key(0.0);
   int nzero = 0;
 #pragma unroll
@@ -536,12 +557,15 @@ __device__ void small_constraint_set(const double* r, const double* cu, int B, i
     int e = E * tid + u;
     if (zero_set) e = k[u] == kzero ? before++ : n_c;
     if (e < n_c) {
-      sh.ckey[e] = ord_key(cu[x[u]] + r[x[u]]);
+      const unsigned long long kc = zero_set ? ord_key(c[u]) : ord_key(cu[x[u]] + r[x[u]]);
+      sh.ckey[e] = kc;
+      sh.ck32[e] = unsigned(kc >> 32);
       sh.idx[e] = x[u];
     }
   }
   for (int e = n_c + tid; e < P2; e += blockDim.x) {
     sh.ckey[e] = ~0ull;
+    sh.ck32[e] = ~0u;
     sh.idx[e] = B + e;
   }
   __syncthreads();
@@ -580,21 +604,29 @@ __device__ void small_elites(const double* r, const double* cu, int B, int n_c, 
   }
   if (n_c <= 256) {
     // few candidates: each one's rank is the number of (cost key, index)
-    // pairs below it (no barriers); ranks are distinct since indices are
+    // pairs below it (no barriers); ranks are distinct since indices are.
+    // The upper 32 bits of the keys order all pairs whose upper halves
+    // differ (four per 16-byte load); only candidates that share their upper
+    // half with another compare the full pairs.  Entries n_c..P2-1 hold the
+    // largest upper half and never count.
     const int tid = threadIdx.x;
     if (tid < n_c) {
       const unsigned long long kc = sh.ckey[tid];
+      const unsigned k32 = unsigned(kc >> 32);
       const int ic = sh.idx[tid];
-      int r0 = 0, r1 = 0, r2 = 0, r3 = 0;   // independent counts hide the load latency
-      int h = 0;
-      for (; h + 4 <= n_c; h += 4) {
-        r0 += pair_gt(kc, ic, sh.ckey[h], sh.idx[h]) ? 1 : 0;
-        r1 += pair_gt(kc, ic, sh.ckey[h + 1], sh.idx[h + 1]) ? 1 : 0;
-        r2 += pair_gt(kc, ic, sh.ckey[h + 2], sh.idx[h + 2]) ? 1 : 0;
-        r3 += pair_gt(kc, ic, sh.ckey[h + 3], sh.idx[h + 3]) ? 1 : 0;
+      const uint4* c4 = reinterpret_cast<const uint4*>(sh.ck32);
+      int lt0 = 0, lt1 = 0, eq = 0;
+      for (int h4 = 0; h4 < (n_c + 3) / 4; ++h4) {
+        const uint4 a = c4[h4];
+        lt0 += (a.x < k32 ? 1 : 0) + (a.y < k32 ? 1 : 0);
+        lt1 += (a.z < k32 ? 1 : 0) + (a.w < k32 ? 1 : 0);
+        eq += (a.x == k32 ? 1 : 0) + (a.y == k32 ? 1 : 0) + (a.z == k32 ? 1 : 0) +
+              (a.w == k32 ? 1 : 0);
       }
-      for (; h < n_c; ++h) r0 += pair_gt(kc, ic, sh.ckey[h], sh.idx[h]) ? 1 : 0;
-      const int rank = (r0 + r1) + (r2 + r3);
+      int rank = lt0 + lt1;
+      if (eq > 1)      // another candidate shares the upper half (itself counts once)
+        for (int h = 0; h < n_c; ++h)
+          if (sh.ck32[h] == k32) rank += pair_gt(kc, ic, sh.ckey[h], sh.idx[h]) ? 1 : 0;
       if (rank < q) sh.kidx[rank] = ic;
     }
     __syncthreads();
@@ -608,7 +640,9 @@ __device__ void small_elites(const double* r, const double* cu, int B, int n_c, 
   }
 }
 
-__global__ void __launch_bounds__(kSmallThreads)
+// one block per SM is all it needs: the explicit bound lets ptxas use the
+// registers it wants (its default for 256 threads spilled)
+__global__ void __launch_bounds__(kSmallThreads, 1)
 select_update_small_kernel(const Layout* layout, DevCem* cem, int l, Params prm, const double* p,
                            const double* xi, const double* r, const double* cu, int* elite_out) {
   extern __shared__ __align__(16) unsigned char shraw[];
@@ -655,9 +689,13 @@ select_update_small_kernel(const Layout* layout, DevCem* cem, int l, Params prm,
   };
   auto c_e = [&](int e) { return sh.ce[e]; };
   update_moments(p_e, c_e, c_e(0), q, d_p, prm.gamma, prm.eta, st.mu, st.sigma, kMaxDp, sh.sw,
-                 sh.acc);
+                 sh.acc, sh.sig);
+  // the factorisation reads the covariance from shared memory and its factor
+  // is written out by the whole block
+  if (threadIdx.x == 0) cholesky(sh.sig, prm.cov_eps, d_p, sh.chol);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kMaxDp * kMaxDp; i += blockDim.x) st.chol[i] = sh.chol[i];
   if (threadIdx.x == 0) {
-    cholesky(st.sigma, prm.cov_eps, d_p, st.chol);
     st.best_index = best;
     st.best_r = sh.bestv[0];
     st.best_cu = sh.bestv[1];
