@@ -105,7 +105,7 @@ struct SelShared {
   double sw[kMaxEliteC];
   unsigned long long prefix;
   int need, digit, count;
-  double acc[kMaxDp * kMaxDp + kMaxDp + 1];
+  double acc[kMaxDp * kMaxDp + kMaxDp + 2];
 };
 
 // Block-wide exclusive prefix sum of one flag per thread; returns the prefix and
@@ -250,51 +250,69 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
   return v;
 }
 
-// Eqs. (mean_update, cov_update, s_formula) over the q elites p_e(e), costs c_e(e).
-// Every sum runs on one warp: lane i adds the terms e = i, i + 32, ... in
-// increasing order, then the lanes combine in a fixed butterfly.  The result
-// does not depend on the block size, and the float64 chains stay a few terms
-// long (float64 runs at 1/64 of the float32 rate here).  accum holds
-// 1 + kMaxDp doubles: the weight total, then the new mean.
+// Eqs. (mean_update, cov_update, s_formula) over the q elites p_e(e), costs c_e(e),
+// with the weights s_e = exp(-(c_e - cmin) inv_gamma), inv_gamma = 1 / gamma.
+// One pass of sums about the first elite c = p_0 (a point of the elite cloud,
+// so the centred sums lose no digits to cancellation):
+//   S = sum s_e,  d = sum s_e (p_e - c) / S,  T = sum s_e (p_e - c)(p_e - c)^T / S,
+// then with pbar = c + d (the weighted elite mean), the new mean
+// mu' = (1 - eta) mu + eta pbar and g = pbar - mu' = (1 - eta)(pbar - mu),
+//   sum s_e (p_e - mu')(p_e - mu')^T / S = T - d d^T + g g^T,
+// which is Eq. cov_update's weighted covariance about mu' exactly (in exact
+// arithmetic).  Every sum runs on one warp: lane i adds the terms e = i,
+// i + 32, ... in increasing order, then the lanes combine in a fixed butterfly,
+// so the result does not depend on the block size.  float64 runs at 1/64 of
+// the float32 rate here, and every dependent float64 operation is long: the
+// mean and second-moment sums run in parallel, on different warps.  accum
+// holds 2 + kMaxDp + kMaxDp^2 doubles.  With sig_copy (shared memory, leading
+// dimension kMaxDp) the new covariance is also left there.
 template <class PE, class CE>
-__device__ void update_moments(PE p_e, CE c_e, double cmin, int q, int d_p, double gamma,
+__device__ void update_moments(PE p_e, CE c_e, double cmin, int q, int d_p, double inv_gamma,
                                double eta, double* mu, double* sigma, int ld, double* sw,
                                double* accum, double* sig_copy = nullptr) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  for (int e = tid; e < q; e += blockDim.x) sw[e] = exp(-(c_e(e) - cmin) / gamma);
+  // the previous moments this thread combines, read while the weights are computed
+  const bool combines = tid < d_p * d_p;
+  const int ca_ = combines ? tid / d_p : 0, cb_ = combines ? tid % d_p : 0;
+  const double mu_a = combines ? mu[ca_] : 0.0, mu_b = combines ? mu[cb_] : 0.0;
+  const double sig_ab = combines ? sigma[ca_ * ld + cb_] : 0.0;
+  const double mu_t = tid < d_p ? mu[tid] : 0.0;
+  for (int e = tid; e < q; e += blockDim.x) sw[e] = exp(-(c_e(e) - cmin) * inv_gamma);
   __syncthreads();
-  // the weight total and the weighted sums of each coordinate
-  for (int j = warp; j <= d_p; j += nw) {
+  const int nsum = 1 + d_p + d_p * d_p;   // S, then d_p first and d_p^2 second moments
+  for (int j = warp; j < nsum; j += nw) {
     double part = 0.0;
-    for (int e = lane; e < q; e += 32) part += j == 0 ? sw[e] : sw[e] * p_e(e, j - 1);
-    part = warp_sum_f64(part);
-    if (lane == 0) accum[j] = part;
-  }
-  __syncthreads();
-  double* mu_new = accum + 1;
-  if (warp == 0) {
-    // one float64 division for the whole update (float64 runs one warp
-    // instruction at a time per SM sub-partition: the other warps skip it)
-    const double inv = 1.0 / accum[0];
-    if (lane == 0) accum[1 + kMaxDp] = inv;
-    if (tid < d_p) mu_new[tid] = (1.0 - eta) * mu[tid] + eta * mu_new[tid] * inv;
-  }
-  __syncthreads();
-  const double inv_s = accum[1 + kMaxDp];
-  for (int j = warp; j < d_p * d_p; j += nw) {
-    const int a = j / d_p, b = j % d_p;
-    const double ma = mu_new[a], mb = mu_new[b];
-    double part = 0.0;
-    for (int e = lane; e < q; e += 32) part += sw[e] * (p_e(e, a) - ma) * (p_e(e, b) - mb);
+    if (j == 0) {
+      for (int e = lane; e < q; e += 32) part += sw[e];
+    } else if (j <= d_p) {
+      const int a = j - 1;
+      const double ca = p_e(0, a);
+      for (int e = lane; e < q; e += 32) part += sw[e] * (p_e(e, a) - ca);
+    } else {
+      const int a = (j - 1 - d_p) / d_p, b = (j - 1 - d_p) % d_p;
+      const double ca = p_e(0, a), cb = p_e(0, b);
+      for (int e = lane; e < q; e += 32) part += sw[e] * (p_e(e, a) - ca) * (p_e(e, b) - cb);
+    }
     part = warp_sum_f64(part);
     if (lane == 0) {
-      const double v = (1.0 - eta) * sigma[a * ld + b] + eta * part * inv_s;
-      sigma[a * ld + b] = v;
-      if (sig_copy != nullptr) sig_copy[a * kMaxDp + b] = v;
+      accum[j] = part;
+      if (j == 0) accum[nsum] = 1.0 / part;   // one float64 division for the update
     }
   }
   __syncthreads();
-  if (tid < d_p) mu[tid] = mu_new[tid];
+  const double inv_s = accum[nsum];
+  // every read of the previous mu and sigma happened before the first barrier
+  if (combines) {
+    const int a = ca_, b = cb_;
+    const double da = accum[1 + a] * inv_s, db = accum[1 + b] * inv_s;
+    const double pa = p_e(0, a) + da, pb = p_e(0, b) + db;             // weighted means
+    const double ga = (1.0 - eta) * (pa - mu_a), gb = (1.0 - eta) * (pb - mu_b);
+    const double cov = accum[1 + d_p + tid] * inv_s - da * db + ga * gb;
+    const double sig_new = (1.0 - eta) * sig_ab + eta * cov;
+    sigma[a * ld + b] = sig_new;
+    if (sig_copy != nullptr) sig_copy[a * kMaxDp + b] = sig_new;
+    if (tid < d_p) mu[tid] = (1.0 - eta) * mu_t + eta * (p_e(0, tid) + accum[1 + tid] * inv_s);
+  }
   __syncthreads();
 }
 
@@ -340,8 +358,8 @@ select_update_kernel(const Layout* layout, DevCem* cem, int l, Params prm, const
   auto id_of = [&](int e) { const int id = sh.idx[e]; return (id >= 0 && id < B) ? id : 0; };
   auto p_e = [&](int e, int a) { return ps[size_t(id_of(e)) * d_p + a]; };
   auto c_e = [&](int e) { return cs[id_of(e)] + rs[id_of(e)]; };
-  update_moments(p_e, c_e, c_e(0), q, d_p, prm.gamma, prm.eta, st.mu, st.sigma, kMaxDp, sh.sw,
-                 sh.acc);
+  update_moments(p_e, c_e, c_e(0), q, d_p, 1.0 / prm.gamma, prm.eta, st.mu, st.sigma, kMaxDp,
+                 sh.sw, sh.acc);
   const int best = id_of(0);
   if (threadIdx.x == 0) {
     cholesky(st.sigma, prm.cov_eps, d_p, st.chol);
@@ -381,7 +399,7 @@ update_only_kernel(const double* p_elite, const double* cost, int q, int d_p, do
   __syncthreads();
   auto p_e = [&](int e, int a) { return p_elite[size_t(e) * d_p + a]; };
   auto c_e = [&](int e) { return cost[e]; };
-  update_moments(p_e, c_e, cmin, q, d_p, gamma, eta, mu, sigma, d_p, sh.sw, sh.acc);
+  update_moments(p_e, c_e, cmin, q, d_p, 1.0 / gamma, eta, mu, sigma, d_p, sh.sw, sh.acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -402,11 +420,12 @@ struct SmallSel {
   unsigned ck32[kSmallMaxC];             // their upper 32 bits
   int idx[kSmallMaxC];                   // EliteSet, sorted by (cost, index)
   double sw[kSmallMaxC];
-  double acc[kMaxDp * kMaxDp + kMaxDp + 1];
+  double acc[kMaxDp * kMaxDp + kMaxDp + 2];
   double ce[kSmallMaxC];                 // costs c_u + r of the elites
   double pe[kSmallPre * kMaxDp];         // p of the first kSmallPre elites
   double bestv[2 + kMaxDp + 2 * kMaxCoef];   // best sample: r, c_u, p, xi
   double sig[kMaxDp * kMaxDp];           // the new covariance
+  double inv_gamma;                      // 1 / gamma, taken while the elites are ranked
   double chol[kMaxDp * kMaxDp];          // its Cholesky factor
   int wsum[32];
   int total;
@@ -683,12 +702,14 @@ select_update_small_kernel(const Layout* layout, DevCem* cem, int l, Params prm,
                                 : xi[size_t(lay.off + best) * nx + (b - 2 - d_p)];
     }
   }
+  // the last thread (idle in the gather when it is short) takes 1 / gamma
+  if (threadIdx.x == blockDim.x - 1) sh.inv_gamma = 1.0 / prm.gamma;
   __syncthreads();
   auto p_e = [&](int e, int a) {
     return e < kSmallPre ? sh.pe[e * d_p + a] : ps[size_t(id_of(e)) * d_p + a];
   };
   auto c_e = [&](int e) { return sh.ce[e]; };
-  update_moments(p_e, c_e, c_e(0), q, d_p, prm.gamma, prm.eta, st.mu, st.sigma, kMaxDp, sh.sw,
+  update_moments(p_e, c_e, c_e(0), q, d_p, sh.inv_gamma, prm.eta, st.mu, st.sigma, kMaxDp, sh.sw,
                  sh.acc, sh.sig);
   // the factorisation reads the covariance from shared memory and its factor
   // is written out by the whole block
