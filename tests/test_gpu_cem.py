@@ -42,6 +42,45 @@ def test_select_elites_bit_exact(B, n_c, q, ties):
     assert list(el) == list(E)
 
 
+@pytest.mark.parametrize("case", ["near_equal_zero_path", "near_equal_sort_path", "signed_zeros",
+                                  "nan_inf", "negative_costs"])
+def test_select_elites_key_edge_cases(case):
+    """Keys the selection must order exactly: costs equal in their upper 32
+    bits (the EliteSet rank count compares those first), -0 against +0 (the
+    same key), NaN after +inf, negative costs; with at least n_c zero scores
+    (compaction path) and with fewer (sort path)."""
+    B, n_c, q = 1000, 150, 50
+    s = sg.Stream(sum(map(ord, case)))
+    if case.startswith("near_equal"):
+        # 1000 + j 2^-40: the doubles differ only in their lowest mantissa bits
+        cu = 1000.0 + s.integers(0, 64, B).astype(float) * 2.0 ** -40
+        n_zero = 400 if case.endswith("zero_path") else 100
+        r = np.where(np.arange(B) < n_zero, 0.0, s.uniform(0.1, 2.0, B))
+        r = r[np.argsort(s.uniform(0.0, 1.0, B))]
+    elif case == "signed_zeros":
+        r = np.where(s.uniform(0.0, 1.0, B) < 0.5, 0.0, -0.0)
+        r[s.integers(0, B - 1, 200)] = 0.25
+        cu = s.integers(0, 5, B).astype(float)
+        cu[::7] = -0.0
+    elif case == "nan_inf":
+        r = s.integers(0, 3, B).astype(float) * 0.5
+        r[s.integers(0, B - 1, 30)] = np.nan
+        r[s.integers(0, B - 1, 30)] = np.inf
+        cu = s.uniform(0.0, 10.0, B)
+        cu[s.integers(0, B - 1, 30)] = np.nan
+        cu[s.integers(0, B - 1, 30)] = np.inf
+    else:
+        r = s.integers(0, 3, B).astype(float)
+        cu = s.uniform(-50.0, 50.0, B)
+    prm = sg.Params()
+    pl = planner(prm, "fp32", max_obs=1, max_samples=16)
+    el = pl.select_elites(to_dev(r), to_dev(cu), n_c, q).cpu().numpy()
+    pl.close()
+    C = upper.select_lowest(r, n_c)
+    E = upper.select_lowest(cu + r, q, among=C)
+    assert list(el) == list(E)
+
+
 def test_update_distribution():
     prm = sg.Params(n_seg=2, eta=0.7, gamma=0.9)
     s = sg.Stream(5)
@@ -59,6 +98,32 @@ def test_update_distribution():
     pl.close()
     np.testing.assert_allclose(mu_t.cpu().numpy(), mu_o, rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(sg_t.cpu().numpy(), sg_o, rtol=1e-11, atol=1e-11)
+
+
+@pytest.mark.parametrize("n_seg,q,offset,mu_shift", [(1, 1, 0.0, 3.0), (4, 50, 1.0e4, 250.0),
+                                                   (4, 500, -30.0, 0.0), (2, 33, 5.0e3, -1.0e3)])
+def test_update_distribution_shapes(n_seg, q, offset, mu_shift):
+    """The update at d_p = 2 .. 8, one elite, many elites, an elite cloud far
+    from the origin and a previous mean far from the cloud, against the
+    oracle's two-pass Eqs. mean_update and cov_update."""
+    prm = sg.Params(n_seg=n_seg, eta=0.6, gamma=0.9)
+    d = prm.d_p
+    s = sg.Stream(q * 7 + d)
+    centre = offset + np.arange(d, dtype=float)
+    pe = s.normal(0.0, 2.0, q * d).reshape(q, d) + centre
+    cost = s.uniform(300.0, 330.0, q)
+    mu = centre + mu_shift
+    A = s.normal(0.0, 1.0, d * d).reshape(d, d)
+    sigma = A @ A.T + np.eye(d)
+    mu_o, sg_o = upper.update_distribution(mu, sigma, pe, cost, prm)
+    pl = planner(prm, "fp32", max_obs=1, max_samples=16)
+    mu_t, sg_t = to_dev(mu), to_dev(sigma)
+    pl.update_distribution(to_dev(pe), to_dev(cost), mu_t, sg_t)
+    torch.cuda.synchronize()
+    pl.close()
+    np.testing.assert_allclose(mu_t.cpu().numpy(), mu_o, rtol=1e-12, atol=1e-12)
+    scale = np.abs(sg_o).max()
+    np.testing.assert_allclose(sg_t.cpu().numpy(), sg_o, rtol=1e-11, atol=1e-12 * scale)
 
 
 @pytest.mark.parametrize("n_seg", [1, 2, 4])
