@@ -26,6 +26,9 @@ scale_point : the scale sweep's largest point (6 lanes, 30 obstacles, m = 200,
               fraction of the FP32 pipe, with its own clock record.
 batched     : the 256-scene workload (N ~ U{4..20}, B ~ U{256..2048}): ms per
               graph-captured step, value, solve fraction, clocks.
+serving     : the served MPC loop (Poisson arrivals over 64 episodes) at 600 and
+              1000 requests/s, 3 s of arrivals each: latency from arrival to
+              completion, throughput, drops.
 precision   : one B = 1000 solve per arithmetic mode against the plain FP64 GPU
               path, and the same with goal entries in p.
 
@@ -497,6 +500,16 @@ def gpu_arm(args):
                                            stream, sms, local)
         extra["batched"] = batched_point(max(3, min(args.steps, 5)), args.warmup, flush, stream,
                                          sms, local)
+        # the served MPC loop below and at its saturation rate, 3 s of arrivals each
+        extra["serving"] = []
+        for rate in (600.0, 1000.0):
+            sv = serve(rate, 3.0)
+            extra["serving"].append({
+                "rate_req_s": rate, "achieved_req_s": sv["achieved_req_s"], "value": sv["value"],
+                "unit": UNIT, "p50_ms": sv["latency_ms"]["p50"], "p99_ms": sv["latency_ms"]["p99"],
+                "server_p50_ms": sv["server_latency_ms"]["p50"],
+                "server_p99_ms": sv["server_latency_ms"]["p99"], "completed": sv["completed"],
+                "dropped": sv["dropped"], "config": sv["config"]["workload"]})
 
     # ---- precision modes: one lower-level solve of the same B = 1000 samples per
     # mode, timed alone, and its error against the plain FP64 GPU path
@@ -789,6 +802,11 @@ def scale_arm(args):
 
 
 def serving_arm(args):
+    print(json.dumps(serve(args.rate, args.serve_seconds, args.serve_episodes, args.serve_b,
+                           args.executors)))
+
+
+def serve(rate, seconds, n_ep=64, serve_b=(512, 2048), executors=16):
     """Served MPC loop: Poisson arrivals of cycle requests at `rate` per second
     over rolling 50-cycle episodes (N 4..24, B 512..2048, horizon in
     {80, 100, 125, 150}); each episode advances its scene by plan_advance after
@@ -803,15 +821,14 @@ def serving_arm(args):
     from paper_2212_02224_gb300 import scenegen as sg
     from paper_2212_02224_gb300.planner import Server, advance
     prm, _, _ = sg.workload(1)
-    srv = Server(prm, max_obs=24, max_samples=16384, max_scenes=32, max_executors=args.executors,
+    srv = Server(prm, max_obs=24, max_samples=16384, max_scenes=32, max_executors=executors,
                  device_budget=16 << 30, max_episodes=4096)
     rng = np.random.default_rng(11)
     s = sg.Stream(4242)
-    n_ep = args.serve_episodes
     eps = []
     for e in range(n_ep):
         sc = sg.make_scene(50000 + e, n_lanes=4, n_obs=int(s.integers(4, 24, 1)[0]))
-        eps.append(dict(id=e, scene=sc, B=int(s.integers(args.serve_b[0], args.serve_b[1], 1)[0]),
+        eps.append(dict(id=e, scene=sc, B=int(s.integers(serve_b[0], serve_b[1], 1)[0]),
                         m=int(rng.choice([80, 100, 125, 150])), cycle=0, busy=False, ticket=None,
                         t_arr=0.0))
     # warm the executors (one per horizon) before timing
@@ -824,7 +841,7 @@ def serving_arm(args):
     max_waiting = 0
     t0 = time.perf_counter()
     next_arrival = t0
-    duration = args.serve_seconds
+    duration = seconds
     offered = submitted = completed = 0
     next_ep_id = n_ep
     while True:
@@ -834,7 +851,7 @@ def serving_arm(args):
         while now >= next_arrival and next_arrival - t0 <= duration:
             waiting.append(next_arrival)     # every arrival that is due
             offered += 1
-            next_arrival += rng.exponential(1.0 / args.rate)
+            next_arrival += rng.exponential(1.0 / rate)
         max_waiting = max(max_waiting, len(waiting))
         if waiting:
             idle = [e for e in eps if not e["busy"]]
@@ -874,8 +891,8 @@ def serving_arm(args):
     def pct(v, q):
         return float(np.percentile(v, q))
 
-    print(json.dumps({
-        "metric": METRIC, "workload": "serving", "rate_req_s": args.rate,
+    return {
+        "metric": METRIC, "workload": "serving", "rate_req_s": rate,
         "achieved_req_s": completed / wall, "value": done_units / wall, "unit": UNIT,
         "latency_ms": {"p50": pct(lat_e2e, 50), "p99": pct(lat_e2e, 99), "mean": float(np.mean(lat_e2e)),
                        "basis": "arrival to completion: the wait for an idle episode and the "
@@ -888,7 +905,7 @@ def serving_arm(args):
         "dtype": "f32",
         "config": {"workload": "Poisson arrivals over %d rolling 50-cycle episodes, N 4..24, "
                                "B %d..%d, m in {80,100,125,150}, K=100, L=5, elites 150/50"
-                               % (n_ep, args.serve_b[0], args.serve_b[1])}}))
+                               % (n_ep, serve_b[0], serve_b[1])}}
 
 
 def main():
