@@ -56,8 +56,10 @@ class PlanRoadKnot(ctypes.Structure):
 class PlanScene(ctypes.Structure):
     _fields_ = [("ego", PlanEgo), ("n_lanes", ctypes.c_int), ("lane_width", ctypes.c_double),
                 ("kappa_road", ctypes.c_double), ("n_obs", ctypes.c_int),
-                ("obs", ctypes.POINTER(PlanObstacle)), ("n_road", ctypes.c_int),
-                ("road", ctypes.POINTER(PlanRoadKnot)), ("road_origin", ctypes.c_double)]
+                # const plan_obstacle* / const plan_road_knot*: set from the
+                # address of a float64 buffer with the same row layout
+                ("obs", ctypes.c_void_p), ("n_road", ctypes.c_int),
+                ("road", ctypes.c_void_p), ("road_origin", ctypes.c_double)]
 
 
 class PlanCemState(ctypes.Structure):
@@ -204,14 +206,14 @@ def make_scenes(scenes):
         arr[i].n_obs = ob.shape[0]
         if ob.shape[0]:
             keep.append(ob)
-            arr[i].obs = ob.ctypes.data_as(ctypes.POINTER(PlanObstacle))
+            arr[i].obs = ob.ctypes.data
         else:
             arr[i].obs = None
         road = np.ascontiguousarray(np.asarray(getattr(sc, "road", ()), dtype=np.float64).reshape(-1, 4))
         arr[i].n_road = road.shape[0]
         if road.shape[0]:
             keep.append(road)
-            arr[i].road = road.ctypes.data_as(ctypes.POINTER(PlanRoadKnot))
+            arr[i].road = road.ctypes.data
         else:
             arr[i].road = None
         arr[i].road_origin = float(getattr(sc, "road_origin", 0.0))

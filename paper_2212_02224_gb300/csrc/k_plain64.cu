@@ -73,6 +73,14 @@ __global__ void forward_kernel(int total, Consts c, Params prm, Plain64Work w) {
 // Eq. split_alpha_o with the clips of Eqs. clip_d_o, clip_d_v, clip_d_a and the
 // slack of Eq. update_slack, stored as the residual rows h - F xi and
 // e - s - G xi (per t: obstacle sum x, y; velocity x, y; acceleration x, y; lane).
+// Closed forms without trigonometry: with (dx, dy) = p - o and the scaled
+// distance d of an obstacle, cos(alpha) = dx / (a d) and sin(alpha) = dy / (b d),
+// so the clipped point differs from p by (dx, dy)(1/d - 1) when d < 1 (at d = 0,
+// atan2(0, 0) = 0 gives (a, 0)) and by zero otherwise.  The test d < 1 is
+// dx^2 b^2 + dy^2 a^2 < a^2 b^2, free of divisions; only points inside an
+// ellipse take the divisions and the reciprocal square root.  Velocity and
+// acceleration directions come from one reciprocal square root of |v|^2, |a|^2.
+// float64 division and square root are long instruction sequences on this part.
 __global__ void project_kernel(int total, const DevScene* scenes, const int* sample_scene,
                                const double* obs, Params prm, Plain64Work w, int first) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -89,20 +97,31 @@ __global__ void project_kernel(int total, const DevScene* scenes, const int* sam
   for (int i = 0; i < sc.n_obs; ++i) {
     const double* o = obs + size_t(sc.obs_off + i) * 6;
     const double dx = x - (o[0] + o[2] * tt), dy = y - (o[1] + o[3] * tt);
-    const double sx = dx / o[4], sy = dy / o[5];
-    const double d = sqrt(sx * sx + sy * sy);
-    double ca = 1.0, sa = 0.0;
-    if (d > 0.0) { ca = sx / d; sa = sy / d; }
-    const double dc = fmax(1.0, d);
-    ex += (o[0] + o[2] * tt) + o[4] * dc * ca - x;
-    ey += (o[1] + o[3] * tt) + o[5] * dc * sa - y;
+    const double a2 = o[4] * o[4], b2 = o[5] * o[5];
+    if (fma(dx * dx, b2, dy * dy * a2) < a2 * b2) {      // d < 1
+      const double sx = dx / o[4], sy = dy / o[5];
+      const double d2 = fma(sx, sx, sy * sy);
+      if (d2 > 0.0) {
+        const double g = rsqrt(d2) - 1.0;
+        ex += dx * g;
+        ey += dy * g;
+      } else {
+        ex += o[4];
+      }
+    }
   }
-  const double sp = sqrt(vx * vx + vy * vy);
-  double cv = 1.0, sv = 0.0;
-  if (sp > 0.0) { cv = vx / sp; sv = vy / sp; }
-  const double am = sqrt(ax * ax + ay * ay);
-  double ca = 1.0, sa = 0.0;
-  if (am > 0.0) { ca = ax / am; sa = ay / am; }
+  const double v2 = vx * vx + vy * vy;
+  double sp = 0.0, cv = 1.0, sv = 0.0;
+  if (v2 > 0.0) {
+    const double rv = rsqrt(v2);
+    sp = v2 * rv; cv = vx * rv; sv = vy * rv;
+  }
+  const double a2n = ax * ax + ay * ay;
+  double am = 0.0, ca = 1.0, sa = 0.0;
+  if (a2n > 0.0) {
+    const double ra = rsqrt(a2n);
+    am = a2n * ra; ca = ax * ra; sa = ay * ra;
+  }
   const double S = fabs(sa * cv - ca * sv);
   double* da = w.da + size_t(j) * m;
   const double dap = first ? fmin(am, prm.a_max) : da[t];
@@ -134,24 +153,41 @@ __global__ void project_kernel(int total, const DevScene* scenes, const int* sam
   e[6 * m + t] = (yub - s1 - y) - (-ylb - s2 + y);
 }
 
-// w = F^T (h - F xi) + G^T (e - s - G xi): thread = (sample, slot).
-__global__ void transpose_kernel(Consts c, Params prm, Plain64Work w) {
-  const int j = blockIdx.x, lane = threadIdx.x;
+// w = F^T (h - F xi) + G^T (e - s - G xi): one 128-thread block per sample;
+// warp q sums the timesteps t = q (mod 4) for every coefficient slot (lane),
+// and the four partial sums are added in a fixed order.
+constexpr int kTrWarps = 4;
+__global__ void __launch_bounds__(32 * kTrWarps) transpose_kernel(Consts c, Params prm,
+                                                                  Plain64Work w) {
+  const int j = blockIdx.x, lane = threadIdx.x & 31, q = threadIdx.x >> 5;
   const int m = prm.m, n = prm.n;
   const int axis = lane >> 4, k = lane & 15;
-  if (k >= n) return;
+  __shared__ double part[kTrWarps][32];
   const double* e = w.eps + size_t(j) * 7 * m;
   const double* W0 = c.basis64;
   const double* W1 = c.basis64 + m * n;
   const double* W2 = c.basis64 + 2 * m * n;
-  double acc = 0.0;
-  for (int t = 0; t < m; ++t) {
-    double e0 = e[axis * m + t];
-    if (axis == 1) e0 += e[6 * m + t];
-    acc += W0[t * n + k] * e0 + W1[t * n + k] * e[(2 + axis) * m + t] +
-           W2[t * n + k] * e[(4 + axis) * m + t];
+  // two independent chains per warp (t = q + 8 i and t = q + 4 + 8 i)
+  double acc[2] = {0.0, 0.0};
+  if (k < n) {
+    for (int t0 = q; t0 < m; t0 += 2 * kTrWarps) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int t = t0 + u * kTrWarps;
+        if (t < m) {
+          double e0 = e[axis * m + t];
+          if (axis == 1) e0 += e[6 * m + t];
+          acc[u] = fma(W0[t * n + k], e0, acc[u]);
+          acc[u] = fma(W1[t * n + k], e[(2 + axis) * m + t], acc[u]);
+          acc[u] = fma(W2[t * n + k], e[(4 + axis) * m + t], acc[u]);
+        }
+      }
+    }
   }
-  w.w[size_t(j) * 32 + lane] = acc;
+  part[q][lane] = acc[0] + acc[1];
+  __syncthreads();
+  if (q == 0 && k < n)
+    w.w[size_t(j) * 32 + lane] = (part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane]);
 }
 
 // lambda^it = lambda^{it-1} + rho/2 w (it > 0) and the xi-step.
@@ -240,7 +276,7 @@ cudaError_t launch_plain64(const DevScene* scenes, const Layout* layout, const i
   for (int it = 0; it < prm.K; ++it) {
     forward_kernel<<<grid, blk, 0, s>>>(total_B, c, prm, w);
     project_kernel<<<grid, blk, 0, s>>>(total_B, scenes, sample_scene, obs, prm, w, it == 0);
-    transpose_kernel<<<total_B, 32, 0, s>>>(c, prm, w);
+    transpose_kernel<<<total_B, 32 * kTrWarps, 0, s>>>(c, prm, w);
     update_kernel<<<total_B, 32, 0, s>>>(scenes, sample_scene, c, prm, w, it);
   }
   forward_kernel<<<grid, blk, 0, s>>>(total_B, c, prm, w);
