@@ -72,10 +72,13 @@ __global__ void sample_kernel(const DevScene* scenes, const Layout* layout, cons
   } else {
     double z[kMaxDp];
     for (int q = 0; 2 * q < d_p; ++q) {
+      // Box-Muller: r (cos, sin)(2 pi u2); sincospi takes the angle as a
+      // multiple of pi (2 u2 is exact), one argument reduction for both
       const double r = sqrt(-2.0 * log(unit_open(w[2 * q])));
-      const double th = 2.0 * CUDART_PI * unit_open(w[2 * q + 1]);
-      z[2 * q] = r * cos(th);
-      z[2 * q + 1] = r * sin(th);
+      double sn, cs;
+      sincospi(2.0 * unit_open(w[2 * q + 1]), &sn, &cs);
+      z[2 * q] = r * cs;
+      z[2 * q + 1] = r * sn;
     }
     for (int a = 0; a < d_p; ++a) {
       double v = 0.0;
