@@ -429,6 +429,23 @@ int plan_probe_alu(double* out, void* stream);
  * of range), ECUDA. */
 int plan_probe_wait_timeout(int wait_us, void* stream);
 
+/* Issue cost of the two contractions of one Alg. 2 iteration on the tensor
+ * cores at a wide N: a CTA of 64 samples of the m = 200, n = 16 workload
+ * (N = 128 columns = 64 samples x 2 axes), TF32 MMAs with `passes` 1 (TF32)
+ * or 3 (split TF32, the TF32X3 mode), operands staged in shared memory and
+ * accumulators in tensor memory; one CTA per SM, `iters` iterations
+ * (1..10000).  Only the MMAs are timed (zero operands, results not read).
+ * out[0]: SM cycles per iteration of the forward product (3 derivatives x 2
+ * row tiles of 128 timesteps x K = 16, M = N = 128); out[1]: the transposed
+ * product over K = 768 as M = 128 columns x N = 16 coefficients; out[2]: the
+ * same as M = 64 (coefficients, padded) x N = 128 columns; out[3], out[4]:
+ * out[1], out[2] with the K steps dealt round-robin to four accumulators;
+ * medians over the CTAs; out[5]: the number of CTAs (out holds 6 doubles).  The paper has no counterpart: this is the
+ * evidence for where B x (basis) is dense enough for the tensor cores.  Every
+ * wait is bounded.  Synchronous on `stream`; allocates small buffers.
+ * Errors: EINVAL (NULL out, passes, iters), ETIMEOUT (a wait gave up), ECUDA. */
+int plan_probe_tc_wide(int passes, int iters, double* out, void* stream);
+
 /* ------------------------------------------------ allocation-free lower level */
 
 /* The float64 lower-level solve of plan_solve (same kernels, same results) for

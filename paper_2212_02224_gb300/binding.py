@@ -92,7 +92,8 @@ EXPORTS = ("plan_init", "plan_destroy", "plan_status_str", "plan_last_error", "p
            "plan_update_distribution", "plan_sample", "plan_set_tuning", "plan_autotune",
            "plan_solve_fp64_noalloc", "plan_advance", "plan_server_create", "plan_server_destroy",
            "plan_submit", "plan_poll", "plan_poll_any", "plan_end_episode", "plan_server_info",
-           "plan_qp_forward", "plan_qp_backward", "plan_probe_alu", "plan_probe_wait_timeout")
+           "plan_qp_forward", "plan_qp_backward", "plan_probe_alu", "plan_probe_wait_timeout",
+           "plan_probe_tc_wide")
 
 _lib = None
 
@@ -146,6 +147,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "plan_qp_backward": (I, [V, V, I, V, V, V]),
         "plan_probe_alu": (I, [P(D), V]),
         "plan_probe_wait_timeout": (I, [I, V]),
+        "plan_probe_tc_wide": (I, [I, I, P(D), V]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -333,6 +335,17 @@ def plan_probe_alu(stream: int = 0) -> dict:
     check(load().plan_probe_alu(out, stream), None)
     return dict(fp32_tflops=out[0], fp32x2_tflops=out[1], fp64_tflops=out[2],
                 rsqrt_tops=out[3], sms=int(out[4]))
+
+
+def plan_probe_tc_wide(passes: int = 3, iters: int = 200, stream: int = 0) -> dict:
+    """SM cycles per Alg. 2 iteration of the tensor-core contractions at
+    N = 128 columns (64 samples of the n = 16, m = 200 workload), see
+    include/plan.h."""
+    out = (ctypes.c_double * 6)()
+    check(load().plan_probe_tc_wide(int(passes), int(iters), out, stream), None)
+    return dict(forward_cycles=out[0], transposed_n16_cycles=out[1],
+                transposed_n128_cycles=out[2], transposed_n16_4acc_cycles=out[3],
+                transposed_n128_4acc_cycles=out[4], ctas=int(out[5]))
 
 
 def plan_probe_wait_timeout(wait_us: int, stream: int = 0) -> int:

@@ -247,6 +247,10 @@ cudaError_t launch_tc(int prec, const DevScene* scenes, const Layout* layout, co
 // One bounded mbarrier wait that receives no arrival (k_tc.cu): *timed_out = 1
 // when it gave up after `limit` SM cycles.  Synchronous on s.
 cudaError_t wait_probe(long long limit, cudaStream_t s, int* timed_out);
+// SM cycles per iteration of the wide-N tensor-core contractions, per CTA
+// (5 doubles each); see plan_probe_tc_wide.
+cudaError_t tc_wide_probe(int passes, int iters, int ctas, double* cycles, cudaStream_t s,
+                          int* timed_out);
 
 // Arithmetic throughput probe (k_peaks.cu): out[0..4] as plan_probe_alu.
 int probe_alu(double* out, cudaStream_t s);

@@ -192,6 +192,148 @@ __device__ __forceinline__ void op_put(unsigned char* buf, uint32_t copy, uint32
 
 __device__ __forceinline__ float fast_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
 
+// Issue cost of the contractions of one Alg. 2 iteration at a wide N, for a
+// CTA that would hold 64 samples (N = 128 columns = 64 samples x 2 axes) of
+// the m = 200, n = 16 workload: TF32 MMAs (kind::tf32, `passes` 1 or 3 for
+// the split mode), operands in shared memory, accumulators in tensor memory.
+//   forward     3 derivatives x 2 row tiles (256 timesteps) x 2 K steps (n =
+//               16), M = 128, N = 128: D[t][c] in columns 0..383, one commit
+//               and wait per row tile;
+//   transposed  K = 3 x 256 = 768 (96 K steps) either as M = 128 (columns) x
+//               N = 16 (coefficients), or as M = 64 (16 coefficients padded) x
+//               N = 128 (columns); each with one accumulator, and again with
+//               the K steps dealt round-robin to four accumulators (partial
+//               sums a kernel would add afterwards), so that consecutive MMAs
+//               do not depend on one another.
+// Only the MMAs are timed: the operand values are zeros and the results are
+// not read; the K-step operands cycle through 8 staged chunks.  Thread 0
+// issues and waits (bounded); out[kProbeParts * cta + q] = SM cycles per
+// iteration of part q.  The paper has no counterpart: this measures whether B x (basis) is
+// dense enough for the tensor cores on this part.
+constexpr int kProbeThreads = 128;
+constexpr int kProbeParts = 5;
+constexpr uint32_t kProbeCols = 512;
+
+__global__ void __launch_bounds__(kProbeThreads, 1)
+tc_wide_probe_kernel(int passes, int iters, double* out, int* err) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // canonical no-swizzle K-major operands: [8-row group][16-byte K chunk][8 rows][16 B]
+  unsigned char* aF = dsm;                // 128 rows x K 16:  8 KB (SBO 512)
+  unsigned char* bF = aF + 8192;          // 128 rows x K 16:  8 KB
+  unsigned char* aT1 = bF + 8192;         // 128 rows x K 64: 32 KB (SBO 2048)
+  unsigned char* bT1 = aT1 + 32768;       //  16 rows x K 64:  4 KB
+  unsigned char* aT2 = bT1 + 4096;        //  64 rows x K 64: 16 KB
+  unsigned char* bT2 = aT2 + 16384;       // 128 rows x K 64: 32 KB
+  const uint32_t bytes = 8192u + 8192u + 32768u + 4096u + 16384u + 32768u;
+  for (uint32_t i = tid; i < bytes / 16; i += kProbeThreads)
+    reinterpret_cast<uint4*>(dsm)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_addr(&tslot)), "r"(kProbeCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tslot;
+  if (tid == 0) {
+    using T = Tc<PLAN_PREC_TF32>;
+    const uint32_t bar = smem_addr(&mbar);
+    const uint32_t idF = T::idesc(128, 128), id1 = T::idesc(128, 16), id2 = T::idesc(64, 128);
+    const uint32_t sF = smem_addr(aF), sFB = smem_addr(bF);
+    const uint32_t s1 = smem_addr(aT1), s1B = smem_addr(bT1);
+    const uint32_t s2 = smem_addr(aT2), s2B = smem_addr(bT2);
+    uint32_t phase = 0;
+    long long c_f = 0, c_1 = 0, c_2 = 0, c_3 = 0, c_4 = 0;
+    bool ok = true;
+    for (int it = 0; it < iters && ok; ++it) {
+      const long long t0 = clock64();
+      for (int tile = 0; tile < 2 && ok; ++tile) {
+        fence_after();
+        for (int d = 0; d < 3; ++d)
+          for (int ks = 0; ks < 2; ++ks)
+            for (int ps = 0; ps < passes; ++ps)
+              mma<PLAN_PREC_TF32>(tmem + 128u * d, sdesc(sF + ks * 256u, 128u, 512u),
+                                  sdesc(sFB + ks * 256u, 128u, 512u), idF, (ks | ps) != 0);
+        mma_commit(bar);
+        ok = mbar_wait(bar, phase);
+        phase ^= 1u;
+      }
+      const long long t1 = clock64();
+      if (ok) {
+        fence_after();
+        for (int ks = 0; ks < 96; ++ks)
+          for (int ps = 0; ps < passes; ++ps)
+            mma<PLAN_PREC_TF32>(tmem + 384u, sdesc(s1 + (ks & 7) * 256u, 128u, 2048u),
+                                sdesc(s1B + (ks & 7) * 256u, 128u, 2048u), id1, (ks | ps) != 0);
+        mma_commit(bar);
+        ok = mbar_wait(bar, phase);
+        phase ^= 1u;
+      }
+      const long long t2 = clock64();
+      if (ok) {
+        fence_after();
+        for (int ks = 0; ks < 96; ++ks)
+          for (int ps = 0; ps < passes; ++ps)
+            mma<PLAN_PREC_TF32>(tmem + 384u, sdesc(s2 + (ks & 7) * 256u, 128u, 2048u),
+                                sdesc(s2B + (ks & 7) * 256u, 128u, 2048u), id2, (ks | ps) != 0);
+        mma_commit(bar);
+        ok = mbar_wait(bar, phase);
+        phase ^= 1u;
+      }
+      const long long t3 = clock64();
+      if (ok) {    // four accumulators of N = 16 (columns 384 .. 447)
+        fence_after();
+        for (int ks = 0; ks < 96; ++ks)
+          for (int ps = 0; ps < passes; ++ps)
+            mma<PLAN_PREC_TF32>(tmem + 384u + 16u * (ks & 3), sdesc(s1 + (ks & 7) * 256u, 128u, 2048u),
+                                sdesc(s1B + (ks & 7) * 256u, 128u, 2048u), id1, (ks >= 4) | (ps != 0));
+        mma_commit(bar);
+        ok = mbar_wait(bar, phase);
+        phase ^= 1u;
+      }
+      const long long t4 = clock64();
+      if (ok) {    // four accumulators of N = 128 (all 512 columns)
+        fence_after();
+        for (int ks = 0; ks < 96; ++ks)
+          for (int ps = 0; ps < passes; ++ps)
+            mma<PLAN_PREC_TF32>(tmem + 128u * (ks & 3), sdesc(s2 + (ks & 7) * 256u, 128u, 2048u),
+                                sdesc(s2B + (ks & 7) * 256u, 128u, 2048u), id2, (ks >= 4) | (ps != 0));
+        mma_commit(bar);
+        ok = mbar_wait(bar, phase);
+        phase ^= 1u;
+      }
+      const long long t5 = clock64();
+      c_f += t1 - t0;
+      c_1 += t2 - t1;
+      c_2 += t3 - t2;
+      c_3 += t4 - t3;
+      c_4 += t5 - t4;
+    }
+    if (!ok) atomicExch(err, 1);
+    double* o = out + kProbeParts * blockIdx.x;
+    o[0] = double(c_f) / iters;
+    o[1] = double(c_1) / iters;
+    o[2] = double(c_2) / iters;
+    o[3] = double(c_3) / iters;
+    o[4] = double(c_4) / iters;
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kProbeCols));
+  }
+}
+
 template <int NC, int MODE>
 __global__ void __launch_bounds__(kTcThreads, 1)
 tc_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ layout,
@@ -700,6 +842,31 @@ cudaError_t wait_probe(long long limit, cudaStream_t s, int* timed_out) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(d);
   *timed_out = h;
+  return e;
+}
+
+cudaError_t tc_wide_probe(int passes, int iters, int ctas, double* cycles, cudaStream_t s,
+                          int* timed_out) {
+  *timed_out = 0;
+  double* d = nullptr;
+  int* flag = nullptr;
+  // 120 KB of dynamic shared memory keeps one probe CTA per SM
+  constexpr size_t kProbeSmem = 120 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(tc_wide_probe_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(kProbeSmem));
+  if (e == cudaSuccess) e = cudaMalloc(&d, sizeof(double) * kProbeParts * ctas);
+  if (e == cudaSuccess) e = cudaMalloc(&flag, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    tc_wide_probe_kernel<<<ctas, kProbeThreads, kProbeSmem, s>>>(passes, iters, d, flag);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(cycles, d, sizeof(double) * kProbeParts * ctas, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(timed_out, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d);
+  cudaFree(flag);
   return e;
 }
 

@@ -915,6 +915,45 @@ int plan_probe_alu(double* out, void* stream) {
   return PLAN_OK;
 }
 
+int plan_probe_tc_wide(int passes, int iters, double* out, void* stream) {
+  if (!out) {
+    set_unbound_error("NULL out");
+    return PLAN_EINVAL;
+  }
+  if ((passes != 1 && passes != 3) || iters < 1 || iters > 10000) {
+    set_unbound_error("passes must be 1 or 3 and iters in [1, 10000]");
+    return PLAN_EINVAL;
+  }
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+    cudaGetLastError();
+    set_unbound_error("no CUDA device");
+    return PLAN_ECUDA;
+  }
+  std::vector<double> cyc(size_t(5) * sms);
+  int timed_out = 0;
+  const cudaError_t e = tc_wide_probe(passes, iters, sms, cyc.data(),
+                                      static_cast<cudaStream_t>(stream), &timed_out);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_unbound_error(cudaGetErrorString(e));
+    return PLAN_ECUDA;
+  }
+  if (timed_out) {
+    set_unbound_error("a bounded tensor-core wait gave up");
+    return PLAN_ETIMEOUT;
+  }
+  for (int q = 0; q < 5; ++q) {
+    std::vector<double> v(sms);
+    for (int c = 0; c < sms; ++c) v[c] = cyc[size_t(5) * c + q];
+    std::nth_element(v.begin(), v.begin() + sms / 2, v.end());
+    out[q] = v[sms / 2];
+  }
+  out[5] = double(sms);
+  return PLAN_OK;
+}
+
 int plan_probe_wait_timeout(int wait_us, void* stream) {
   if (wait_us < 1 || wait_us > 100000) {
     set_unbound_error("wait_us must be in [1, 100000]");
