@@ -1,8 +1,9 @@
 """Seeded random configurations through plan_solve against the FP64 oracle:
 basis width n in {8, 11, 16}, horizons m on both sides of the 128-step slot
 boundary, 0 to 32 obstacles, 1, 2 or 4 set-point segments, with and without
-goal entries, straight and curved roads, the plain FP64 path and the fused
-FP32 kernel at a random shape.  Each case draws its own configuration from
+goal entries, straight and curved roads, 1 to 40 samples (ragged against
+every tile size), the plain FP64 path and the fused FP32 kernel at a random
+shape.  Each case draws its own configuration from
 its index, so a failure names a reproducible case."""
 import numpy as np
 import pytest
@@ -31,6 +32,7 @@ def _case(idx):
     prec = pick(["fp64", "fp32", "fp32"])
     shape = pick(SHAPES)
     n_lanes = pick([2, 3, 4])
+    B = pick([1, 7, 24, 33, 40])
     prm = sg.Params(m=m, n_coef=n_coef, n_seg=n_seg, goal=goal, inner_iters=40)
     sc = sg.make_scene(7000 + idx, n_lanes=n_lanes, n_obs=n_obs,
                        obs_x=(10.0, 10.0 + 0.8 * m))
@@ -38,7 +40,7 @@ def _case(idx):
         kappa = float(s.uniform(0.005, 0.02, 1)[0])
         sc.road = sg.curved_road(n_lanes, kappa=kappa, bend=(20.0, 120.0),
                                  narrow_at=pick([None, 60.0]))
-    p = sg.make_samples(8000 + idx, sc, 24, n_seg,
+    p = sg.make_samples(8000 + idx, sc, B, n_seg,
                         goal_tf=(m - 1) * prm.dt if goal else None)
     return prm, sc, p, prec, shape
 
