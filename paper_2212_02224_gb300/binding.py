@@ -191,29 +191,38 @@ def make_config(prm, prec: int, max_obs: int, max_samples: int, max_scenes: int 
     return c
 
 
+def _rows(a, width):
+    """Contiguous float64 (rows x width) view of a, copied only when needed."""
+    if isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous:
+        return a.reshape(-1, width)
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1, width))
+
+
 def make_scenes(scenes):
     """(PlanScene array, keep-alive list) from objects with ego / n_lanes /
     lane_width / kappa_road / obstacles (N x 6 rows x0, y0, vx, vy, a, b)."""
     arr = (PlanScene * len(scenes))()
     keep = []
     for i, sc in enumerate(scenes):
-        e = [float(v) for v in sc.ego]
-        arr[i].ego = PlanEgo(*e)
+        e = sc.ego
+        arr[i].ego = PlanEgo(float(e[0]), float(e[1]), float(e[2]), float(e[3]), float(e[4]),
+                             float(e[5]))
         arr[i].n_lanes = int(sc.n_lanes)
         arr[i].lane_width = float(sc.lane_width)
         arr[i].kappa_road = float(sc.kappa_road)
         # obstacle rows and road knots are passed straight from float64 buffers
         # laid out like plan_obstacle / plan_road_knot
-        ob = np.ascontiguousarray(np.asarray(sc.obstacles, dtype=np.float64).reshape(-1, 6))
+        ob = _rows(sc.obstacles, 6)
         arr[i].n_obs = ob.shape[0]
         if ob.shape[0]:
             keep.append(ob)
             arr[i].obs = ob.ctypes.data
         else:
             arr[i].obs = None
-        road = np.ascontiguousarray(np.asarray(getattr(sc, "road", ()), dtype=np.float64).reshape(-1, 4))
-        arr[i].n_road = road.shape[0]
-        if road.shape[0]:
+        road = getattr(sc, "road", None)
+        road = _rows(road, 4) if road is not None and len(road) else None
+        arr[i].n_road = 0 if road is None else road.shape[0]
+        if road is not None:
             keep.append(road)
             arr[i].road = road.ctypes.data
         else:
