@@ -350,6 +350,26 @@ int plan_server_info(plan_server* srv, plan_server_stats* out);
  * the paper's method: it only changes how the work is laid out on the GPU. */
 int plan_set_tuning(plan_ctx* ctx, int warps_per_sample, int samples_per_cta);
 
+/* Launch form of the fused FP32 kernel.  With one CTA per tile of
+ * samples_per_cta samples, a CTA holds its SM until its slowest sample has
+ * finished, and every CTA stages the basis again.  The persistent form
+ * launches one wave of CTAs (as many as fit on the SMs at once); each CTA
+ * stages the basis once and each sample group takes the next unsolved sample
+ * from a device counter until none is left, so no group waits for the other
+ * groups of its CTA.  Results are bit-identical between the two forms.  The
+ * persistent form exists for the shapes with one warp per sample, and for two
+ * warps per sample when m > 128; the other shapes always run one CTA per tile.
+ *   PLAN_PERSIST_AUTO (the default): the persistent form when the tiles need
+ *                      more than one wave of CTAs,
+ *   PLAN_PERSIST_OFF:  always one CTA per tile,
+ *   PLAN_PERSIST_ON:   the persistent form whenever the shape has one.
+ * The counter belongs to the context, so solves of one context must not run
+ * concurrently on different streams.  Clears the captured graphs of
+ * plan_step_resident.  Errors: EINVAL (unknown mode).  Like plan_set_tuning,
+ * it changes only how the work is laid out on the GPU. */
+enum { PLAN_PERSIST_AUTO = 0, PLAN_PERSIST_OFF = 1, PLAN_PERSIST_ON = 2 };
+int plan_set_persistent(plan_ctx* ctx, int mode);
+
 /* Time every fused-kernel shape on B samples of `scene` (drawn from the
  * uniform first-iteration distribution), keep the fastest for this context and
  * return it.  Synchronous on `stream`; must not overlap other work of the

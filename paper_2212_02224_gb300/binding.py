@@ -93,7 +93,7 @@ EXPORTS = ("plan_init", "plan_destroy", "plan_status_str", "plan_last_error", "p
            "plan_solve_fp64_noalloc", "plan_advance", "plan_server_create", "plan_server_destroy",
            "plan_submit", "plan_poll", "plan_poll_any", "plan_end_episode", "plan_server_info",
            "plan_qp_forward", "plan_qp_backward", "plan_probe_alu", "plan_probe_wait_timeout",
-           "plan_probe_tc_wide")
+           "plan_probe_tc_wide", "plan_set_persistent")
 
 _lib = None
 
@@ -133,6 +133,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "plan_update_distribution": (I, [V, V, V, I, V, V, V]),
         "plan_sample": (I, [V, P(PlanScene), V, V, I, I, U64, U64, I, V, V]),
         "plan_set_tuning": (I, [V, I, I]),
+        "plan_set_persistent": (I, [V, I]),
         "plan_autotune": (I, [V, P(PlanScene), I, P(I), P(I), V]),
         "plan_solve_fp64_noalloc": (I, [P(PlanConfig), P(PlanScene), V, I, V, V, V, V]),
         "plan_advance": (I, [P(PlanConfig), P(PlanScene), P(D), I, P(PlanScene), P(PlanObstacle)]),
@@ -365,6 +366,15 @@ def plan_probe_wait_timeout(wait_us: int, stream: int = 0) -> int:
 
 def plan_set_tuning(ctx, warps_per_sample: int, samples_per_cta: int):
     check(load().plan_set_tuning(ctx, int(warps_per_sample), int(samples_per_cta)), ctx)
+
+
+PLAN_PERSIST_AUTO, PLAN_PERSIST_OFF, PLAN_PERSIST_ON = 0, 1, 2
+_PERSIST = {"auto": PLAN_PERSIST_AUTO, "off": PLAN_PERSIST_OFF, "on": PLAN_PERSIST_ON}
+
+
+def plan_set_persistent(ctx, mode):
+    """mode: "auto", "off", "on" or the PLAN_PERSIST_* value."""
+    check(load().plan_set_persistent(ctx, int(_PERSIST.get(mode, mode))), ctx)
 
 
 def plan_autotune(ctx, scene, B: int, stream: int = 0):

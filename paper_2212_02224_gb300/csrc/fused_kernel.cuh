@@ -2,6 +2,11 @@
 // k_fused_road.cu): Step 1 (Alg. 1 line 7 through the folded KKT
 // inverse of Eq. over_3), all K iterations of Alg. 2 and the scoring of
 // Alg. 1 line 9 / Sec. V-A, 1, 2 or 4 warps per sample, all state on chip.
+// Two launch forms run the same per-sample code (solve_sample): one tile of
+// samples per CTA (fused_kernel), or one wave of CTAs whose sample groups
+// take samples from a device counter (fused_persistent_kernel).  Products
+// whose rounding the compiler could otherwise contract in two ways are written
+// as explicit fmaf, so both forms give the same bits.
 //
 // State is kept relative to the Step-1 solution: delta = xi - xi_bar.  Per
 // iteration and sample the warp(s)
@@ -29,6 +34,11 @@
 // point h = o + (a max(1,d) cos, b max(1,d) sin) differs from the trajectory
 // point by (x - x_o, y - y_o) (1/d - 1) when d < 1 and by zero otherwise.
 #pragma once
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "internal.cuh"
 
@@ -141,57 +151,33 @@ struct RegCap {
   // rest is per-sample state; capped so that enough warps stay resident.  At
   // 4 warps per sample, 72 registers let 7 CTAs of 128 threads share an SM
   // (7 x 128 x 72 <= 65536), so 1000 samples fit one wave on 152 SMs; n = 16
-  // needs 80 to avoid spills
+  // needs 88 to avoid spills
   static constexpr int value =
       SLOTS * WPS >= 8 ? 255
                        : (SLOTS >= 4 ? 224
-                                     : (SLOTS == 2 ? 144 : (WPS == 4 ? (NC <= 11 ? 72 : 80) : 96)));
+                                     : (SLOTS == 2 ? 144 : (WPS == 4 ? (NC <= 11 ? 72 : 88) : 96)));
 };
 
-template <int NC, int SLOTS, int WPS, bool ROAD>
-__global__ void __launch_bounds__(256) __maxnreg__((RegCap<NC, SLOTS, WPS, ROAD>::value))
-fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ layout,
-             const double* __restrict__ obs, const Tile* __restrict__ tiles,
-             const double* __restrict__ pin, Consts c, Params prm,
-             double* __restrict__ xi_out, double* __restrict__ r_out,
-             double* __restrict__ cu_out, int* __restrict__ st_out) {
-  constexpr int NCP = basis32_ncp(NC);
-  constexpr int NP = NCP / 2;              // coefficient pairs
+// Rows 0..m-1 of the basis, then one zero row that lanes past the horizon
+// read: their kinematics are zero and their residual rows contribute nothing.
+// Threads first, first + step, ... copy.
+template <int NC>
+__device__ __forceinline__ void stage_basis(const Consts& c, int m, float* sW, int first, int step) {
   constexpr int ST = basis32_stride(NC);
-  constexpr int LPS = 32 * WPS;
-  constexpr bool kPairSlots = SLOTS % 2 == 0;
-  extern __shared__ __align__(16) float smem[];
-  const int m = prm.m;
-  const int ns = prm.n_seg;
-  const Tile tile = tiles[blockIdx.x];
-  const DevScene& sc = scenes[tile.scene];
+  const float4* src = reinterpret_cast<const float4*>(c.basis32);
+  float4* dst = reinterpret_cast<float4*>(sW);
+  for (int i = first; i < (m + 1) * ST / 4; i += step)
+    dst[i] = i < m * ST / 4 ? src[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// The scene's data in shared memory: the scaled obstacle trajectories
+// ([N][4] float4) and the rows of M for N obstacles ([2][NC][NC]).
+template <int NC>
+__device__ __forceinline__ void stage_scene(const DevScene& sc, const double* __restrict__ obs,
+                                            const Consts& c, const Params& prm, float4* sObs,
+                                            float* sM, int first, int step) {
   const int N = sc.n_obs;
-  const int warps = blockDim.x >> 5;
-  const int groups = warps / WPS;
-
-  float* sW = smem;                                          // [m + 1][ST]
-  float4* sObs = reinterpret_cast<float4*>(smem + (m + 1) * ST);   // [N][4]
-  float* sBuf = reinterpret_cast<float*>(sObs + 4 * N);      // [warps][64]
-  constexpr int RS = 32 * WPS + 4;                           // row stride of the reduction table
-  // floats per sample group: one warp transposes through a [2n][RS] table; with
-  // several warps each warp reduces with shuffles and the warps add their
-  // [32] results through a double-buffered [2][WPS][32] table
-  constexpr int RED = WPS > 1 ? 2 * WPS * 32 : 2 * NC * RS;
-  float* sRedAll = sBuf + 64 * warps;                        // [groups][RED]
-  float* sScore = sRedAll + groups * RED;                    // [groups][WPS][2]
-  float* sM = sScore + groups * WPS * 2;                     // [2][NC][NC] rows of M
-  float* sRef = sM + 2 * NC * NC;                            // [warps][6][SLOTS][32]
-  float* sThr = sRef + warps * 6 * SLOTS * 32;               // [warps][N] obstacle re-test levels
-
-  {
-    // rows 0..m-1 of the basis, then one zero row that lanes past the horizon
-    // read: their kinematics are zero and their residual rows contribute nothing
-    const float4* src = reinterpret_cast<const float4*>(c.basis32);
-    float4* dst = reinterpret_cast<float4*>(sW);
-    for (int i = threadIdx.x; i < (m + 1) * ST / 4; i += blockDim.x)
-      dst[i] = i < m * ST / 4 ? src[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+  for (int i = first; i < N; i += step) {
     // scaled trajectory: (x - x_o(t)) / a = x / a + (-x0/a) + (-vx dt / a) t,
     // constants duplicated for packed pairs of timesteps
     const double* o = obs + size_t(sc.obs_off + i) * 6;
@@ -203,17 +189,46 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
     sObs[4 * i + 2] = make_float4(float(ia), float(ia), float(ib), float(ib));
     sObs[4 * i + 3] = make_float4(float(o[4]), float(o[5]), 0.f, 0.f);
   }
-  for (int e = threadIdx.x; e < 2 * NC * NC; e += blockDim.x) {
+  for (int e = first; e < 2 * NC * NC; e += step) {
     const int ax_ = e / (NC * NC), k_ = (e / NC) % NC, i_ = e % NC;
     sM[e] = c.pj32[size_t((N * 2 + ax_) * NC + k_) * (2 * NC + c.ne) + i_];
   }
-  __syncthreads();
+}
 
+// Floats per sample group of the reduction table: one warp transposes through
+// a [2n][RS] table (RS = 32 WPS + 4); with several warps each warp reduces with
+// shuffles and the warps add their [32] results through a double-buffered
+// [2][WPS][32] table.
+template <int NC, int WPS>
+__host__ __device__ constexpr int red_floats() {
+  return WPS > 1 ? 2 * WPS * 32 : 2 * NC * (32 * WPS + 4);
+}
+
+// Step 1, the K iterations of Alg. 2 and the scoring of sample j by the
+// calling warp's sample group (group = warp / WPS of the CTA).  sW: the basis
+// rows; sObs, sM: the sample's scene data; sBuf ([warps][64]), sRedAll
+// ([groups][red_floats]), sScore ([groups][WPS][2]) and sRef
+// ([warps][6][SLOTS][32]) are the CTA's work areas; thr holds the calling
+// warp's obstacle re-test levels (n_obs floats).
+template <int NC, int SLOTS, int WPS, bool ROAD>
+__device__ __forceinline__ void solve_sample(
+    const DevScene& sc, int j, const float* sW, const float4* sObs, const float* sM, float* sBuf,
+    float* sRedAll, float* sScore, float* sRef, float* thr, const double* __restrict__ pin,
+    const Consts& c, const Params& prm, double* __restrict__ xi_out, double* __restrict__ r_out,
+    double* __restrict__ cu_out, int* __restrict__ st_out) {
+  constexpr int NCP = basis32_ncp(NC);
+  constexpr int NP = NCP / 2;              // coefficient pairs
+  constexpr int ST = basis32_stride(NC);
+  constexpr int LPS = 32 * WPS;
+  constexpr bool kPairSlots = SLOTS % 2 == 0;
+  constexpr int RS = 32 * WPS + 4;         // row stride of the reduction table
+  constexpr int RED = red_floats<NC, WPS>();
+  const int m = prm.m;
+  const int ns = prm.n_seg;
+  const int N = sc.n_obs;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = warp / WPS, wig = warp % WPS;
-  if (grp >= tile.count) return;
   const int gl = wig * 32 + lane;                           // lane within the sample group
-  const int j = layout[tile.scene].off + tile.first + grp;  // global sample index
   float* xbuf = sBuf + warp * 64;      // slot layout: xi_bar, then delta (per warp copy)
   float* vbuf = xbuf + 32;             // slot layout: lambda + rho w - delta
   float* sRed = sRedAll + grp * RED;
@@ -223,7 +238,6 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   // tested: positions are convex combinations of the coefficients (Bernstein
   // rows are nonnegative and sum to one), so no point moves further than the
   // largest coefficient change.  Skipped obstacles contribute exactly zero.
-  float* thr = sThr + warp * N;
   for (int i = lane; i < N; i += 32) thr[i] = -3.0e38f;
   float ia_max = 0.f, ib_max = 0.f;
   for (int i = lane; i < N; i += 32) {
@@ -373,14 +387,16 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       for (int s = 0; s < SLOTS; ++s) {
         const float sp = fast_sqrt(fmaf(vx[s], vx[s], vy[s] * vy[s]));
         const float am = fast_sqrt(fmaf(ax[s], ax[s], ay[s] * ay[s]));
-        const float kap = sp > 0.f ? __fdividef(ay[s] * vx[s] - ax[s] * vy[s], sp * sp * sp) : 0.f;
+        const float kap =
+            sp > 0.f ? __fdividef(fmaf(ay[s], vx[s], -(ax[s] * vy[s])), sp * sp * sp) : 0.f;
         float kro = kr, ylo = y_lb, yup = y_ub;
         if (road) {
           road_eval<float>(sc, px[s], &kro, &ylo, &yup);
           kro = fabsf(kro);
         }
         const float rt = coll[s] + fmaxf(0.f, sp - v_max) + fmaxf(0.f, am - a_max) +
-                         fmaxf(0.f, fabsf(kap) - kmax) + fmaxf(0.f, vx[s] * vx[s] * kro - c_max) +
+                         fmaxf(0.f, fabsf(kap) - kmax) +
+                         fmaxf(0.f, fmaf(vx[s] * vx[s], kro, -c_max)) +
                          fmaxf(0.f, py[s] - yup) + fmaxf(0.f, ylo - py[s]);
         const float dv = sp - v_max;
         r_acc = fmaf(act[s], rt, r_acc);
@@ -389,7 +405,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       break;
     }
 
-    moved += 1.41422f * moved_step;
+    moved = fmaf(1.41422f, moved_step, moved);
     // ---- B: obstacle projection, accumulated residual sum_i (h_o,i - p).
     // For every obstacle within reach, one pass computes the scaled offsets of
     // all slots and gives the points inside its ellipse (d < 1) the correction
@@ -475,7 +491,7 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
       const bool ap = a2 >= kFltMin;
       const float ra = rsqrt_ftz(a2);
       const float ca = ap ? ax[s] * ra : 1.f, sa = ap ? ay[s] * ra : 0.f, am = ap ? a2 * ra : 0.f;
-      const float S = fabsf(sa * cv - ca * sv);               // |sin(alpha_a - alpha_v)|
+      const float S = fabsf(fmaf(sa, cv, -(ca * sv)));       // |sin(alpha_a - alpha_v)|
       const float dap = (it == 0) ? fminf(am, a_max) : da[s];
       const float vmin_b = fmaxf(v_min, fast_sqrt(dap * S * inv_kmax));
       float vmax_b = v_max;
@@ -628,33 +644,231 @@ fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ lay
   }
 }
 
+// One tile (up to samples_per_cta samples of one scene) per CTA.
+template <int NC, int SLOTS, int WPS, bool ROAD>
+__global__ void __launch_bounds__(256) __maxnreg__((RegCap<NC, SLOTS, WPS, ROAD>::value))
+fused_kernel(const DevScene* __restrict__ scenes, const Layout* __restrict__ layout,
+             const double* __restrict__ obs, const Tile* __restrict__ tiles,
+             const double* __restrict__ pin, Consts c, Params prm,
+             double* __restrict__ xi_out, double* __restrict__ r_out,
+             double* __restrict__ cu_out, int* __restrict__ st_out) {
+  constexpr int ST = basis32_stride(NC);
+  constexpr int RED = red_floats<NC, WPS>();
+  extern __shared__ __align__(16) float smem[];
+  const int m = prm.m;
+  const Tile tile = tiles[blockIdx.x];
+  const DevScene& sc = scenes[tile.scene];
+  const int N = sc.n_obs;
+  const int warps = blockDim.x >> 5;
+  const int groups = warps / WPS;
+
+  float* sW = smem;                                          // [m + 1][ST]
+  float4* sObs = reinterpret_cast<float4*>(smem + (m + 1) * ST);   // [N][4]
+  float* sBuf = reinterpret_cast<float*>(sObs + 4 * N);      // [warps][64]
+  float* sRedAll = sBuf + 64 * warps;                        // [groups][RED]
+  float* sScore = sRedAll + groups * RED;                    // [groups][WPS][2]
+  float* sM = sScore + groups * WPS * 2;                     // [2][NC][NC] rows of M
+  float* sRef = sM + 2 * NC * NC;                            // [warps][6][SLOTS][32]
+  float* sThr = sRef + warps * 6 * SLOTS * 32;               // [warps][N] obstacle re-test levels
+
+  stage_basis<NC>(c, m, sW, threadIdx.x, blockDim.x);
+  stage_scene<NC>(sc, obs, c, prm, sObs, sM, threadIdx.x, blockDim.x);
+  __syncthreads();
+
+  const int warp = threadIdx.x >> 5;
+  const int grp = warp / WPS;
+  if (grp >= tile.count) return;
+  solve_sample<NC, SLOTS, WPS, ROAD>(sc, layout[tile.scene].off + tile.first + grp, sW, sObs, sM,
+                                     sBuf, sRedAll, sScore, sRef, sThr + warp * N, pin, c, prm,
+                                     xi_out, r_out, cu_out, st_out);
+}
+
+// The persistent form exists for the shapes with four or more timestep slots
+// per lane: one warp per sample, and two warps per sample beyond 128 steps
+// (the shapes chosen for launches of more than one wave); the others always
+// launch one tile per CTA.  Its registers: the sample loop keeps a few more
+// values live than one tile does; where the one-tile form is uncapped, 168 keep
+// three CTAs of 128 threads per SM (3 x 128 x 168 <= 65536).
+template <int SLOTS>
+constexpr bool has_persistent() { return SLOTS >= 4; }
+
+template <int NC, int SLOTS, int WPS, bool ROAD>
+struct RegCapPersistent {
+  static constexpr int value = SLOTS * WPS >= 8 ? 168 : RegCap<NC, SLOTS, WPS, ROAD>::value;
+};
+
+// Persistent form, for launches of more than one wave of CTAs: the grid is one
+// wave, each CTA stages the basis once, and each sample group takes the next
+// sample (a global index into p) from the counter work[0] until none is left,
+// so a group whose sample finished early starts another one instead of
+// waiting for the other groups of its CTA.  Each group keeps its own copy of
+// its sample's scene data (obstacles and rows of M, for up to max_obs
+// obstacles) and restages it when the next sample belongs to another scene.
+// work[1] counts the groups that found no sample left; the last of them resets
+// both counters to zero for the next launch.  No thread waits on another CTA.
+template <int NC, int SLOTS, int WPS, bool ROAD>
+__global__ void __launch_bounds__(256) __maxnreg__((RegCapPersistent<NC, SLOTS, WPS, ROAD>::value))
+fused_persistent_kernel(const DevScene* __restrict__ scenes, const double* __restrict__ obs,
+                        const int* __restrict__ sample_scene, int total, int* work,
+                        const double* __restrict__ pin, Consts c, Params prm,
+                        double* __restrict__ xi_out, double* __restrict__ r_out,
+                        double* __restrict__ cu_out, int* __restrict__ st_out) {
+  constexpr int ST = basis32_stride(NC);
+  constexpr int LPS = 32 * WPS;
+  constexpr int RED = red_floats<NC, WPS>();
+  extern __shared__ __align__(16) float smem[];
+  const int m = prm.m;
+  const int NO = prm.max_obs;
+  const int warps = blockDim.x >> 5;
+  const int groups = warps / WPS;
+
+  float* sW = smem;                                                   // [m + 1][ST]
+  float4* sObsAll = reinterpret_cast<float4*>(smem + (m + 1) * ST);   // [groups][NO][4]
+  float* sBuf = reinterpret_cast<float*>(sObsAll + 4 * NO * groups);  // [warps][64]
+  float* sRedAll = sBuf + 64 * warps;                                 // [groups][RED]
+  float* sScore = sRedAll + groups * RED;                             // [groups][WPS][2]
+  float* sMAll = sScore + groups * WPS * 2;                           // [groups][2][NC][NC]
+  float* sRef = sMAll + groups * 2 * NC * NC;                         // [warps][6][SLOTS][32]
+  float* sThr = sRef + warps * 6 * SLOTS * 32;                        // [warps][NO]
+  int* sTicket = reinterpret_cast<int*>(sThr + warps * NO);           // [groups]
+
+  stage_basis<NC>(c, m, sW, threadIdx.x, blockDim.x);
+  __syncthreads();
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = warp / WPS, wig = warp % WPS;
+  const int gl = wig * 32 + lane;
+  float4* sObs = sObsAll + 4 * NO * grp;
+  float* sM = sMAll + grp * 2 * NC * NC;
+  // the previous launch on the stream resets the counters as it ends, and a
+  // programmatic launch may start before that: take no sample until it is done
+  pdl_wait();
+  int cur = -1;
+  for (;;) {
+    int j;
+    if constexpr (WPS == 1) {
+      int t = 0;
+      if (lane == 0) t = atomicAdd(work, 1);
+      j = __shfl_sync(kFull, t, 0);
+    } else {
+      // every warp of the group has read the previous ticket: it passed the
+      // group barriers of that sample's solve since
+      if (gl == 0) sTicket[grp] = atomicAdd(work, 1);
+      group_barrier(grp, LPS);
+      j = sTicket[grp];
+    }
+    if (j >= total) break;
+    const int s = sample_scene[j];
+    if (s != cur) {
+      // the group's warps are past the previous sample: restage its scene data
+      stage_scene<NC>(scenes[s], obs, c, prm, sObs, sM, gl, LPS);
+      if constexpr (WPS == 1) __syncwarp(); else group_barrier(grp, LPS);
+      cur = s;
+    }
+    solve_sample<NC, SLOTS, WPS, ROAD>(scenes[s], j, sW, sObs, sM, sBuf, sRedAll, sScore, sRef,
+                                       sThr + warp * NO, pin, c, prm, xi_out, r_out, cu_out,
+                                       st_out);
+  }
+  if (gl == 0) {
+    __threadfence();   // this group's last ticket is taken before it counts itself done
+    if (atomicAdd(work + 1, 1) == int(gridDim.x) * groups - 1) {
+      atomicExch(work, 0);
+      atomicExch(work + 1, 0);
+    }
+  }
+}
+
 template <int NC, int SLOTS, int WPS>
 size_t smem_bytes(const Params& prm, int spc) {
   const int warps = spc * WPS;
-  const int red = WPS > 1 ? 2 * WPS * 32 : 2 * NC * (32 * WPS + 4);
+  const int red = red_floats<NC, WPS>();
   size_t f = size_t(prm.m + 1) * basis32_stride(NC) + 16 * prm.max_obs + 64 * warps + spc * red +
              spc * WPS * 2 + 2 * NC * NC + size_t(6) * SLOTS * 32 * warps + size_t(warps) * prm.max_obs;
   return f * sizeof(float);
 }
 
+// Shared memory of fused_persistent_kernel: the basis once, the scene data and
+// the reduction table per group, the work areas per warp, one ticket per group.
+template <int NC, int SLOTS, int WPS>
+size_t smem_bytes_persistent(const Params& prm, int spc) {
+  const int warps = spc * WPS;
+  const size_t per_group =
+      size_t(16) * prm.max_obs + 2 * NC * NC + red_floats<NC, WPS>() + WPS * 2 + 1;
+  const size_t per_warp = 64 + size_t(6) * SLOTS * 32 + prm.max_obs;
+  const size_t f = size_t(prm.m + 1) * basis32_stride(NC) + spc * per_group + warps * per_warp;
+  return f * sizeof(float);
+}
+
+// Resident CTAs per SM of a kernel at a block size and dynamic shared memory,
+// from the occupancy calculator, cached per (device, kernel, block, bytes).
+inline cudaError_t blocks_per_sm(const void* fn, int threads, size_t smem, int* out) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void*, int, size_t>, int> cache;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const auto key = std::make_tuple(dev, fn, threads, smem);
+  std::lock_guard<std::mutex> lk(mu);
+  const auto it = cache.find(key);
+  if (it != cache.end()) {
+    *out = it->second;
+    return cudaSuccess;
+  }
+  int n = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (n < 1) return cudaErrorInvalidConfiguration;
+  cache[key] = n;
+  *out = n;
+  return cudaSuccess;
+}
+
 template <int NC, int SLOTS, int WPS, bool ROAD>
-cudaError_t launch_t(const DevScene* scenes, const Layout* layout, const double* obs,
-                     const Tile* tiles, int n_tiles, int spc, const double* p, const Consts& c,
-                     const Params& prm, double* xi, double* r, double* cu, int* st, cudaStream_t s) {
-  return launch_pdl(fused_kernel<NC, SLOTS, WPS, ROAD>, dim3(n_tiles), dim3(spc * WPS * 32),
-                    smem_bytes<NC, SLOTS, WPS>(prm, spc), s, scenes, layout, obs, tiles, p, c, prm,
-                    xi, r, cu, st);
+cudaError_t launch_t(const FusedLaunch& L, const Consts& c, const Params& prm, cudaStream_t s) {
+  const int threads = L.spc * WPS * 32;
+  bool persist = has_persistent<SLOTS>() && L.persist == PLAN_PERSIST_ON;
+  if (has_persistent<SLOTS>() && L.persist == PLAN_PERSIST_AUTO) {
+    // persistent once the tiles need more than one wave of CTAs
+    int per_sm = 0;
+    const cudaError_t e =
+        blocks_per_sm(reinterpret_cast<const void*>(fused_kernel<NC, SLOTS, WPS, ROAD>), threads,
+                      smem_bytes<NC, SLOTS, WPS>(prm, L.spc), &per_sm);
+    if (e != cudaSuccess) return e;
+    persist = L.n_tiles > per_sm * L.sms;
+  }
+  if (!persist)
+    return launch_pdl(fused_kernel<NC, SLOTS, WPS, ROAD>, dim3(L.n_tiles), dim3(threads),
+                      smem_bytes<NC, SLOTS, WPS>(prm, L.spc), s, L.scenes, L.layout, L.obs, L.tiles,
+                      L.p, c, prm, L.xi, L.r, L.cu, L.st);
+  if constexpr (has_persistent<SLOTS>()) {
+    auto* fn = fused_persistent_kernel<NC, SLOTS, WPS, ROAD>;
+    const size_t bytes = smem_bytes_persistent<NC, SLOTS, WPS>(prm, L.spc);
+    int per_sm = 0;
+    const cudaError_t e = blocks_per_sm(reinterpret_cast<const void*>(fn), threads, bytes, &per_sm);
+    if (e != cudaSuccess) return e;
+    const int ctas = std::min(per_sm * L.sms, (L.total + L.spc - 1) / L.spc);
+    return launch_pdl(fn, dim3(ctas), dim3(threads), bytes, s, L.scenes, L.obs, L.sample_scene,
+                      L.total, L.work, L.p, c, prm, L.xi, L.r, L.cu, L.st);
+  }
+  return cudaErrorInvalidValue;   // not reached: persist is false without the form
 }
 
 template <int NC, int SLOTS, int WPS, bool ROAD>
 void set_attr() {
-  cudaFuncSetAttribute(fused_kernel<NC, SLOTS, WPS, ROAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       200 * 1024);
   // every CTA stages the basis: ask for the largest shared-memory carveout so
   // that occupancy is bounded by registers, not by the L1 / shared split
+  cudaFuncSetAttribute(fused_kernel<NC, SLOTS, WPS, ROAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       200 * 1024);
   cudaFuncSetAttribute(fused_kernel<NC, SLOTS, WPS, ROAD>,
                        cudaFuncAttributePreferredSharedMemoryCarveout,
                        int(cudaSharedmemCarveoutMaxShared));
+  if constexpr (has_persistent<SLOTS>()) {
+    cudaFuncSetAttribute(fused_persistent_kernel<NC, SLOTS, WPS, ROAD>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(fused_persistent_kernel<NC, SLOTS, WPS, ROAD>,
+                         cudaFuncAttributePreferredSharedMemoryCarveout,
+                         int(cudaSharedmemCarveoutMaxShared));
+  }
 }
 
 template <int NC, bool ROAD>
@@ -665,27 +879,23 @@ void set_attr_nc() {
 }
 
 template <int NC, bool ROAD>
-cudaError_t launch_nc(int wps, const DevScene* scenes, const Layout* layout, const double* obs,
-                      const Tile* tiles, int n_tiles, int spc, const double* p, const Consts& c,
-                      const Params& prm, double* xi, double* r, double* cu, int* st, cudaStream_t s) {
-  const int m = prm.m;
-#define PLAN_L(SL, W) \
-  launch_t<NC, SL, W, ROAD>(scenes, layout, obs, tiles, n_tiles, spc, p, c, prm, xi, r, cu, st, s)
-  if (wps == 1) return m <= 128 ? PLAN_L(4, 1) : PLAN_L(8, 1);
-  if (wps == 2) return m <= 128 ? PLAN_L(2, 2) : PLAN_L(4, 2);
-  if (wps == 4) return m <= 128 ? PLAN_L(1, 4) : PLAN_L(2, 4);
-#undef PLAN_L
+cudaError_t launch_nc(const FusedLaunch& L, const Consts& c, const Params& prm, cudaStream_t s) {
+  // timestep slots per lane: horizons up to 128 steps fit half as many
+  const bool short_h = prm.m <= 128;
+  if (L.wps == 1)
+    return short_h ? launch_t<NC, 4, 1, ROAD>(L, c, prm, s) : launch_t<NC, 8, 1, ROAD>(L, c, prm, s);
+  if (L.wps == 2)
+    return short_h ? launch_t<NC, 2, 2, ROAD>(L, c, prm, s) : launch_t<NC, 4, 2, ROAD>(L, c, prm, s);
+  if (L.wps == 4)
+    return short_h ? launch_t<NC, 1, 4, ROAD>(L, c, prm, s) : launch_t<NC, 2, 4, ROAD>(L, c, prm, s);
   return cudaErrorInvalidValue;
 }
 
 template <bool ROAD>
-cudaError_t launch_road(const DevScene* scenes, const Layout* layout, const double* obs,
-                        const Tile* tiles, int n_tiles, int wps, int spc, const double* p,
-                        const Consts& c, const Params& prm, double* xi, double* r, double* cu,
-                        int* st, cudaStream_t s) {
-  if (prm.n == 8) return launch_nc<8, ROAD>(wps, scenes, layout, obs, tiles, n_tiles, spc, p, c, prm, xi, r, cu, st, s);
-  if (prm.n == 11) return launch_nc<11, ROAD>(wps, scenes, layout, obs, tiles, n_tiles, spc, p, c, prm, xi, r, cu, st, s);
-  if (prm.n == 16) return launch_nc<16, ROAD>(wps, scenes, layout, obs, tiles, n_tiles, spc, p, c, prm, xi, r, cu, st, s);
+cudaError_t launch_road(const FusedLaunch& L, const Consts& c, const Params& prm, cudaStream_t s) {
+  if (prm.n == 8) return launch_nc<8, ROAD>(L, c, prm, s);
+  if (prm.n == 11) return launch_nc<11, ROAD>(L, c, prm, s);
+  if (prm.n == 16) return launch_nc<16, ROAD>(L, c, prm, s);
   return cudaErrorInvalidValue;
 }
 
@@ -700,9 +910,7 @@ void setup_road() {
 
 // The road-profile instantiations live in k_fused_road.cu (compiled in parallel).
 void fused_setup_road();
-cudaError_t launch_fused_f32_road(const DevScene* scenes, const Layout* layout, const double* obs,
-                                  const Tile* tiles, int n_tiles, int wps, int spc, const double* p,
-                                  const Consts& c, const Params& prm, double* xi, double* r,
-                                  double* cu, int* st, cudaStream_t s);
+cudaError_t launch_fused_f32_road(const FusedLaunch& L, const Consts& c, const Params& prm,
+                                  cudaStream_t s);
 
 }  // namespace plan

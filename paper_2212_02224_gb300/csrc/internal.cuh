@@ -228,12 +228,28 @@ cudaError_t build_constants(const Consts& c, const Params& p, cudaStream_t s);
 bool fused_supported(int n, int m);
 // wps = warps per sample (1, 2, 4), spc = samples per CTA (spc * wps <= 8)
 bool fused_shape_ok(int wps, int spc);
-// road: some scene of the launch has a road profile (selects the instantiations
-// that evaluate curvature and lane limits per timestep)
-cudaError_t launch_fused_f32(const DevScene* scenes, const Layout* layout, const double* obs,
-                             const Tile* tiles, int n_tiles, int wps, int spc, const double* p,
-                             const Consts& c, const Params& prm, double* xi, double* r,
-                             double* cu, int* st, bool road, cudaStream_t s);
+
+// One launch of the fused FP32 solve over `total` samples of the scenes.
+struct FusedLaunch {
+  const DevScene* scenes;
+  const Layout* layout;
+  const double* obs;
+  const Tile* tiles;        // tiles of spc samples (one CTA each)
+  int n_tiles;
+  const int* sample_scene;  // scene of every sample (persistent form)
+  int total;
+  int* work;                // two zeroed ints owned by the context (persistent form)
+  int sms;
+  int persist;              // PLAN_PERSIST_AUTO, _OFF or _ON
+  int wps, spc;
+  bool road;                // some scene has a road profile (selects the instantiations
+                            // that evaluate curvature and lane limits per timestep)
+  const double* p;
+  double *xi, *r, *cu;
+  int* st;
+};
+cudaError_t launch_fused_f32(const FusedLaunch& L, const Consts& c, const Params& prm,
+                             cudaStream_t s);
 
 // Tensor-core modes (PLAN_PREC_TF32, _BF16, _TF32X3): tiles of
 // tc_samples_per_cta() samples; err is set to 1 if a wait timed out.

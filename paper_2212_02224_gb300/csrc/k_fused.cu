@@ -20,16 +20,17 @@ bool fused_shape_ok(int wps, int spc) {
   return wps == 4 && spc == 1;
 }
 
-cudaError_t launch_fused_f32(const DevScene* scenes, const Layout* layout, const double* obs,
-                             const Tile* tiles, int n_tiles, int wps, int spc, const double* p,
-                             const Consts& c, const Params& prm, double* xi, double* r,
-                             double* cu, int* st, bool road, cudaStream_t s) {
-  if (n_tiles == 0) return cudaSuccess;
-  if (!fused_shape_ok(wps, spc)) return cudaErrorInvalidValue;
-  if (road)
-    return launch_fused_f32_road(scenes, layout, obs, tiles, n_tiles, wps, spc, p, c, prm, xi, r,
-                                 cu, st, s);
-  return launch_road<false>(scenes, layout, obs, tiles, n_tiles, wps, spc, p, c, prm, xi, r, cu, st, s);
+cudaError_t launch_fused_f32(const FusedLaunch& L, const Consts& c, const Params& prm,
+                             cudaStream_t s) {
+  if (L.n_tiles == 0) return cudaSuccess;
+  if (!fused_shape_ok(L.wps, L.spc)) return cudaErrorInvalidValue;
+  if (L.persist != PLAN_PERSIST_AUTO && L.persist != PLAN_PERSIST_OFF &&
+      L.persist != PLAN_PERSIST_ON)
+    return cudaErrorInvalidValue;
+  if (L.persist != PLAN_PERSIST_OFF && (!L.work || !L.sample_scene || L.sms < 1))
+    return cudaErrorInvalidValue;
+  if (L.road) return launch_fused_f32_road(L, c, prm, s);
+  return launch_road<false>(L, c, prm, s);
 }
 
 }  // namespace plan

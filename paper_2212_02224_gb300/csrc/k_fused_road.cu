@@ -6,11 +6,9 @@ namespace plan {
 
 void fused_setup_road() { setup_road<true>(); }
 
-cudaError_t launch_fused_f32_road(const DevScene* scenes, const Layout* layout, const double* obs,
-                                  const Tile* tiles, int n_tiles, int wps, int spc, const double* p,
-                                  const Consts& c, const Params& prm, double* xi, double* r,
-                                  double* cu, int* st, cudaStream_t s) {
-  return launch_road<true>(scenes, layout, obs, tiles, n_tiles, wps, spc, p, c, prm, xi, r, cu, st, s);
+cudaError_t launch_fused_f32_road(const FusedLaunch& L, const Consts& c, const Params& prm,
+                                  cudaStream_t s) {
+  return launch_road<true>(L, c, prm, s);
 }
 
 }  // namespace plan

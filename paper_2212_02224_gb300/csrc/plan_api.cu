@@ -50,6 +50,7 @@ struct plan_ctx {
   int device = 0;
   int sms = 0;                      // multiprocessors of the device
   int tune_wps = 0, tune_spc = 0;   // fused-kernel shape; 0 = automatic
+  int persist = PLAN_PERSIST_AUTO;  // launch form of the fused kernel
   cudaStream_t internal = nullptr;
   cudaStream_t capture = nullptr;
 
@@ -72,6 +73,7 @@ struct plan_ctx {
   double* cu = nullptr;
   int* elite = nullptr;    // [max_scenes][q]
   int* tc_err = nullptr;   // timeout flag of the tensor-core kernel
+  int* work = nullptr;     // [2] sample counter and finished groups of the persistent kernel
   Plain64Work pw{};
   DevCem* cem_tmp = nullptr;   // single-stage sampling
   Layout* layout_tmp = nullptr;
@@ -349,8 +351,26 @@ cudaError_t run_solve(plan_ctx* ctx, const SceneSet& set, const SceneSet& lay, i
                       int* status, cudaStream_t s) {
   if (ctx->cfg.prec == PLAN_PREC_FP32) {
     const Shape sh = pick_shape(ctx, total_B);
-    return launch_fused_f32(set.scenes, lay.layout, set.obs, lay.tiles, n_tiles, sh.wps, sh.spc,
-                            p, ctx->c, ctx->prm, xi, r, cu, status, set.road, s);
+    FusedLaunch L{};
+    L.scenes = set.scenes;
+    L.layout = lay.layout;
+    L.obs = set.obs;
+    L.tiles = lay.tiles;
+    L.n_tiles = n_tiles;
+    L.sample_scene = lay.sample_scene;
+    L.total = total_B;
+    L.work = ctx->work;
+    L.sms = ctx->sms;
+    L.persist = ctx->persist;
+    L.wps = sh.wps;
+    L.spc = sh.spc;
+    L.road = set.road;
+    L.p = p;
+    L.xi = xi;
+    L.r = r;
+    L.cu = cu;
+    L.st = status;
+    return launch_fused_f32(L, ctx->c, ctx->prm, s);
   }
   if (ctx->cfg.prec >= PLAN_PREC_TF32)
     return launch_tc(ctx->cfg.prec, set.scenes, lay.layout, set.obs, lay.tiles, n_tiles, p, ctx->c,
@@ -582,6 +602,7 @@ int plan_init(const plan_config* cfg, plan_ctx** out) {
   A(dalloc(ctx, &ctx->elite, size_t(c.max_scenes) * c.n_elite));
   A(dalloc(ctx, &ctx->rows, size_t(2) * c.max_scenes));
   A(dalloc(ctx, &ctx->tc_err, 1));
+  A(dalloc(ctx, &ctx->work, 2));
   if (c.prec == PLAN_PREC_FP64) {
     A(dalloc(ctx, &ctx->pw.xibarp, B * 32));
     A(dalloc(ctx, &ctx->pw.xi, B * 32));
@@ -616,6 +637,7 @@ int plan_init(const plan_config* cfg, plan_ctx** out) {
   if (build_constants(k, p, ctx->internal) != cudaSuccess ||
       cudaMemsetAsync(ctx->cem, 0, sizeof(DevCem) * c.max_scenes, ctx->internal) != cudaSuccess ||
       cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), ctx->internal) != cudaSuccess ||
+      cudaMemsetAsync(ctx->work, 0, 2 * sizeof(int), ctx->internal) != cudaSuccess ||
       cudaStreamSynchronize(ctx->internal) != cudaSuccess) {
     cudaGetLastError();
     return bail(PLAN_ECUDA);
@@ -1043,6 +1065,19 @@ int plan_set_tuning(plan_ctx* ctx, int warps_per_sample, int samples_per_cta) {
   ctx->graphs.clear();   // their layout buffers stay in the arena until plan_destroy
   ctx->tune_wps = warps_per_sample;
   ctx->tune_spc = samples_per_cta;
+  return PLAN_OK;
+}
+
+int plan_set_persistent(plan_ctx* ctx, int mode) {
+  if (!ctx) return PLAN_EINVAL;
+  if (mode != PLAN_PERSIST_AUTO && mode != PLAN_PERSIST_OFF && mode != PLAN_PERSIST_ON)
+    return fail(ctx, PLAN_EINVAL, "mode must be PLAN_PERSIST_AUTO, _OFF or _ON");
+  CU(ctx, cudaSetDevice(ctx->device));
+  CU(ctx, cudaStreamSynchronize(ctx->internal));
+  for (auto& g : ctx->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  ctx->graphs.clear();
+  ctx->persist = mode;
   return PLAN_OK;
 }
 

@@ -116,6 +116,10 @@ class Planner:
     def set_tuning(self, warps_per_sample: int, samples_per_cta: int):
         B.plan_set_tuning(self.ctx, warps_per_sample, samples_per_cta)
 
+    def set_persistent(self, mode):
+        """Launch form of the fused FP32 kernel: "auto", "off" or "on"."""
+        B.plan_set_persistent(self.ctx, mode)
+
     def autotune(self, scene, Bn: int, stream=None):
         return B.plan_autotune(self.ctx, scene, Bn, _stream(stream))
 
