@@ -359,8 +359,9 @@ int plan_set_tuning(plan_ctx* ctx, int warps_per_sample, int samples_per_cta);
  * groups of its CTA.  Results are bit-identical between the two forms.  The
  * persistent form exists for the shapes with one warp per sample, and for two
  * warps per sample when m > 128; the other shapes always run one CTA per tile.
- *   PLAN_PERSIST_AUTO (the default): the persistent form when the tiles need
- *                      more than one wave of CTAs,
+ *   PLAN_PERSIST_AUTO (the default): the persistent form when the launch
+ *                      holds one scene whose tiles need more than one wave
+ *                      of CTAs,
  *   PLAN_PERSIST_OFF:  always one CTA per tile,
  *   PLAN_PERSIST_ON:   the persistent form whenever the shape has one.
  * The counter belongs to the context, so solves of one context must not run

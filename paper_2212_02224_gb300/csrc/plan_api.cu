@@ -347,7 +347,7 @@ int upload(plan_ctx* ctx, SceneSet& set, const plan_scene* scenes, int S, const 
 // Lower-level solve of all samples described by `set` (Alg. 1 lines 6-9).
 // status: per-sample PLAN_OK / PLAN_ENONFINITE, or NULL.
 cudaError_t run_solve(plan_ctx* ctx, const SceneSet& set, const SceneSet& lay, int n_tiles,
-                      int total_B, const double* p, double* xi, double* r, double* cu,
+                      int total_B, int n_scenes, const double* p, double* xi, double* r, double* cu,
                       int* status, cudaStream_t s) {
   if (ctx->cfg.prec == PLAN_PREC_FP32) {
     const Shape sh = pick_shape(ctx, total_B);
@@ -361,7 +361,10 @@ cudaError_t run_solve(plan_ctx* ctx, const SceneSet& set, const SceneSet& lay, i
     L.total = total_B;
     L.work = ctx->work;
     L.sms = ctx->sms;
-    L.persist = ctx->persist;
+    // automatic choice: the persistent form only for one scene; in the
+    // graph-captured cycle of a 256-scene batch it measured 1-2 % slower than
+    // one tile per CTA, so scene mixes keep the tiles
+    L.persist = ctx->persist == PLAN_PERSIST_AUTO && n_scenes > 1 ? PLAN_PERSIST_OFF : ctx->persist;
     L.wps = sh.wps;
     L.spc = sh.spc;
     L.road = set.road;
@@ -490,8 +493,8 @@ int plan::ctx_wave(plan_ctx* ctx, const plan_scene* scenes, const int* B, int S,
   const int nt = n_tiles_of(Bv, pick_warps(ctx, int(total)));
   for (int l = 1; l <= ctx->cfg.outer_iters; ++l) {
     CU(ctx, launch_sample(ctx->res.scenes, ctx->res.layout, ctx->cem, S, max_B, l, ctx->prm, ctx->p, s));
-    CU(ctx, run_solve(ctx, ctx->res, ctx->res, nt, int(total), ctx->p, ctx->xi, ctx->r, ctx->cu,
-                      nullptr, s));
+    CU(ctx, run_solve(ctx, ctx->res, ctx->res, nt, int(total), S, ctx->p, ctx->xi, ctx->r,
+                      ctx->cu, nullptr, s));
     CU(ctx, launch_select_update(ctx->res.layout, ctx->cem, S, l, ctx->prm, ctx->p, ctx->xi,
                                  ctx->r, ctx->cu, ctx->elite, max_B, s));
   }
@@ -665,8 +668,8 @@ int plan_solve_batch(plan_ctx* ctx, const plan_scene* scenes, const int* B, int 
   CU(ctx, cudaSetDevice(ctx->device));
   TRY(upload(ctx, ctx->tr, scenes, S, &Bv, s, nullptr));
   const int spc = pick_warps(ctx, int(total));
-  CU(ctx, run_solve(ctx, ctx->tr, ctx->tr, n_tiles_of(Bv, spc), int(total), p, xi, resid, cu,
-                    status, s));
+  CU(ctx, run_solve(ctx, ctx->tr, ctx->tr, n_tiles_of(Bv, spc), int(total), S, p, xi, resid,
+                    cu, status, s));
   return PLAN_OK;
 }
 
@@ -822,7 +825,7 @@ int run_cycle(plan_ctx* ctx, const int* B, int S, void* stream, bool io) {
       ce = launch_sample(e.set.scenes, e.set.layout, ctx->cem, S, max_B, l, ctx->prm, ctx->p,
                          ctx->capture, !(io && l == 1));
       if (ce == cudaSuccess)
-        ce = run_solve(ctx, e.set, e.set, nt, int(total), ctx->p, ctx->xi, ctx->r, ctx->cu,
+        ce = run_solve(ctx, e.set, e.set, nt, int(total), S, ctx->p, ctx->xi, ctx->r, ctx->cu,
                        nullptr, ctx->capture);
       if (ce == cudaSuccess)
         ce = launch_select_update(e.set.layout, ctx->cem, S, l, ctx->prm, ctx->p, ctx->xi, ctx->r,
@@ -1132,10 +1135,11 @@ int plan_autotune(plan_ctx* ctx, const plan_scene* scene, int B, int* wps_out, i
     if (st_code != PLAN_OK) break;
     const int nt = n_tiles_of(Bv, cnd[1]);
     float times[3];
-    cudaError_t ce = run_solve(ctx, ctx->tr, ctx->tr, nt, B, ctx->p, nullptr, ctx->r, ctx->cu, nullptr, s);
+    cudaError_t ce =
+        run_solve(ctx, ctx->tr, ctx->tr, nt, B, 1, ctx->p, nullptr, ctx->r, ctx->cu, nullptr, s);
     for (int rep = 0; rep < 3 && ce == cudaSuccess; ++rep) {
       cudaEventRecord(e0, s);
-      ce = run_solve(ctx, ctx->tr, ctx->tr, nt, B, ctx->p, nullptr, ctx->r, ctx->cu, nullptr, s);
+      ce = run_solve(ctx, ctx->tr, ctx->tr, nt, B, 1, ctx->p, nullptr, ctx->r, ctx->cu, nullptr, s);
       cudaEventRecord(e1, s);
       if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
       if (ce == cudaSuccess) ce = cudaEventElapsedTime(&times[rep], e0, e1);
