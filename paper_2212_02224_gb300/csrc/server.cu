@@ -113,11 +113,10 @@ int make_executor(plan_server* s, int m, std::unique_ptr<Executor>* out) {
   int st = plan_init(&cfg, &ctx);
   if (st != PLAN_OK) return st;
   // a fixed kernel shape per executor: a scene's arithmetic must not depend on
-  // how many other samples share its wave
-  // (the two launch forms give the same bits).  Waves of several executors
-  // share the device: a persistent grid would hold every SM it fits on until
-  // its last sample is done, keeping the other waves' CTAs out, so executors
-  // launch one CTA per tile and the block scheduler interleaves the waves
+  // how many other samples share its wave.  Executors launch one CTA per tile:
+  // waves of several executors share the device, and a persistent grid would
+  // hold every SM it fits on until its last sample is done, keeping the other
+  // waves' CTAs out (both launch forms give the same bits)
   if (cfg.prec == PLAN_PREC_FP32) {
     st = m > 128 ? plan_set_tuning(ctx, 2, 2) : plan_set_tuning(ctx, 1, 4);
     if (st == PLAN_OK) st = plan_set_persistent(ctx, PLAN_PERSIST_OFF);
