@@ -293,10 +293,17 @@ cudaError_t launch_plain64(const DevScene* scenes, const Layout* layout, const i
                            const Params& prm, const Plain64Work& w, double* xi_out, double* r,
                            double* cu, int* st, cudaStream_t s);
 
-// pdl = false: a full dependency on the preceding work of the stream
+// pdl = false: a full dependency on the preceding work of the stream.  zbuf:
+// the normals of iteration l written by launch_normals ([total B][d_p]), or
+// NULL to draw them in the sampling kernel.
 cudaError_t launch_sample(const DevScene* scenes, const Layout* layout, const DevCem* cem, int S,
                           int max_B, int l, const Params& prm, double* p, cudaStream_t s,
-                          bool pdl = true);
+                          bool pdl = true, const double* zbuf = nullptr);
+// The standard normals of outer iteration l >= 2 for every sample (Philox and
+// Box-Muller in float64), into zbuf; a plain launch, meant for a stream that
+// runs beside the solve of iteration l - 1.
+cudaError_t launch_normals(const Layout* layout, const DevCem* cem, int S, int max_B, int l,
+                           const Params& prm, double* zbuf, cudaStream_t s);
 // Staging of one cycle through a pinned, device-mapped host buffer `io`: the
 // scene record (offset 0), its obstacle rows (o_obs) and the sampling state
 // (o_cem) go to the device copies; the final state and the tensor-core timeout

@@ -28,18 +28,10 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 
 __device__ __forceinline__ double unit_open(unsigned w) { return (double(w) + 0.5) * 0x1p-32; }
 
-// Alg. 1 line 4 for every scene: grid (ceil(max_B / 128), S).
-__global__ void sample_kernel(const DevScene* scenes, const Layout* layout, const DevCem* cem,
-                              int l, Params prm, double* p) {
-  pdl_wait();      // the distribution comes from the previous selection kernel
-  pdl_trigger();
-  const int s = blockIdx.y;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const Layout lay = layout[s];
-  if (j >= lay.B) return;
-  const DevCem& st = cem[s];
-  const int d_p = prm.d_p, ns = prm.n_seg;
-  unsigned w[kMaxDp];
+// The Philox words of sample j in outer iteration l: entry e of p_j uses word
+// e mod 4 of block e div 4.
+__device__ __forceinline__ void philox_words(const DevCem& st, int j, int l, int d_p,
+                                             unsigned (&w)[kMaxDp]) {
   const uint2 key = make_uint2(unsigned(st.seed & 0xffffffffull), unsigned(st.seed >> 32));
   for (int c = 0; c < (d_p + 3) / 4; ++c) {
     const uint4 ctr = make_uint4(unsigned(j), unsigned(l) | (unsigned(c) << 16),
@@ -50,8 +42,43 @@ __global__ void sample_kernel(const DevScene* scenes, const Layout* layout, cons
     if (4 * c + 2 < kMaxDp) w[4 * c + 2] = o.z;
     if (4 * c + 3 < kMaxDp) w[4 * c + 3] = o.w;
   }
+}
+
+// Standard normals z of sample j in outer iteration l (Box-Muller on the word
+// pairs (2q, 2q+1)).  They depend only on the seed, the episode step, j and l,
+// not on the distribution being sampled.
+__device__ __forceinline__ void normals(const DevCem& st, int j, int l, int d_p,
+                                        double (&z)[kMaxDp]) {
+  unsigned w[kMaxDp];
+  philox_words(st, j, l, d_p, w);
+  for (int q = 0; 2 * q < d_p; ++q) {
+    // Box-Muller: r (cos, sin)(2 pi u2); sincospi takes the angle as a
+    // multiple of pi (2 u2 is exact), one argument reduction for both
+    const double r = sqrt(-2.0 * log(unit_open(w[2 * q])));
+    double sn, cs;
+    sincospi(2.0 * unit_open(w[2 * q + 1]), &sn, &cs);
+    z[2 * q] = r * cs;
+    z[2 * q + 1] = r * sn;
+  }
+}
+
+// Alg. 1 line 4 for every scene: grid (ceil(max_B / 128), S).  With zbuf the
+// normals of the Gaussian draw were computed beforehand by normals_kernel
+// (zbuf[(off + j) d_p + a]); without it they are computed here.
+__global__ void sample_kernel(const DevScene* scenes, const Layout* layout, const DevCem* cem,
+                              int l, Params prm, const double* zbuf, double* p) {
+  pdl_wait();      // the distribution comes from the previous selection kernel
+  pdl_trigger();
+  const int s = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const Layout lay = layout[s];
+  if (j >= lay.B) return;
+  const DevCem& st = cem[s];
+  const int d_p = prm.d_p, ns = prm.n_seg;
   double* out = p + size_t(lay.off + j) * d_p;
   if (l == 1 && st.fresh) {
+    unsigned w[kMaxDp];
+    philox_words(st, j, l, d_p, w);
     const DevScene& sc = scenes[s];
     for (int e = 0; e < ns; ++e) {
       int idx = int(floor(unit_open(w[e]) * sc.n_lanes));
@@ -71,21 +98,35 @@ __global__ void sample_kernel(const DevScene* scenes, const Layout* layout, cons
     }
   } else {
     double z[kMaxDp];
-    for (int q = 0; 2 * q < d_p; ++q) {
-      // Box-Muller: r (cos, sin)(2 pi u2); sincospi takes the angle as a
-      // multiple of pi (2 u2 is exact), one argument reduction for both
-      const double r = sqrt(-2.0 * log(unit_open(w[2 * q])));
-      double sn, cs;
-      sincospi(2.0 * unit_open(w[2 * q + 1]), &sn, &cs);
-      z[2 * q] = r * cs;
-      z[2 * q + 1] = r * sn;
+    if (zbuf) {
+      const double* zj = zbuf + size_t(lay.off + j) * d_p;
+      for (int a = 0; a < d_p; ++a) z[a] = zj[a];
+    } else {
+      normals(st, j, l, d_p, z);
     }
     for (int a = 0; a < d_p; ++a) {
       double v = 0.0;
-      for (int b = 0; b <= a; ++b) v += z[b] * st.chol[a * kMaxDp + b];
+      for (int b = 0; b <= a; ++b) v = fma(z[b], st.chol[a * kMaxDp + b], v);
       out[a] = st.mu[a] + v;
     }
   }
+}
+
+// The normals of outer iteration l for every sample into zbuf: grid
+// (ceil(max_B / 128), S).  It reads only the seed and the episode step, which
+// no kernel of the cycle changes before the last selection, so it can run
+// beside the solve of iteration l - 1.
+__global__ void normals_kernel(const Layout* layout, const DevCem* cem, int l, Params prm,
+                               double* zbuf) {
+  const int s = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const Layout lay = layout[s];
+  if (j >= lay.B) return;
+  const int d_p = prm.d_p;
+  double z[kMaxDp];
+  normals(cem[s], j, l, d_p, z);
+  double* out = zbuf + size_t(lay.off + j) * d_p;
+  for (int a = 0; a < d_p; ++a) out[a] = z[a];
 }
 
 // Total order on doubles: -0 is +0, NaN sorts after everything.  Integer
@@ -794,14 +835,22 @@ cudaError_t launch_cem_copy(DevCem* dst, const DevCem* src, const int* idx, int 
 
 cudaError_t launch_sample(const DevScene* scenes, const Layout* layout, const DevCem* cem, int S,
                           int max_B, int l, const Params& prm, double* p, cudaStream_t s,
-                          bool pdl) {
+                          bool pdl, const double* zbuf) {
   if (S == 0 || max_B == 0) return cudaSuccess;
   dim3 grid((max_B + 127) / 128, S);
   if (!pdl) {
-    sample_kernel<<<grid, 128, 0, s>>>(scenes, layout, cem, l, prm, p);
+    sample_kernel<<<grid, 128, 0, s>>>(scenes, layout, cem, l, prm, zbuf, p);
     return cudaGetLastError();
   }
-  return launch_pdl(sample_kernel, grid, dim3(128), 0, s, scenes, layout, cem, l, prm, p);
+  return launch_pdl(sample_kernel, grid, dim3(128), 0, s, scenes, layout, cem, l, prm, zbuf, p);
+}
+
+cudaError_t launch_normals(const Layout* layout, const DevCem* cem, int S, int max_B, int l,
+                           const Params& prm, double* zbuf, cudaStream_t s) {
+  if (S == 0 || max_B == 0) return cudaSuccess;
+  dim3 grid((max_B + 127) / 128, S);
+  normals_kernel<<<grid, 128, 0, s>>>(layout, cem, l, prm, zbuf);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_io_in(const void* io, size_t o_obs, size_t o_cem, DevScene* scene, double* obs,

@@ -53,6 +53,10 @@ struct plan_ctx {
   int persist = PLAN_PERSIST_AUTO;  // launch form of the fused kernel
   cudaStream_t internal = nullptr;
   cudaStream_t capture = nullptr;
+  // side branch of the captured cycle: the next iteration's normals are drawn
+  // on `side` while the current iteration solves (fork / join events)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 
   // arena
   std::vector<void*> allocs;
@@ -74,6 +78,7 @@ struct plan_ctx {
   int* elite = nullptr;    // [max_scenes][q]
   int* tc_err = nullptr;   // timeout flag of the tensor-core kernel
   int* work = nullptr;     // [2] sample counter and finished groups of the persistent kernel
+  double* zbuf = nullptr;  // [max_samples][d_p] normals of the next outer iteration
   Plain64Work pw{};
   DevCem* cem_tmp = nullptr;   // single-stage sampling
   Layout* layout_tmp = nullptr;
@@ -538,8 +543,11 @@ int plan_destroy(plan_ctx* ctx) {
   if (ctx->io) cudaFreeHost(ctx->io);
   if (ctx->stage_done) cudaEventDestroy(ctx->stage_done);
   if (ctx->tr_ready) cudaEventDestroy(ctx->tr_ready);
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
   if (ctx->internal) cudaStreamDestroy(ctx->internal);
   if (ctx->capture) cudaStreamDestroy(ctx->capture);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
   cudaSetDevice(dev);
   delete ctx;
   return PLAN_OK;
@@ -575,6 +583,9 @@ int plan_init(const plan_config* cfg, plan_ctx** out) {
   }
   if (cudaStreamCreateWithFlags(&ctx->internal, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->stage_done, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->tr_ready, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
@@ -606,6 +617,7 @@ int plan_init(const plan_config* cfg, plan_ctx** out) {
   A(dalloc(ctx, &ctx->rows, size_t(2) * c.max_scenes));
   A(dalloc(ctx, &ctx->tc_err, 1));
   A(dalloc(ctx, &ctx->work, 2));
+  if (c.outer_iters > 1) A(dalloc(ctx, &ctx->zbuf, B * d));
   if (c.prec == PLAN_PREC_FP64) {
     A(dalloc(ctx, &ctx->pw.xibarp, B * 32));
     A(dalloc(ctx, &ctx->pw.xi, B * 32));
@@ -819,11 +831,27 @@ int run_cycle(plan_ctx* ctx, const int* B, int S, void* stream, bool io) {
     if (io)
       ce = launch_io_in(ctx->io_dev, ctx->io_obs, ctx->io_cem, e.set.scenes, e.set.obs, ctx->cem,
                         ctx->capture);
-    for (int l = 1; l <= ctx->cfg.outer_iters && ce == cudaSuccess; ++l) {
+    const int L = ctx->cfg.outer_iters;
+    for (int l = 1; l <= L && ce == cudaSuccess; ++l) {
+      // the normals of iteration l >= 2 were drawn on the side stream beside
+      // the previous solve: join that branch before sampling
+      if (l >= 2) ce = cudaStreamWaitEvent(ctx->capture, ctx->join_ev, 0);
       // after the staging kernel the first sampling waits for it in full (its
       // writes are read by the solve's prologue before that kernel's own wait)
-      ce = launch_sample(e.set.scenes, e.set.layout, ctx->cem, S, max_B, l, ctx->prm, ctx->p,
-                         ctx->capture, !(io && l == 1));
+      if (ce == cudaSuccess)
+        ce = launch_sample(e.set.scenes, e.set.layout, ctx->cem, S, max_B, l, ctx->prm, ctx->p,
+                           ctx->capture, !(io && l == 1), l >= 2 ? ctx->zbuf : nullptr);
+      if (ce == cudaSuccess && l < L) {
+        // fork: the normals of iteration l + 1 (they depend only on the seed
+        // and the episode step) on the side stream, once this sampling has
+        // read the buffer; the float64 draws then overlap the float32 solve
+        ce = cudaEventRecord(ctx->fork_ev, ctx->capture);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(ctx->side, ctx->fork_ev, 0);
+        if (ce == cudaSuccess)
+          ce = launch_normals(e.set.layout, ctx->cem, S, max_B, l + 1, ctx->prm, ctx->zbuf,
+                              ctx->side);
+        if (ce == cudaSuccess) ce = cudaEventRecord(ctx->join_ev, ctx->side);
+      }
       if (ce == cudaSuccess)
         ce = run_solve(ctx, e.set, e.set, nt, int(total), S, ctx->p, ctx->xi, ctx->r, ctx->cu,
                        nullptr, ctx->capture);
