@@ -567,7 +567,9 @@ def gpu_arm(args):
                                     "each); e2e = wall time per plan_step call"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps * 3 * L,
+            # per cycle: sampling, solve and selection in each outer iteration, and
+            # the normals of iterations 2..L on the graph's side branch
+            "gpu_launches": args.steps * (3 * L + max(0, L - 1)),
             "plain_fp64": plain,
             "speedup_vs_plain_fp64": (value / plain["value"]) if plain else None,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
