@@ -86,6 +86,25 @@ def test_server_episode_matches_plan_step():
     pl.close()
 
 
+@pytest.mark.parametrize("outer", [2, 4])
+def test_fresh_cycle_through_the_server_matches_plan_step_bits(outer):
+    """plan_step's captured graph draws the normals of outer iterations 2..L on
+    a side stream beside the previous solve; the server's waves draw them inside
+    the sampling kernel.  A fresh cycle (nothing carried through the host) gives
+    the same bits on both."""
+    prm = _prm(outer_iters=outer)
+    sc = _scene(23, n_obs=8)
+    srv = Server(prm, max_obs=16, max_samples=2048, max_scenes=4, max_executors=1)
+    pl = Planner(prm, prec="fp32", max_obs=16, max_samples=2048)
+    pl.set_tuning(1, 4)                       # the executors' fixed shape
+    r_s = srv.wait(srv.submit(sc, 400, episode=7, seed=13))
+    r_p = pl.step(sc, 400, seed=13, step=0)
+    srv.close()
+    pl.close()
+    for key in ("p", "xi", "cost", "resid", "cu", "index"):
+        assert r_s[key] == r_p[key], key
+
+
 def test_fp64_episode_matches_oracle_episode():
     """Receding horizon on the FP64 path (plan_step + plan_advance) against the
     oracle's episode (upper.plan with warm starts + mpc.advance)."""
