@@ -239,7 +239,10 @@ int plan_solve_batch(plan_ctx* ctx, const plan_scene* scenes, const int* B, int 
 int plan_upload_scenes(plan_ctx* ctx, const plan_scene* scenes, int S, void* stream);
 
 /* Load (host -> device) or read back (device -> host, synchronous) the
- * sampling distribution of scene slot `slot`. */
+ * sampling distribution of scene slot `slot`.  A loaded covariance is factored
+ * on the device by the routine of the selection kernels, so that an episode
+ * exported after some cycles and loaded into a new context continues bit for
+ * bit as it would have without the interruption. */
 int plan_set_state(plan_ctx* ctx, int slot, const plan_cem_state* st, void* stream);
 int plan_get_state(plan_ctx* ctx, int slot, plan_cem_state* st, void* stream);
 

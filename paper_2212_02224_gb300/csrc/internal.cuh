@@ -299,6 +299,9 @@ cudaError_t launch_plain64(const DevScene* scenes, const Layout* layout, const i
 cudaError_t launch_sample(const DevScene* scenes, const Layout* layout, const DevCem* cem, int S,
                           int max_B, int l, const Params& prm, double* p, cudaStream_t s,
                           bool pdl = true, const double* zbuf = nullptr);
+// The Cholesky factor of one imported sampling state (not fresh), on the
+// device, by the selection kernels' routine.
+cudaError_t launch_import_chol(DevCem* cem, const Params& prm, cudaStream_t s);
 // The standard normals of outer iteration l >= 2 for every sample (Philox and
 // Box-Muller in float64), into zbuf; a plain launch, meant for a stream that
 // runs beside the solve of iteration l - 1.

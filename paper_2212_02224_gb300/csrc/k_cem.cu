@@ -378,6 +378,13 @@ __device__ __forceinline__ void cholesky(const double* sigma, double eps, int d,
   }
 }
 
+// Cholesky factor of an imported state (plan_set_state) by the routine the
+// selection kernels use, so that a resumed episode samples from the factor the
+// interrupted one would have used, bit for bit.  One thread.
+__global__ void import_chol_kernel(DevCem* cem, Params prm) {
+  if (threadIdx.x == 0 && !cem->fresh) cholesky(cem->sigma, prm.cov_eps, prm.d_p, cem->chol);
+}
+
 __global__ void __launch_bounds__(kSelThreads)
 select_update_kernel(const Layout* layout, DevCem* cem, int l, Params prm, const double* p,
                      const double* xi, const double* r, const double* cu, int* elite_out) {
@@ -843,6 +850,11 @@ cudaError_t launch_sample(const DevScene* scenes, const Layout* layout, const De
     return cudaGetLastError();
   }
   return launch_pdl(sample_kernel, grid, dim3(128), 0, s, scenes, layout, cem, l, prm, zbuf, p);
+}
+
+cudaError_t launch_import_chol(DevCem* cem, const Params& prm, cudaStream_t s) {
+  import_chol_kernel<<<1, 32, 0, s>>>(cem, prm);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_normals(const Layout* layout, const DevCem* cem, int S, int max_B, int l,

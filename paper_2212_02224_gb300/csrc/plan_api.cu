@@ -715,6 +715,10 @@ int plan_set_state(plan_ctx* ctx, int slot, const plan_cem_state* st, void* stre
   std::memcpy(ctx->stage, &c, sizeof c);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CU(ctx, cudaMemcpyAsync(ctx->cem + slot, ctx->stage, sizeof c, cudaMemcpyHostToDevice, s));
+  // the factor of an imported covariance is taken again on the device, by the
+  // routine that factored it in the interrupted episode (reciprocal square
+  // roots; the host's, with square root and division, differs in the last bits)
+  CU(ctx, launch_import_chol(ctx->cem + slot, ctx->prm, s));
   return stage_release(ctx, s);
 }
 

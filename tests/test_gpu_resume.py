@@ -1,10 +1,8 @@
 """Checkpoint and resume of an episode through plan_get_state / plan_set_state:
 an episode of four warm-started MPC cycles, interrupted after two (state
 exported, context destroyed, a new context created and the state imported),
-ends where the uninterrupted episode ends.  The Cholesky factor of the
-imported covariance is taken on the host (square root and division) while the
-device takes it with reciprocal square roots, so the two runs agree to
-rounding, not bit for bit: same chosen samples, plans within 1e-9."""
+ends where the uninterrupted episode ends, bit for bit (the imported
+covariance is factored on the device by the selection kernels' routine)."""
 import numpy as np
 import pytest
 
@@ -50,13 +48,7 @@ def test_resumed_episode_matches_uninterrupted(prec):
     pl.close()
 
     assert first == whole[:2]                      # the same program up to the checkpoint
-    tol = 1e-9 if prec == "fp64" else 1e-5
-    for got, ref in zip(second, whole[2:]):
-        assert got["index"] == ref["index"]
-        np.testing.assert_allclose(got["p"], ref["p"], rtol=tol, atol=tol)
-        np.testing.assert_allclose(got["xi"], ref["xi"], rtol=tol, atol=tol)
-        np.testing.assert_allclose(got["cost"], ref["cost"], rtol=tol, atol=tol)
+    assert second == whole[2:]                     # and after it, bit for bit
     assert resumed_state["step"] == final_state["step"] == 4
-    np.testing.assert_allclose(resumed_state["mu"], final_state["mu"], rtol=tol, atol=tol)
-    np.testing.assert_allclose(resumed_state["sigma"], final_state["sigma"], rtol=1e3 * tol,
-                               atol=tol)
+    np.testing.assert_array_equal(resumed_state["mu"], final_state["mu"])
+    np.testing.assert_array_equal(resumed_state["sigma"], final_state["sigma"])
