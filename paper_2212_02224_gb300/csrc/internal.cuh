@@ -310,9 +310,10 @@ cudaError_t launch_normals(const Layout* layout, const DevCem* cem, int S, int m
 // Staging of one cycle through a pinned, device-mapped host buffer `io`: the
 // scene record (offset 0), its obstacle rows (o_obs) and the sampling state
 // (o_cem) go to the device copies; the final state and the tensor-core timeout
-// flag come back to offset o_ret.  One CTA each.
+// flag come back to offset o_ret.  One CTA each.  The input kernel also
+// factors a warm start's covariance (the selection kernels' routine).
 cudaError_t launch_io_in(const void* io, size_t o_obs, size_t o_cem, DevScene* scene, double* obs,
-                         DevCem* cem, cudaStream_t s);
+                         DevCem* cem, const Params& prm, cudaStream_t s);
 cudaError_t launch_io_out(const DevCem* cem, const int* tc_err, void* io, size_t o_ret,
                           cudaStream_t s);
 

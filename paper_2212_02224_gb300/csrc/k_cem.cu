@@ -809,7 +809,7 @@ __global__ void cem_copy_kernel(DevCem* dst, const DevCem* src, const int* idx, 
 // the timeout flag back at its tail.  Offsets are in words; the host sizes the
 // obstacle region for max_obs rows and checks n_obs <= max_obs before staging.
 __global__ void io_in_kernel(const unsigned long long* io, size_t w_obs, size_t w_cem,
-                             DevScene* scene, double* obs, DevCem* cem) {
+                             DevScene* scene, double* obs, DevCem* cem, Params prm) {
   constexpr int WS = sizeof(DevScene) / sizeof(unsigned long long);
   constexpr int WC = sizeof(DevCem) / sizeof(unsigned long long);
   const int n_obs_w = reinterpret_cast<const DevScene*>(io)->n_obs * 6;
@@ -819,6 +819,11 @@ __global__ void io_in_kernel(const unsigned long long* io, size_t w_obs, size_t 
   for (int i = threadIdx.x; i < WS; i += blockDim.x) ds[i] = io[i];
   for (int i = threadIdx.x; i < n_obs_w; i += blockDim.x) dob[i] = io[w_obs + i];
   for (int i = threadIdx.x; i < WC; i += blockDim.x) dc[i] = io[w_cem + i];
+  // a warm start's covariance is factored here by the selection kernels'
+  // routine, so that the cycle samples exactly as one that kept its state on
+  // the device would
+  __syncthreads();
+  if (threadIdx.x == 0 && !cem->fresh) cholesky(cem->sigma, prm.cov_eps, prm.d_p, cem->chol);
 }
 
 __global__ void io_out_kernel(const DevCem* cem, const int* tc_err, unsigned long long* io,
@@ -866,9 +871,9 @@ cudaError_t launch_normals(const Layout* layout, const DevCem* cem, int S, int m
 }
 
 cudaError_t launch_io_in(const void* io, size_t o_obs, size_t o_cem, DevScene* scene, double* obs,
-                         DevCem* cem, cudaStream_t s) {
+                         DevCem* cem, const Params& prm, cudaStream_t s) {
   io_in_kernel<<<1, 256, 0, s>>>(static_cast<const unsigned long long*>(io), o_obs / 8, o_cem / 8,
-                                 scene, obs, cem);
+                                 scene, obs, cem, prm);
   return cudaGetLastError();
 }
 

@@ -834,7 +834,7 @@ int run_cycle(plan_ctx* ctx, const int* B, int S, void* stream, bool io) {
     cudaError_t ce = cudaSuccess;
     if (io)
       ce = launch_io_in(ctx->io_dev, ctx->io_obs, ctx->io_cem, e.set.scenes, e.set.obs, ctx->cem,
-                        ctx->capture);
+                        ctx->prm, ctx->capture);
     const int L = ctx->cfg.outer_iters;
     for (int l = 1; l <= L && ce == cudaSuccess; ++l) {
       // the normals of iteration l >= 2 were drawn on the side stream beside

@@ -17,7 +17,6 @@ from oracle import mpc
 from paper_2212_02224_gb300 import binding, scenegen as sg
 from paper_2212_02224_gb300.planner import Planner, Server, advance
 
-from gpu_common import FP32_POS_M, positions
 
 pytestmark = pytest.mark.gpu
 
@@ -64,7 +63,8 @@ def test_result_same_alone_and_in_the_mix():
 
 def test_server_episode_matches_plan_step():
     """Three cycles through the server vs three plan_step calls with the
-    distribution carried by the caller."""
+    distribution carried by the caller: the same bits (plan_step factors the
+    carried covariance on the device, as the server's selection did)."""
     prm = _prm()
     sc0 = _scene(21, n_obs=10)
     srv = Server(prm, max_obs=16, max_samples=2048, max_scenes=4, max_executors=1)
@@ -76,10 +76,8 @@ def test_server_episode_matches_plan_step():
         r_s = srv.wait(srv.submit(sc_s, 400, episode=5, seed=11))
         r_p = pl.step(sc_p, 400, mu=mu, sigma=sigma, seed=11, step=c)
         mu, sigma = r_p["mu"], r_p["sigma"]
-        xs, ys = positions(np.array([r_s["xi"]]), prm)
-        xp, yp = positions(np.array([r_p["xi"]]), prm)
-        assert float(np.hypot(xs - xp, ys - yp).max()) <= FP32_POS_M
-        assert abs(r_s["cost"] - r_p["cost"]) <= 1e-4 * abs(r_p["cost"]) + 1e-3
+        for key in ("p", "xi", "cost", "resid", "cu", "index"):
+            assert r_s[key] == r_p[key], (c, key)
         sc_s = advance(prm, sc_s, r_s["xi"])
         sc_p = advance(prm, sc_p, r_p["xi"])
     srv.close()
